@@ -1,0 +1,100 @@
+/*
+ * oracle.h — plain CPU oracle for BVH traversal with subspace culling
+ * (Yoshimura & Harada, "Subspace Culling for Ray-Box Intersection", 2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is a slow, direct restatement of
+ * the paper's definitions and algorithms.  It exists so that tests, the
+ * package's smoke check and the benchmark's CPU baseline can check and time
+ * the GPU path against it.  The product never links it, and it shares no
+ * code or header with the product.
+ *
+ * Conventions (shared *by specification* with the GPU path, not by code):
+ *  - triangles: float[n][9] (v0, v1, v2); the id of a triangle is its index.
+ *  - rays: float[n][8] = o.xyz, tmin, d.xyz, tmax.
+ *  - voxel bit order inside an R^3 mask: bit = x + R*y + R*R*z, packed in
+ *    little-endian uint32 words; W(R) = ceil(R^3 / 32) words per mask.
+ *  - BVH: binary, nodes hold two child slots; slot (child, count): count > 0
+ *    is a leaf with `count` triangles starting at position `child` of the
+ *    permuted triangle order, count == 0 an inner node with index `child`.
+ *    Node 0 is the root's node; nodes are numbered in pre-order.
+ */
+#ifndef SUBCULL_ORACLE_H
+#define SUBCULL_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+int or_mask_words(int R);
+
+/* Ray-mask lookup table (Sec. 3.1.1): bit v of entry (beg, end) is set iff
+   cell v is met by the sweep of cell beg towards cell end. */
+int or_raylut_cell(int R, const int* b, const int* e, const int* v);
+void or_raylut(int R, uint32_t* lut /* [R^3 * R^3][W] */);
+
+/* Conservative voxelization (Sec. 3.1.1): triangle-box overlap by the
+   separating axis theorem, in double. */
+int or_tri_box(const double* tri9, const double* bmin, const double* bmax);
+void or_voxelize(const float* tri9, const float* lo, const float* hi, int R,
+                 double eps, uint32_t* mask);
+/* Hierarchical fill (Alg. 2), borders dilated by eps. */
+void or_fill(uint32_t* mask, const float* plo, const float* phi,
+             const uint32_t* cmask, const float* clo, const float* chi, int R,
+             double eps);
+
+/* Compression LUT (Sec. 3.2.2, 3.2.3). */
+int or_clut_build(const uint32_t* masks, const float* boxes, int64_t nslots,
+                  int R, int K, uint32_t* clut /* [K][W] */,
+                  double* importance /* [K] or NULL */);
+void or_req_luts(const uint32_t* clut, int K, int R, int b,
+                 uint32_t* req /* [ceil(R^3/b)][2^b][8] */);
+int or_encode(const uint32_t* mask, const uint32_t* req, int R, int b);
+int or_encode_naive(const uint32_t* mask, const uint32_t* clut, int K, int R);
+
+/* BVH (binned SAH, binary) + masks + compression. */
+typedef struct OrBvh OrBvh;
+OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins);
+void or_bvh_free(OrBvh* b);
+int64_t or_bvh_num_nodes(const OrBvh* b);
+int or_bvh_max_depth(const OrBvh* b);
+void or_bvh_root(const OrBvh* b, int32_t* child, int32_t* count, float* box6);
+void or_bvh_nodes(const OrBvh* b, int32_t* child, int32_t* count, float* box);
+void or_bvh_perm(const OrBvh* b, int32_t* perm);
+double or_bvh_sah(const OrBvh* b, double ct, double ci);
+double or_scene_eps(const float* tris, int64_t n, double eps_rel);
+int or_bvh_masks(OrBvh* b, const float* tris, int R, int L, double eps);
+void or_bvh_get_masks(const OrBvh* b, uint32_t* masks /* [nn][2][W] */);
+int or_bvh_compress(OrBvh* b, int K, int bits);
+void or_bvh_get_clut(const OrBvh* b, uint32_t* clut, uint8_t* idx);
+
+/* Traversal (Alg. 4 with Alg. 1).  mode 0 = closest hit, 1 = any hit.
+   cull: 0 = plain, 1 = uncompressed masks, 2 = compressed masks.
+   hit_t/hit_id/hit_uv: n, n, 2n; counts: [n][2] {node tests, tri tests};
+   mask_tests: n or NULL.  Returns 0 or a negative error. */
+int or_trace(const OrBvh* b, const float* tris, const float* rays, int64_t n,
+             int mode, int cull, float* hit_t, int32_t* hit_id, float* hit_uv,
+             uint32_t* counts, uint32_t* mask_tests);
+/* The same, for rays [r_begin, r_end) only (threads may split the rays). */
+int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
+                   int64_t r_begin, int64_t r_end, int mode, int cull,
+                   float* hit_t, int32_t* hit_id, float* hit_uv,
+                   uint32_t* counts, uint32_t* mask_tests);
+
+/* Brute force over all ray x triangle pairs, same ray-triangle test.
+   t2: second smallest accepted t (or +inf), for near-tie detection. */
+void or_brute(const float* tris, int64_t ntri, const float* rays, int64_t n,
+              int mode, float* hit_t, int32_t* hit_id, float* t2);
+
+/* Single ray-triangle test and slab test, exposed for pins. */
+int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
+               float* u, float* v);
+int or_slab(const float* ray8, const float* box6, float tcur, float* tn,
+            float* tf);
+int or_cell(float p, float lo, float hi, int R);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

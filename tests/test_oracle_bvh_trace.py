@@ -1,0 +1,245 @@
+"""Pins of the oracle's BVH (binned SAH, Sec. 4) and traversal (Alg. 4 with
+Alg. 1, culling of Sec. 3.1.2).
+
+Independent facts: brute force over all ray x triangle pairs (closest hit),
+closed-form ray-triangle and ray-box results, structural validity of the
+tree, the paper's conservativeness claim (culling never removes a true hit,
+Sec. 3.1.1 / 3.2.3) and its consequence on counts, and dense sampling of the
+clipped segment against the looked-up ray mask.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_08343_gb300 import scenegen as sg
+
+
+def _tri_boxes(tris):
+    v = tris.reshape(-1, 3, 3)
+    return v.min(1), v.max(1)
+
+
+def test_bvh_structure(hair_small):
+    tris, _ = hair_small
+    b = oracle.OracleBVH(tris)
+    child, count, box = b.nodes()
+    perm = b.perm()
+    assert sorted(perm.tolist()) == list(range(len(tris)))
+    assert (count <= 4).all()
+    lo, hi = _tri_boxes(tris)
+    seen = np.zeros(len(tris), int)
+    order = []
+    # pre-order walk: nodes appear as 0, 1, 2, ...
+    stack = [0]
+    while stack:
+        n = stack.pop()
+        order.append(n)
+        for c in (1, 0):
+            if count[n, c] == 0:
+                assert child[n, c] > n
+                stack.append(int(child[n, c]))
+    assert order == list(range(b.num_nodes))
+    for n in range(b.num_nodes):
+        for c in range(2):
+            if count[n, c] > 0:
+                ids = perm[child[n, c]:child[n, c] + count[n, c]]
+                seen[ids] += 1
+                exp_lo, exp_hi = lo[ids].min(0), hi[ids].max(0)
+            else:
+                m = child[n, c]
+                exp_lo = np.minimum(box[m, 0, :3], box[m, 1, :3])
+                exp_hi = np.maximum(box[m, 0, 3:], box[m, 1, 3:])
+            assert np.array_equal(box[n, c, :3], exp_lo) and np.array_equal(box[n, c, 3:], exp_hi)
+    assert (seen == 1).all()
+    # Eq. 1 cost is finite and better than a single big leaf
+    assert b.sah() < len(tris)
+
+
+def test_sah_separates_clusters():
+    # two clusters of 8 triangles far apart: the root split separates them
+    rng = np.random.default_rng(0)
+    a = rng.uniform(0, 1, (8, 9)).astype(np.float32)
+    bb = (rng.uniform(0, 1, (8, 9)) + 100).astype(np.float32)
+    tris = np.vstack([bb[:4], a, bb[4:]])
+    b = oracle.OracleBVH(tris)
+    child, count, box = b.nodes()
+    perm = b.perm()
+
+    def leaves(n, c):
+        if count[n, c] > 0:
+            return list(perm[child[n, c]:child[n, c] + count[n, c]])
+        m = child[n, c]
+        return leaves(m, 0) + leaves(m, 1)
+    left, right = set(leaves(0, 0)), set(leaves(0, 1))
+    cl_a = set(range(4, 12))
+    assert left == cl_a or right == cl_a
+
+
+def test_ray_triangle_closed_form():
+    tri = np.array([0, 0, 0, 1, 0, 0, 0, 1, 0], np.float32)
+    ray = np.array([0.25, 0.25, 1, 0, 0, 0, -1, np.inf], np.float32)
+    ok, t, u, v = oracle.ray_tri(ray, tri)
+    assert ok and t == 1.0 and u == 0.25 and v == 0.25
+    ray2 = np.array([0.75, 0.75, 1, 0, 0, 0, -1, np.inf], np.float32)   # outside
+    assert not oracle.ray_tri(ray2, tri)[0]
+    ray3 = np.array([0.5, 0.5, 1, 0, 0, 0, -1, np.inf], np.float32)     # on edge u+v=1
+    assert oracle.ray_tri(ray3, tri)[0]
+    assert not oracle.ray_tri(ray, tri, tcur=1.0)[0]                     # strict t < tcur
+    ray4 = np.array([0.25, 0.25, 1, 1.0, 0, 0, -1, np.inf], np.float32)  # tmin = 1
+    assert not oracle.ray_tri(ray4, tri)[0]
+
+
+def test_slab_closed_form():
+    box = np.array([1, 1, 1, 2, 2, 2], np.float32)
+    ray = np.array([0, 1.5, 1.5, 0, 1, 0, 0, np.inf], np.float32)
+    ok, tn, tf = oracle.slab(ray, box)
+    assert ok and tn == 1.0 and tf == 2.0
+    ok, tn, tf = oracle.slab(ray, box, tcur=0.5)
+    assert not ok
+    ray_in = np.array([1.5, 1.5, 1.5, 0, 0, 0, 1, np.inf], np.float32)
+    ok, tn, tf = oracle.slab(ray_in, box)
+    assert ok and tn == 0.0 and tf == 0.5
+
+
+def test_cell_index_alg1():
+    # Alg. 1: floor(R/extent * (p - lower)), clamped to [0, R-1]
+    assert oracle.cell(0.0, 0.0, 1.0, 4) == 0
+    assert oracle.cell(0.25, 0.0, 1.0, 4) == 1
+    assert oracle.cell(0.999, 0.0, 1.0, 4) == 3
+    assert oracle.cell(1.0, 0.0, 1.0, 4) == 3      # min(., R-1)
+    assert oracle.cell(-1e-7, 0.0, 1.0, 4) == 0    # clamp at 0
+    assert oracle.cell(5.0, 5.0, 5.0, 6) == 0      # flat box
+
+
+def _check_against_brute(tris, rays, near_tie_rel=1e-6):
+    b = oracle.OracleBVH(tris)
+    o = b.trace(rays, 0, 0)
+    bt, bid, t2 = oracle.brute(tris, rays, 0)
+    assert np.array_equal(o["t"], bt)
+    with np.errstate(invalid="ignore"):
+        tie = (t2 - bt) <= near_tie_rel * np.abs(bt)
+    diff = o["id"] != bid
+    assert not (diff & ~tie).any(), "hit id differs on a ray without a near tie"
+    return b, o
+
+
+def test_plain_traversal_equals_brute_force_hair(hair_small):
+    tris, rays = hair_small
+    _check_against_brute(tris, rays)
+
+
+def test_plain_traversal_equals_brute_force_soup():
+    tris = sg.soup(4096, seed=21)
+    rays = sg.random_rays(4096, seed=22)
+    b, o = _check_against_brute(tris, rays)
+    assert (o["id"] >= 0).sum() > 10
+
+
+def test_plain_traversal_equals_brute_force_ground():
+    tris = sg.hair(64, 16, True, seed=23)
+    rays = sg.pinhole(48, 32)
+    b, o = _check_against_brute(tris, rays)
+    assert (o["id"] == len(tris) - 1).any() or (o["id"] == len(tris) - 2).any()
+
+
+@pytest.mark.parametrize("R,L", [(4, 3), (6, 3), (6, 1), (8, 3)])
+def test_culling_keeps_hits_and_reduces_counts(hair_small, R, L):
+    tris, rays = hair_small
+    b = oracle.OracleBVH(tris).build_masks(R, L=L).compress(256, 8)
+    plain = b.trace(rays, 0, 0)
+    for cull in (1, 2):
+        o = b.trace(rays, 0, cull)
+        assert np.array_equal(o["id"], plain["id"])
+        assert np.array_equal(o["t"], plain["t"])
+        assert (o["counts"] <= plain["counts"]).all()
+    unc = b.trace(rays, 0, 1)
+    assert unc["counts"].sum() < plain["counts"].sum()
+
+
+def test_culling_keeps_hits_soup_bounce_like():
+    tris = sg.soup(8192, seed=31)
+    rays = sg.random_rays(8192, seed=32)
+    b = oracle.OracleBVH(tris).build_masks(6, L=3).compress(256, 8)
+    plain = b.trace(rays, 0, 0)
+    for cull in (1, 2):
+        o = b.trace(rays, 0, cull)
+        assert np.array_equal(o["id"], plain["id"]) and np.array_equal(o["t"], plain["t"])
+        assert (o["counts"] <= plain["counts"]).all()
+
+
+def test_any_hit_consistency():
+    tris = sg.soup(4096, seed=41)
+    rays = sg.random_rays(2048, seed=42)
+    b = oracle.OracleBVH(tris).build_masks(6, L=3)
+    cl = b.trace(rays, 0, 0)
+    for cull in (0, 1):
+        an = b.trace(rays, 1, cull)
+        assert np.array_equal(an["id"] >= 0, cl["id"] >= 0)
+        hit = cl["id"] >= 0
+        assert (an["t"][hit] >= cl["t"][hit]).all()
+        assert (an["counts"] <= cl["counts"]).all() if cull == 0 else True
+
+
+def test_edge_cases():
+    # empty scene
+    rays = sg.pinhole(8, 4)
+    b = oracle.OracleBVH(np.zeros((0, 9), np.float32))
+    o = b.trace(rays)
+    assert (o["id"] == -1).all() and np.isinf(o["t"]).all() and (o["counts"] == 0).all()
+    # one triangle: the root is a leaf (no box test)
+    tri = np.array([[-1, -1, 0, 1, -1, 0, 0, 1, 0]], np.float32)
+    b = oracle.OracleBVH(tri)
+    assert b.num_nodes == 0
+    o = b.trace(rays)
+    assert (o["counts"][:, 0] == 0).all() and (o["counts"][:, 1] == 1).all()
+    assert (o["id"] == 0).any()
+    # identical triangles (no SAH split possible): median split, all found
+    tris = np.tile(tri, (9, 1))
+    b = oracle.OracleBVH(tris)
+    assert b.num_nodes >= 2
+    o = b.trace(rays)
+    bt, bid, _ = oracle.brute(tris, rays)
+    assert np.array_equal(o["t"], bt)
+
+
+def test_ray_mask_covers_sampled_segment():
+    """C9: for random boxes and rays, every densely sampled point of the true
+    clipped segment lies within a small distance of a cell set in the ray
+    mask looked up from the float segment ends (Alg. 1)."""
+    R = 6
+    lut = oracle.raylut(R)
+    bits = np.unpackbits(lut.view(np.uint8), axis=1, bitorder="little")[:, : R ** 3].astype(bool)
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(4000):
+        lo = rng.uniform(-1, 1, 3).astype(np.float32)
+        hi = (lo + rng.uniform(0.01, 1, 3)).astype(np.float32)
+        o = rng.uniform(-2, 2, 3)
+        tgt = lo + rng.uniform(0, 1, 3) * (hi - lo)
+        d = tgt - o
+        d /= np.linalg.norm(d)
+        ray = np.array([*o, 0, *d, np.inf], np.float32)
+        ok, tn, tf = oracle.slab(ray, np.concatenate([lo, hi]))
+        if not ok:
+            continue
+        r32 = ray.astype(np.float32)
+        p0 = r32[:3] + np.float32(tn) * r32[4:7]
+        p1 = r32[:3] + np.float32(tf) * r32[4:7]
+        cb = [oracle.cell(p0[k], lo[k], hi[k], R) for k in range(3)]
+        ce = [oracle.cell(p1[k], lo[k], hi[k], R) for k in range(3)]
+        row = (cb[0] + R * cb[1] + R * R * cb[2]) * R ** 3 + (ce[0] + R * ce[1] + R * R * ce[2])
+        m = bits[row].reshape(R, R, R)  # [z, y, x]
+        od, dd = ray[:3].astype(np.float64), ray[4:7].astype(np.float64)
+        ts = np.linspace(tn, tf, 64)
+        ext = (hi.astype(np.float64) - lo) / R
+        tol = 1e-5 * ext
+        for t in ts:
+            p = od + t * dd
+            rngs = []
+            for k in range(3):
+                a = int(np.clip(np.floor((p[k] - tol[k] - lo[k]) / ext[k]), 0, R - 1))
+                z = int(np.clip(np.floor((p[k] + tol[k] - lo[k]) / ext[k]), 0, R - 1))
+                rngs.append(range(a, z + 1))
+            assert any(m[z, y, x] for x in rngs[0] for y in rngs[1] for z in rngs[2])
+        checked += 1
+    assert checked > 1000
