@@ -1,0 +1,223 @@
+/*
+ * subcull.h — C-ABI of libsubcull: GB300 (sm_103a) BVH traversal with
+ * subspace culling (Yoshimura & Harada, "Subspace Culling for Ray-Box
+ * Intersection", 2023).
+ *
+ * Path: seeded scene -> binned-SAH BVH2 (Sec. 4) -> per-child object masks
+ * (Sec. 3.1.1 voxelization, Sec. 3.2.1 / Alg. 2 hierarchical fill) and,
+ * optionally, their compression (Sec. 3.2.2-3.2.3, Alg. 3) -> a 16-byte
+ * aligned node image in device memory -> batched traversal (Alg. 4): after
+ * each ray-box slab test the clipped segment is turned into a ray mask by
+ * table lookup (Alg. 1) and ANDed with the child's object mask; zero culls
+ * the child.
+ *
+ * Conventions for every entry point:
+ *  - Each call returns an sc_status; on failure sc_last_error() describes
+ *    it (thread-local string, valid until the next call on that thread).
+ *    No C++ exception crosses this boundary.
+ *  - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *    global memory of the current device.  The library never frees memory
+ *    it did not allocate; device buffers (BVH image, rays, hits, counts,
+ *    workspace) belong to the caller and must outlive the work queued on
+ *    the stream.  Host-side handles (sc_bvh, sc_dbvh) are owned by the
+ *    library and released with the matching *_destroy call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device
+ *    work is asynchronous; errors detected on the device (a traversal stack
+ *    overflow) are recorded in the workspace and reported by
+ *    sc_status_poll().
+ *  - There is no CPU fallback: without a usable CUDA device the device
+ *    calls return SC_ERR_CUDA.
+ *
+ * Layouts:
+ *  - triangles: float[n][9] = v0.xyz, v1.xyz, v2.xyz (id = array index).
+ *  - rays: float[n][8] = origin.xyz, tmin, direction.xyz, tmax.
+ *  - hits: sc_hit[n]; a miss is {t = +inf, id = -1, u = v = 0}.
+ *  - counts: uint32[n][2] = {ray-box slab tests, ray-triangle tests}.
+ *  - masks: R^3 bits, bit = x + R*y + R*R*z, little-endian uint32 words,
+ *    W(R) = ceil(R^3/32) words.
+ */
+#ifndef SUBCULL_H
+#define SUBCULL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_ABI_VERSION 1
+
+typedef enum {
+  SC_OK = 0,
+  SC_ERR_ARG = -1,         /* invalid argument (NULL, size, range)          */
+  SC_ERR_CUDA = -2,        /* a CUDA runtime call failed / no device        */
+  SC_ERR_NOMEM = -3,       /* host allocation failed or buffer too small    */
+  SC_ERR_TIMEOUT = -4,     /* a bounded device wait ran out                 */
+  SC_ERR_STACK = -5,       /* device traversal stack overflow (recorded)    */
+  SC_ERR_UNSUPPORTED = -6, /* configuration not supported by this build     */
+  SC_ERR_STATE = -7,       /* object in the wrong state for this call       */
+  SC_ERR_IO = -8           /* file could not be read or written             */
+} sc_status;
+
+/* Message of the last failure on the calling thread ("" after success). */
+const char* sc_last_error(void);
+int sc_abi_version(void);
+
+/* ------------------------------------------------------------ inputs --- */
+/* Seeded synthetic scenes standing in for the paper's hair assets (Sec. 4,
+   Fig. 7: Curly Hair, 12.1M thin tilted triangles). */
+enum { SC_SCENE_HAIR = 0, SC_SCENE_SOUP = 1 };
+typedef struct {
+  int64_t count; /* hair: strands; soup: triangles                        */
+  int segments;  /* hair: segments per strand (each = 2 triangles)        */
+  int ground;    /* hair: append a 2-triangle quad at y = -1.2            */
+} sc_scene_params;
+
+/* Two-call size query: with tris == NULL only *n_tris is set.  tris: host
+   float[cap][9].  SC_ERR_NOMEM if cap < the scene's triangle count. */
+sc_status sc_scene_generate(int kind, const sc_scene_params* p, uint64_t seed,
+                            float* tris, int64_t cap, int64_t* n_tris);
+
+enum { SC_RAYS_PINHOLE = 0, SC_RAYS_RANDOM = 1 };
+typedef struct {
+  int width, height;    /* pinhole: image size (rays in 8x4 tile order)   */
+  int64_t count;        /* random: number of rays                          */
+  uint64_t jitter_seed; /* pinhole: 0 = pixel centres, else sub-pixel jitter */
+} sc_ray_params;
+
+/* Host rays: float[cap][8]; pix (host int32[cap] or NULL) receives the
+   pixel index row*W+col of each pinhole ray.  Two-call size query with
+   rays == NULL. */
+sc_status sc_rays_generate(int kind, const sc_ray_params* p, uint64_t seed,
+                           float* rays, int32_t* pix, int64_t cap,
+                           int64_t* n_rays);
+
+/* ------------------------------------------------------------- build --- */
+typedef struct {
+  int max_leaf;   /* triangles per leaf (<= 4), default 4                   */
+  int bins;       /* SAH bins per axis, default 32                          */
+  int L;          /* mask approximation depth (Sec. 3.2.1), default 3       */
+  int lut_size;   /* compression LUT entries (Sec. 4.4), default 256        */
+  int chunk_bits; /* requirement-LUT chunk b (Sec. 3.2.3), default 8        */
+  double eps_rel; /* voxel dilation / max(1, |scene coord|), default 2^-16  */
+  int threads;    /* host threads, 0 = all                                  */
+} sc_build_opts;
+
+void sc_build_opts_default(sc_build_opts* o);
+
+typedef struct sc_bvh sc_bvh;
+
+/* Builds the BVH2 (binned SAH, Sec. 4), then, when grid_res > 0, the object
+   mask of every child (R = grid_res in {4, 6, 8}; Sec. 3.1.1 SAT
+   voxelization and Alg. 2 from L levels below, Sec. 3.2.1), and, when
+   compress != 0, the compression LUT and each child's LUT index (Sec.
+   3.2.2, requirement LUTs and Alg. 3, Sec. 3.2.3).  tris: host, n <= 2^28.
+   opts NULL = defaults.  *out owns copies of everything it needs. */
+sc_status sc_bvh_build(const float* tris, int64_t n_tris, int grid_res,
+                       int compress, const sc_build_opts* opts, sc_bvh** out);
+void sc_bvh_destroy(sc_bvh* b);
+
+typedef struct {
+  int64_t num_tris, num_nodes;
+  int max_depth;      /* deepest slot below the root (root = 0)           */
+  int grid_res, compress, L, clut_entries;
+  double eps;         /* absolute voxel dilation                           */
+  float root_box[6];
+  double ms_bvh, ms_masks, ms_compress; /* host build times               */
+} sc_bvh_info;
+sc_status sc_bvh_get_info(const sc_bvh* b, sc_bvh_info* info);
+
+/* Copies the host arrays of the built BVH (for checkers).  Any output may
+   be NULL.  root2 = {child, count} of the root slot; child/count: int32
+   [num_nodes][2] (count > 0: leaf of `count` triangles starting at position
+   `child` of perm; count == 0: inner node `child`); box: float
+   [num_nodes][2][6] (lo.xyz, hi.xyz); perm: int32[num_tris] triangle id at
+   each leaf position; masks: uint32[num_nodes][2][W]; clut:
+   uint32[clut_entries][W]; cidx: uint8[num_nodes][2]. */
+sc_status sc_bvh_export(const sc_bvh* b, int32_t* root2, int32_t* child,
+                        int32_t* count, float* box, int32_t* perm,
+                        uint32_t* masks, uint32_t* clut, uint8_t* cidx);
+
+/* The ray-mask table (Sec. 3.1.1): uint32[R^3 * R^3][W], row
+   beg*R^3 + end, cell index x + R*y + R*R*z.  Built here from the 2-D
+   sweep tables of each pair of axes (Helly's theorem on intervals of t). */
+sc_status sc_raylut(int R, uint32_t* lut);
+
+/* ------------------------------------------------------ device image --- */
+enum {
+  SC_LAYOUT_PLAIN = 0, /* 64-B nodes without masks (the unculled baseline) */
+  SC_LAYOUT_MASKED = 1 /* nodes with the masks (or LUT indices) as built   */
+};
+
+/* Bytes of the device image of `b` in `layout` (a multiple of 256). */
+sc_status sc_bvh_device_bytes(const sc_bvh* b, int layout, size_t* nbytes);
+
+typedef struct sc_dbvh sc_dbvh;
+
+/* Packs the image on the host and copies it (cudaMemcpyAsync on `stream`)
+   into d_buf: device memory of >= nbytes bytes, 256-byte aligned, owned by
+   the caller.  The image holds 16-B aligned nodes (fetched with 128-bit
+   loads), 48-B triangles {v0,id}{e1}{e2} in leaf order, the ray-mask
+   tables and the compression LUT.  *out is a host-side view of d_buf;
+   destroying it does not touch d_buf. */
+sc_status sc_bvh_upload(const sc_bvh* b, int layout, void* d_buf, size_t nbytes,
+                        void* stream, sc_dbvh** out);
+void sc_dbvh_destroy(sc_dbvh* d);
+
+/* ------------------------------------------------------------- trace --- */
+typedef struct {
+  float t;
+  int32_t id;
+  float u, v;
+} sc_hit;
+
+enum { SC_CLOSEST = 0, SC_ANY = 1 };
+
+enum { SC_LUT_AUTO = 0, SC_LUT_GLOBAL = 1, SC_LUT_SHARED = 2 };
+
+typedef struct {
+  int block;         /* threads per block: 0 (= 128) or 128               */
+  int blocks_per_sm; /* persistent blocks per SM, 0 = occupancy maximum    */
+  int lut_mode;      /* ray-mask lookup: SC_LUT_GLOBAL = full table through
+                        L1/L2; SC_LUT_SHARED = factored tables in shared
+                        memory; SC_LUT_AUTO picks per resolution          */
+} sc_trace_opts;
+
+/* Workspace bytes sc_trace needs (ray counter and device status word). */
+size_t sc_trace_workspace_bytes(void);
+
+/*
+ * Traces n rays (Alg. 4).  d_rays: device float[n][8]; d_hits: device
+ * sc_hit[n]; d_counts: device uint32[n][2] or NULL.  mode SC_CLOSEST or
+ * SC_ANY.  cull != 0 applies subspace culling (Sec. 3.1.2): the image must
+ * be SC_LAYOUT_MASKED with grid_res > 0; cull == 0 runs the plain traversal
+ * on any layout.  d_work: device workspace of >= sc_trace_workspace_bytes()
+ * bytes (reset by this call).  Asynchronous on `stream`.
+ */
+sc_status sc_trace(const sc_dbvh* d, const float* d_rays, int64_t n,
+                   sc_hit* d_hits, uint32_t* d_counts, int mode, int cull,
+                   const sc_trace_opts* opts, void* d_work, size_t work_bytes,
+                   void* stream);
+
+/*
+ * End-to-end form of sc_trace for host data: copies h_rays (host float
+ * [n][8], ideally pinned) to d_rays_buf, traces, and copies the hits (and
+ * counts if h_counts != NULL) back to h_hits / h_counts, all on `stream`,
+ * then synchronizes it.  d_rays_buf, d_hits_buf, d_counts_buf: device
+ * scratch of n*32, n*16 and n*8 bytes owned by the caller.
+ */
+sc_status sc_trace_host(const sc_dbvh* d, const float* h_rays, int64_t n,
+                        sc_hit* h_hits, uint32_t* h_counts, int mode, int cull,
+                        const sc_trace_opts* opts, float* d_rays_buf,
+                        sc_hit* d_hits_buf, uint32_t* d_counts_buf,
+                        void* d_work, size_t work_bytes, void* stream);
+
+/* Synchronizes `stream` and returns the device status word of d_work
+   (SC_OK, or SC_ERR_STACK if a ray's stack overflowed). */
+sc_status sc_status_poll(const void* d_work, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -15,13 +15,14 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_SO = os.path.join(_HERE, "_build", platform.machine() or "unknown", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import shutil
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
@@ -18,7 +19,8 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-OUT = os.path.join(PKG, "_build")
+# per-architecture output: objects built on one host type never mix with another's
+OUT = os.path.join(PKG, "_build", platform.machine() or "unknown")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -1,0 +1,221 @@
+// trace_api.cu — device entry points of the C-ABI: image upload, trace
+// launches, the end-to-end host-buffer form and the status poll.
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "host/internal.h"
+#include "trace_kernel.cuh"
+
+namespace sct {
+KernelFn get_kernel_plain(int mode);
+KernelFn get_kernel_r4(int cull, int mode, int lutv);
+KernelFn get_kernel_r6(int cull, int mode, int lutv);
+KernelFn get_kernel_r8(int cull, int mode, int lutv);
+}  // namespace sct
+
+using namespace sc;
+
+namespace {
+
+constexpr int kBlock = 128;
+constexpr size_t kWorkBytes = 256;
+
+#define CUDA_OK(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      fail(SC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+struct DevInfo {
+  int sms = 0;
+};
+
+DevInfo device_info() {
+  int dev = 0;
+  CUDA_OK(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::vector<DevInfo> cache;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)cache.size() <= dev) cache.resize(dev + 1);
+  if (cache[dev].sms == 0) {
+    int sms = 0;
+    CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cache[dev].sms = sms;
+  }
+  return cache[dev];
+}
+
+sct::KernelFn pick_kernel(const sc_dbvh* d, int mode, int cull, int lutv) {
+  if (!cull) return sct::get_kernel_plain(mode);
+  int c = d->lay.compress ? 2 : 1;
+  switch (d->lay.R) {
+    case 4: return sct::get_kernel_r4(c, mode, lutv);
+    case 6: return sct::get_kernel_r6(c, mode, lutv);
+    case 8: return sct::get_kernel_r8(c, mode, lutv);
+  }
+  fail(SC_ERR_UNSUPPORTED, "no kernel for R = %d", d->lay.R);
+}
+
+void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hits,
+                  uint32_t* d_counts, int mode, int cull, const sc_trace_opts* opts,
+                  void* d_work, size_t work_bytes, cudaStream_t st) {
+  if (!d) fail(SC_ERR_ARG, "sc_trace: NULL device BVH");
+  if (n < 0 || n > (int64_t)0x7FFFFF00) fail(SC_ERR_ARG, "sc_trace: n out of range");
+  if (n > 0 && (!d_rays || !d_hits)) fail(SC_ERR_ARG, "sc_trace: NULL rays or hits");
+  if (!d_work || work_bytes < kWorkBytes) fail(SC_ERR_ARG, "sc_trace: workspace too small");
+  if ((reinterpret_cast<uintptr_t>(d_rays) & 15) || (reinterpret_cast<uintptr_t>(d_hits) & 15) ||
+      (reinterpret_cast<uintptr_t>(d_counts) & 7) || (reinterpret_cast<uintptr_t>(d_work) & 15))
+    fail(SC_ERR_ARG, "sc_trace: rays/hits/workspace must be 16-byte aligned, counts 8-byte");
+  if (mode != SC_CLOSEST && mode != SC_ANY) fail(SC_ERR_ARG, "sc_trace: bad mode %d", mode);
+  if (cull && (d->lay.layout != SC_LAYOUT_MASKED || d->lay.R == 0))
+    fail(SC_ERR_STATE, "sc_trace: culling needs an image uploaded with SC_LAYOUT_MASKED");
+  if (d->stack_need > sct::kStack)
+    fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
+         sct::kStack);
+  sc_trace_opts o{0, 0, SC_LUT_AUTO};
+  if (opts) o = *opts;
+  if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
+  int lutv = (o.lut_mode == SC_LUT_SHARED) ? 1 : 0;
+  if (o.lut_mode == SC_LUT_AUTO) lutv = (d->lay.R == 4) ? 0 : 1;
+  sct::KernelFn k = pick_kernel(d, mode, cull ? 1 : 0, lutv);
+  CUDA_OK(cudaMemsetAsync(d_work, 0, kWorkBytes, st));
+  if (n == 0) return;
+  DevInfo di = device_info();
+  int per_sm = o.blocks_per_sm;
+  if (per_sm <= 0) {
+    CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, kBlock, 0));
+    if (per_sm < 1) per_sm = 1;
+  }
+  int64_t need = (n + kBlock - 1) / kBlock;
+  int64_t grid = (int64_t)di.sms * per_sm;
+  if (grid > need) grid = need;
+  sct::Params p;
+  const uint8_t* base = d->base;
+  p.nodes = reinterpret_cast<const float4*>(base + d->lay.off_nodes);
+  p.node_f4 = d->lay.node_bytes / 16;
+  p.tris = reinterpret_cast<const float4*>(base + d->lay.off_tris);
+  p.lut = d->lay.R ? reinterpret_cast<const uint4*>(base + d->lay.off_lut) : nullptr;
+  p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
+  p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
+  p.rays = reinterpret_cast<const float4*>(d_rays);
+  p.hits = reinterpret_cast<sct::Hit*>(d_hits);
+  p.counts = reinterpret_cast<uint2*>(d_counts);
+  p.work = reinterpret_cast<unsigned*>(d_work);
+  p.n = n;
+  p.num_nodes = d->nn;
+  p.num_tris = d->ntri;
+  p.root_slot = d->root_slot;
+  p.has_root = d->has_root;
+  k<<<(unsigned)grid, kBlock, 0, st>>>(p);
+  CUDA_OK(cudaGetLastError());
+}
+
+}  // namespace
+
+#define SC_TRY \
+  try {        \
+    clear_error();
+#define SC_CATCH                              \
+  }                                           \
+  catch (const Error& e) {                    \
+    set_error("%s", e.msg.c_str());           \
+    return e.code;                            \
+  }                                           \
+  catch (const std::bad_alloc&) {             \
+    set_error("host allocation failed");      \
+    return SC_ERR_NOMEM;                      \
+  }                                           \
+  catch (...) {                               \
+    set_error("unexpected internal error");   \
+    return SC_ERR_STATE;                      \
+  }
+
+extern "C" {
+
+sc_status sc_bvh_upload(const sc_bvh* h, int layout, void* d_buf, size_t nbytes, void* stream,
+                        sc_dbvh** out) {
+  SC_TRY
+  if (!h || !d_buf || !out) fail(SC_ERR_ARG, "sc_bvh_upload: NULL argument");
+  *out = nullptr;
+  if (reinterpret_cast<uintptr_t>(d_buf) & 255) fail(SC_ERR_ARG, "d_buf must be 256-byte aligned");
+  const Bvh& b = h->b;
+  ImageLayout L = image_layout(b, layout);
+  if (nbytes < L.total) fail(SC_ERR_NOMEM, "image needs %zu bytes, buffer has %zu", L.total, nbytes);
+  std::vector<uint8_t> img;
+  pack_image(b, L, img);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_OK(cudaMemcpyAsync(d_buf, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  sc_dbvh* d = new sc_dbvh();
+  d->base = reinterpret_cast<const uint8_t*>(d_buf);
+  d->lay = L;
+  d->ntri = b.ntri;
+  d->nn = b.nn;
+  d->root_slot = root_slot_word(b);
+  d->has_root = b.ntri > 0 ? 1 : 0;
+  d->stack_need = b.max_depth + 1;
+  *out = d;
+  return SC_OK;
+  SC_CATCH
+}
+
+void sc_dbvh_destroy(sc_dbvh* d) { delete d; }
+
+size_t sc_trace_workspace_bytes(void) { return kWorkBytes; }
+
+sc_status sc_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hits,
+                   uint32_t* d_counts, int mode, int cull, const sc_trace_opts* opts, void* d_work,
+                   size_t work_bytes, void* stream) {
+  SC_TRY
+  launch_trace(d, d_rays, n, d_hits, d_counts, mode, cull, opts, d_work, work_bytes,
+               reinterpret_cast<cudaStream_t>(stream));
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_trace_host(const sc_dbvh* d, const float* h_rays, int64_t n, sc_hit* h_hits,
+                        uint32_t* h_counts, int mode, int cull, const sc_trace_opts* opts,
+                        float* d_rays_buf, sc_hit* d_hits_buf, uint32_t* d_counts_buf,
+                        void* d_work, size_t work_bytes, void* stream) {
+  SC_TRY
+  if (n > 0 && (!h_rays || !h_hits || !d_rays_buf || !d_hits_buf))
+    fail(SC_ERR_ARG, "sc_trace_host: NULL buffer");
+  if (h_counts && !d_counts_buf) fail(SC_ERR_ARG, "sc_trace_host: counts need d_counts_buf");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n > 0)
+    CUDA_OK(cudaMemcpyAsync(d_rays_buf, h_rays, (size_t)n * 32, cudaMemcpyHostToDevice, st));
+  launch_trace(d, d_rays_buf, n, d_hits_buf, h_counts ? d_counts_buf : nullptr, mode, cull, opts,
+               d_work, work_bytes, st);
+  if (n > 0) {
+    CUDA_OK(cudaMemcpyAsync(h_hits, d_hits_buf, (size_t)n * 16, cudaMemcpyDeviceToHost, st));
+    if (h_counts)
+      CUDA_OK(cudaMemcpyAsync(h_counts, d_counts_buf, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_OK(cudaStreamSynchronize(st));
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_status_poll(const void* d_work, void* stream) {
+  SC_TRY
+  if (!d_work) fail(SC_ERR_ARG, "sc_status_poll: NULL workspace");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned word[2] = {0, 0};
+  CUDA_OK(cudaMemcpyAsync(word, d_work, sizeof(word), cudaMemcpyDeviceToHost, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  if (word[1] & sct::ST_STACK) {
+    set_error("device: a traversal stack overflowed");
+    return SC_ERR_STACK;
+  }
+  if (word[1] & sct::ST_BAD_NODE) {
+    set_error("device: the BVH image holds an invalid child reference");
+    return SC_ERR_STATE;
+  }
+  return SC_OK;
+  SC_CATCH
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// layout.cpp — the device image of a BVH (node records, triangles, tables).
+//
+// Nodes are child pairs of 64 bytes (four 16-byte vectors, one 128-bit load
+// each); in the masked uncompressed layout the two R^3-bit object masks
+// follow in the same record (mask_stride bytes each, zero padded), so a node
+// is 80 / 128 / 192 bytes at R = 4 / 6 / 8 and stays 16-byte aligned.  In the
+// compressed layout the 1-byte LUT index of each child sits in the fourth
+// vector (Sec. 3.2.4: the index replaces the mask), so the node stays 64 B.
+// Triangles are 48 bytes in leaf order: {v0, id}, {e1 = v1 - v0}, {e2 =
+// v2 - v0}.  Every region starts on a 256-byte boundary.
+#include <cstring>
+
+#include "internal.h"
+
+namespace sc {
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+uint32_t root_slot_word(const Bvh& b) {
+  if (b.root_count > 0)
+    return kLeafBit | ((uint32_t)(b.root_count - 1) << 28) | (uint32_t)b.root_child;
+  return 0u;
+}
+
+static uint32_t slot_word(int32_t child, int32_t count) {
+  if (count > 0) return kLeafBit | ((uint32_t)(count - 1) << 28) | (uint32_t)child;
+  return (uint32_t)child;
+}
+
+ImageLayout image_layout(const Bvh& b, int layout) {
+  ImageLayout L;
+  L.layout = layout;
+  if (layout == SC_LAYOUT_MASKED) {
+    if (b.R <= 0) fail(SC_ERR_STATE, "masked layout requested for a BVH built without masks");
+    L.R = b.R;
+    L.W = mask_words(b.R);
+    L.mstride = mask_stride(b.R);
+    L.compress = b.compress;
+    L.K = b.K;
+    L.node_bytes = b.compress ? 64 : 64 + 2 * L.mstride;
+  } else if (layout != SC_LAYOUT_PLAIN) {
+    fail(SC_ERR_ARG, "unknown layout %d", layout);
+  }
+  size_t off = 256;
+  L.off_nodes = off;
+  off = align256(off + (size_t)b.nn * L.node_bytes);
+  L.off_tris = off;
+  off = align256(off + (size_t)b.ntri * 48);
+  if (L.R > 0) {
+    size_t R3 = (size_t)L.R * L.R * L.R;
+    L.off_lut = off;
+    off = align256(off + R3 * R3 * L.mstride);
+    L.off_pair = off;
+    off = align256(off + R3 * L.R * 8);
+    if (L.compress) {
+      L.off_clut = off;
+      off = align256(off + (size_t)256 * L.mstride);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
+  img.assign(L.total, 0);
+  uint8_t* base = img.data();
+  // header: a few words for debugging tools
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(base);
+  hdr[0] = 0x4C554353u;  // "SCUL"
+  hdr[1] = SC_ABI_VERSION;
+  hdr[2] = (uint32_t)L.layout;
+  hdr[3] = (uint32_t)L.R;
+  hdr[4] = (uint32_t)b.nn;
+  hdr[5] = (uint32_t)b.ntri;
+  hdr[6] = root_slot_word(b);
+  parallel_for(b.nn, resolve_threads(0), 16384, [&](int64_t n) {
+    uint8_t* rec = base + L.off_nodes + (size_t)n * L.node_bytes;
+    float* f = reinterpret_cast<float*>(rec);
+    const float* b0 = &b.box[12 * n];
+    const float* b1 = b0 + 6;
+    f[0] = b0[0]; f[1] = b0[1]; f[2] = b0[2]; f[3] = b0[3];
+    f[4] = b0[4]; f[5] = b0[5]; f[6] = b1[0]; f[7] = b1[1];
+    f[8] = b1[2]; f[9] = b1[3]; f[10] = b1[4]; f[11] = b1[5];
+    uint32_t* u = reinterpret_cast<uint32_t*>(rec + 48);
+    u[0] = slot_word(b.child[2 * n], b.count[2 * n]);
+    u[1] = slot_word(b.child[2 * n + 1], b.count[2 * n + 1]);
+    u[2] = (L.R > 0 && L.compress) ? b.cidx[2 * n] : 0u;
+    u[3] = (L.R > 0 && L.compress) ? b.cidx[2 * n + 1] : 0u;
+    if (L.R > 0 && !L.compress) {
+      for (int c = 0; c < 2; ++c)
+        std::memcpy(rec + 64 + c * L.mstride, &b.masks[((size_t)n * 2 + c) * L.W], 4 * L.W);
+    }
+  });
+  parallel_for(b.ntri, resolve_threads(0), 65536, [&](int64_t k) {
+    float* f = reinterpret_cast<float*>(base + L.off_tris + (size_t)k * 48);
+    int32_t id = b.perm[k];
+    const float* t = &b.tris[9 * (size_t)id];
+    f[0] = t[0]; f[1] = t[1]; f[2] = t[2];
+    std::memcpy(&f[3], &id, 4);
+    f[4] = t[3] - t[0]; f[5] = t[4] - t[1]; f[6] = t[5] - t[2]; f[7] = 0.0f;
+    f[8] = t[6] - t[0]; f[9] = t[7] - t[1]; f[10] = t[8] - t[2]; f[11] = 0.0f;
+  });
+  if (L.R > 0) {
+    const int R = L.R;
+    const size_t R3 = (size_t)R * R * R;
+    std::vector<uint32_t> lut(R3 * R3 * L.W);
+    raylut_full(R, lut.data());
+    for (size_t e = 0; e < R3 * R3; ++e)
+      std::memcpy(base + L.off_lut + e * L.mstride, &lut[e * L.W], 4 * L.W);
+    std::vector<uint64_t> P;
+    raylut_pair2d(R, P);
+    std::memcpy(base + L.off_pair, P.data(), 8 * P.size());
+    if (L.compress) {
+      for (int j = 0; j < b.K; ++j)
+        std::memcpy(base + L.off_clut + (size_t)j * L.mstride, &b.clut[(size_t)j * L.W], 4 * L.W);
+    }
+  }
+}
+
+}  // namespace sc

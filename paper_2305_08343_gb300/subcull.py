@@ -1,0 +1,319 @@
+"""ctypes binding of libsubcull (include/subcull.h), same names as the C-ABI.
+
+Argument marshalling only: every step of the path runs in the native
+library (host builders in C++, traversal in CUDA for sm_103a).  PyTorch is
+used for device memory and streams.  If the library cannot be built or
+loaded this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import _build
+
+SC_OK = 0
+SC_SCENE_HAIR, SC_SCENE_SOUP = 0, 1
+SC_RAYS_PINHOLE, SC_RAYS_RANDOM = 0, 1
+SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED = 0, 1
+SC_CLOSEST, SC_ANY = 0, 1
+SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED = 0, 1, 2
+STATUS_NAMES = {0: "SC_OK", -1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_NOMEM",
+                -4: "SC_ERR_TIMEOUT", -5: "SC_ERR_STACK", -6: "SC_ERR_UNSUPPORTED",
+                -7: "SC_ERR_STATE", -8: "SC_ERR_IO"}
+
+
+class SubcullError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sc_scene_params(C.Structure):
+    _fields_ = [("count", C.c_int64), ("segments", C.c_int), ("ground", C.c_int)]
+
+
+class sc_ray_params(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("count", C.c_int64),
+                ("jitter_seed", C.c_uint64)]
+
+
+class sc_build_opts(C.Structure):
+    _fields_ = [("max_leaf", C.c_int), ("bins", C.c_int), ("L", C.c_int),
+                ("lut_size", C.c_int), ("chunk_bits", C.c_int), ("eps_rel", C.c_double),
+                ("threads", C.c_int)]
+
+
+class sc_bvh_info(C.Structure):
+    _fields_ = [("num_tris", C.c_int64), ("num_nodes", C.c_int64), ("max_depth", C.c_int),
+                ("grid_res", C.c_int), ("compress", C.c_int), ("L", C.c_int),
+                ("clut_entries", C.c_int), ("eps", C.c_double), ("root_box", C.c_float * 6),
+                ("ms_bvh", C.c_double), ("ms_masks", C.c_double), ("ms_compress", C.c_double)]
+
+
+class sc_trace_opts(C.Structure):
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Loads (building if needed) libsubcull.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        L = C.CDLL(_build.build_product())
+        P, vp = C.POINTER, C.c_void_p
+        i64, u64, f32p, i32p, u32p, u8p = (C.c_int64, C.c_uint64, P(C.c_float), P(C.c_int32),
+                                           P(C.c_uint32), P(C.c_uint8))
+        sigs = {
+            "sc_last_error": (C.c_char_p, []),
+            "sc_abi_version": (C.c_int, []),
+            "sc_scene_generate": (C.c_int, [C.c_int, P(sc_scene_params), u64, f32p, i64, P(i64)]),
+            "sc_rays_generate": (C.c_int, [C.c_int, P(sc_ray_params), u64, f32p, i32p, i64,
+                                           P(i64)]),
+            "sc_build_opts_default": (None, [P(sc_build_opts)]),
+            "sc_bvh_build": (C.c_int, [f32p, i64, C.c_int, C.c_int, P(sc_build_opts), P(vp)]),
+            "sc_bvh_destroy": (None, [vp]),
+            "sc_bvh_get_info": (C.c_int, [vp, P(sc_bvh_info)]),
+            "sc_bvh_export": (C.c_int, [vp, i32p, i32p, i32p, f32p, i32p, u32p, u32p, u8p]),
+            "sc_raylut": (C.c_int, [C.c_int, u32p]),
+            "sc_bvh_device_bytes": (C.c_int, [vp, C.c_int, P(C.c_size_t)]),
+            "sc_bvh_upload": (C.c_int, [vp, C.c_int, vp, C.c_size_t, vp, P(vp)]),
+            "sc_dbvh_destroy": (None, [vp]),
+            "sc_trace_workspace_bytes": (C.c_size_t, []),
+            "sc_trace": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, C.c_int, P(sc_trace_opts), vp,
+                                   C.c_size_t, vp]),
+            "sc_trace_host": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, C.c_int,
+                                        P(sc_trace_opts), vp, vp, vp, vp, C.c_size_t, vp]),
+            "sc_status_poll": (C.c_int, [vp, vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(code: int):
+    if code != SC_OK:
+        msg = lib().sc_last_error()
+        raise SubcullError(code, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray, t):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+# ------------------------------------------------------------------ inputs --
+
+def sc_scene_generate(kind: int, count: int, segments: int = 16, ground: int = 0,
+                      seed: int = 1) -> np.ndarray:
+    p = sc_scene_params(count, segments, ground)
+    n = C.c_int64()
+    _check(lib().sc_scene_generate(kind, C.byref(p), seed, None, 0, C.byref(n)))
+    out = np.empty((n.value, 9), np.float32)
+    _check(lib().sc_scene_generate(kind, C.byref(p), seed, _ptr(out, C.c_float), n.value,
+                                   C.byref(n)))
+    return out
+
+
+def sc_rays_generate(kind: int, width: int = 0, height: int = 0, count: int = 0,
+                     jitter_seed: int = 0, seed: int = 0, with_pixels: bool = False):
+    p = sc_ray_params(width, height, count, jitter_seed)
+    n = C.c_int64()
+    _check(lib().sc_rays_generate(kind, C.byref(p), seed, None, None, 0, C.byref(n)))
+    out = np.empty((n.value, 8), np.float32)
+    pix = np.empty(n.value, np.int32)
+    _check(lib().sc_rays_generate(kind, C.byref(p), seed, _ptr(out, C.c_float),
+                                  _ptr(pix, C.c_int32), n.value, C.byref(n)))
+    return (out, pix) if with_pixels else out
+
+
+# ------------------------------------------------------------------- build --
+
+def sc_build_opts_default() -> sc_build_opts:
+    o = sc_build_opts()
+    lib().sc_build_opts_default(C.byref(o))
+    return o
+
+
+class Bvh:
+    """Host BVH handle (sc_bvh*)."""
+
+    def __init__(self, handle, ntri):
+        self._h = handle
+        self.ntri = ntri
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().sc_bvh_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> sc_bvh_info:
+        i = sc_bvh_info()
+        _check(lib().sc_bvh_get_info(self._h, C.byref(i)))
+        return i
+
+    def export(self):
+        """Host arrays: dict(root, child, count, box, perm, masks?, clut?, cidx?)."""
+        i = self.info()
+        nn = i.num_nodes
+        W = (i.grid_res ** 3 + 31) // 32 if i.grid_res else 0
+        root = np.zeros(2, np.int32)
+        child = np.zeros((max(nn, 1), 2), np.int32)
+        count = np.zeros((max(nn, 1), 2), np.int32)
+        box = np.zeros((max(nn, 1), 2, 6), np.float32)
+        perm = np.zeros(max(i.num_tris, 1), np.int32)
+        masks = np.zeros((max(nn, 1), 2, max(W, 1)), np.uint32) if W else None
+        clut = np.zeros((max(i.clut_entries, 1), max(W, 1)), np.uint32) if i.compress else None
+        cidx = np.zeros((max(nn, 1), 2), np.uint8) if i.compress else None
+        _check(lib().sc_bvh_export(
+            self._h, _ptr(root, C.c_int32), _ptr(child, C.c_int32), _ptr(count, C.c_int32),
+            _ptr(box, C.c_float), _ptr(perm, C.c_int32),
+            _ptr(masks, C.c_uint32) if masks is not None else None,
+            _ptr(clut, C.c_uint32) if clut is not None else None,
+            _ptr(cidx, C.c_uint8) if cidx is not None else None))
+        out = dict(root=root, child=child[:nn], count=count[:nn], box=box[:nn],
+                   perm=perm[: i.num_tris])
+        if masks is not None:
+            out["masks"] = masks[:nn]
+        if clut is not None:
+            out["clut"] = clut[: i.clut_entries]
+            out["cidx"] = cidx[:nn]
+        return out
+
+
+def sc_bvh_build(tris: np.ndarray, grid_res: int = 6, compress: int = 0,
+                 opts: sc_build_opts | None = None, **kw) -> Bvh:
+    t = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    o = opts if opts is not None else sc_build_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(lib().sc_bvh_build(_ptr(t, C.c_float) if len(t) else None, t.shape[0], grid_res,
+                              compress, C.byref(o), C.byref(h)))
+    return Bvh(h, t.shape[0])
+
+
+def sc_raylut(R: int) -> np.ndarray:
+    R3 = R ** 3
+    out = np.zeros((R3 * R3, (R3 + 31) // 32), np.uint32)
+    _check(lib().sc_raylut(R, _ptr(out, C.c_uint32)))
+    return out
+
+
+def sc_bvh_device_bytes(bvh: Bvh, layout: int) -> int:
+    n = C.c_size_t()
+    _check(lib().sc_bvh_device_bytes(bvh.handle, layout, C.byref(n)))
+    return n.value
+
+
+def sc_trace_workspace_bytes() -> int:
+    return int(lib().sc_trace_workspace_bytes())
+
+
+# ------------------------------------------------------------ device side --
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class DeviceBVH:
+    """A BVH image in a torch-owned device buffer plus its sc_dbvh view."""
+
+    def __init__(self, bvh: Bvh, layout: int, device="cuda", stream=None):
+        import torch
+        nbytes = sc_bvh_device_bytes(bvh, layout)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.layout = layout
+        self.nbytes = nbytes
+        h = C.c_void_p()
+        _check(lib().sc_bvh_upload(bvh.handle, layout, C.c_void_p(self.buf.data_ptr()), nbytes,
+                                   _stream_ptr(stream), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().sc_dbvh_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def sc_bvh_upload(bvh: Bvh, layout: int, stream=None) -> DeviceBVH:
+    return DeviceBVH(bvh, layout, stream=stream)
+
+
+def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO):
+    return sc_trace_opts(block, blocks_per_sm, lut_mode)
+
+
+def sc_trace(dbvh: DeviceBVH, rays, hits, counts, mode: int, cull: int, work,
+             opts: sc_trace_opts | None = None, stream=None):
+    """All tensors on the device: rays float32[n,8], hits float32[n,4] (16 B
+    per hit: t, id bits, u, v), counts int32[n,2] or None, work uint8[>=256]."""
+    n = rays.shape[0]
+    o = opts or _opts()
+    _check(lib().sc_trace(dbvh.handle, C.c_void_p(rays.data_ptr()), n,
+                          C.c_void_p(hits.data_ptr()),
+                          C.c_void_p(counts.data_ptr()) if counts is not None else None,
+                          mode, cull, C.byref(o), C.c_void_p(work.data_ptr()), work.numel(),
+                          _stream_ptr(stream)))
+
+
+def sc_trace_host(dbvh: DeviceBVH, h_rays, h_hits, h_counts, mode: int, cull: int,
+                  d_rays, d_hits, d_counts, work, opts=None, stream=None):
+    """Host tensors (pinned) in, host tensors out; device scratch given."""
+    n = h_rays.shape[0]
+    o = opts or _opts()
+    _check(lib().sc_trace_host(dbvh.handle, C.c_void_p(h_rays.data_ptr()), n,
+                               C.c_void_p(h_hits.data_ptr()),
+                               C.c_void_p(h_counts.data_ptr()) if h_counts is not None else None,
+                               mode, cull, C.byref(o), C.c_void_p(d_rays.data_ptr()),
+                               C.c_void_p(d_hits.data_ptr()),
+                               C.c_void_p(d_counts.data_ptr()) if d_counts is not None else None,
+                               C.c_void_p(work.data_ptr()), work.numel(), _stream_ptr(stream)))
+
+
+def sc_status_poll(work, stream=None):
+    _check(lib().sc_status_poll(C.c_void_p(work.data_ptr()), _stream_ptr(stream)))
+
+
+# --------------------------------------------------------------- helpers --
+
+def trace(dbvh: DeviceBVH, rays, mode: int = SC_CLOSEST, cull: int = 1, with_counts=True,
+          opts=None, stream=None):
+    """Convenience: allocates outputs and workspace with torch, traces, and
+    returns (hits float32[n,4], counts int32[n,2] | None)."""
+    import torch
+    n = rays.shape[0]
+    dev = rays.device
+    hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    counts = torch.empty((n, 2), dtype=torch.int32, device=dev) if with_counts else None
+    work = torch.empty(sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
+    sc_trace(dbvh, rays, hits, counts, mode, cull, work, opts, stream)
+    sc_status_poll(work, stream)
+    return hits, counts
+
+
+def split_hits(hits):
+    """(t, id, u, v) numpy views of a float32[n,4] hit array."""
+    h = hits.cpu().numpy() if hasattr(hits, "cpu") else np.asarray(hits)
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    return h[:, 0], h[:, 1].view(np.int32), h[:, 2], h[:, 3]
