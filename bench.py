@@ -218,7 +218,7 @@ def run_gpu(args):
     bvh = sc.sc_bvh_build(tris, R, comp)
     build_s = time.perf_counter() - t0
     info = bvh.info()
-    d_masked = sc.DeviceBVH(bvh, sc.SC_LAYOUT_MASKED)
+    d_masked = sc.DeviceBVH(bvh, args.layout)
     d_plain = sc.DeviceBVH(bvh, sc.SC_LAYOUT_PLAIN)
     n = rays_np.shape[0]
     rays = torch.from_numpy(rays_np).to(dev)
@@ -229,13 +229,14 @@ def run_gpu(args):
     work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
-    opts = sc._opts(lut_mode=args.lut)
+    opts = sc._opts(lut_mode=args.lut, refill=args.refill)
 
     # reference pass with counts (untimed): identical hits and tests per ray
     sc.sc_trace(d_masked, rays, hits, counts, 0, 1, work, opts)
     sc.sc_trace(d_plain, rays, hits_plain, counts_plain, 0, 0, work, opts)
     sc.sc_status_poll(work)
-    same = bool(torch.equal(hits, hits_plain))
+    # compare the 16-byte records bitwise (a miss stores id -1, a NaN pattern as float)
+    same = bool(torch.equal(hits.view(torch.int32), hits_plain.view(torch.int32)))
     cnt_c = counts.double().mean(0).tolist()
     cnt_p = counts_plain.double().mean(0).tolist()
     le = bool((counts <= counts_plain).all().item())
@@ -289,7 +290,8 @@ def run_gpu(args):
            "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 16}
 
     # roofline of the traversal kernel: algorithmic bytes per ray
-    node_bytes = (64 if comp else 64 + 2 * {4: 8, 6: 32, 8: 64}[R])
+    node_bytes = ((96 if args.layout == 1 else 64) +
+                  (0 if comp else 2 * {4: 8, 6: 32, 8: 64}[R]))
     b_ray = 32 + 16 + (cnt_c[0] / 2.0) * node_bytes + cnt_c[1] * 48
     per_launch_bytes = b_ray * n
     avg_ms = float(np.mean(ms_cull))
@@ -322,6 +324,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "rays_per_step": n,
                    "grid_res": R, "compressed": bool(comp), "L": 3, "lut_mode": args.lut,
+                   "layout": args.layout, "refill": args.refill,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "plain_mrays_s": plain_value, "speedup_vs_plain": value / world / plain_value,
@@ -351,6 +354,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hair1m", choices=sorted(WORKLOADS))
     ap.add_argument("--lut", type=int, default=0, help="0 auto, 1 global table, 2 shared")
+    ap.add_argument("--layout", type=int, default=1, help="1 masked (scales stored), 2 compact")
+    ap.add_argument("--refill", type=int, default=0, help="idle lanes before a warp refills")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

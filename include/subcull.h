@@ -146,8 +146,14 @@ sc_status sc_raylut(int R, uint32_t* lut);
 
 /* ------------------------------------------------------ device image --- */
 enum {
-  SC_LAYOUT_PLAIN = 0, /* 64-B nodes without masks (the unculled baseline) */
-  SC_LAYOUT_MASKED = 1 /* nodes with the masks (or LUT indices) as built   */
+  SC_LAYOUT_PLAIN = 0,         /* 64-B nodes without masks (unculled baseline) */
+  SC_LAYOUT_MASKED = 1,        /* masks (or LUT indices) plus each child's
+                                  Alg. 1 scales R/extent precomputed in the
+                                  node: 96 B compressed, 64+32+2*mask bytes
+                                  uncompressed                             */
+  SC_LAYOUT_MASKED_COMPACT = 2 /* masks (or LUT indices) only; the scales are
+                                  divided on the fly: 64 B compressed,
+                                  64+2*mask bytes uncompressed               */
 };
 
 /* Bytes of the device image of `b` in `layout` (a multiple of 256). */
@@ -182,6 +188,8 @@ typedef struct {
   int lut_mode;      /* ray-mask lookup: SC_LUT_GLOBAL = full table through
                         L1/L2; SC_LUT_SHARED = factored tables in shared
                         memory; SC_LUT_AUTO picks per resolution          */
+  int refill;        /* a warp fetches new rays once this many of its lanes
+                        are idle (1..32), 0 = default                     */
 } sc_trace_opts;
 
 /* Workspace bytes sc_trace needs (ray counter and device status word). */
@@ -191,7 +199,7 @@ size_t sc_trace_workspace_bytes(void);
  * Traces n rays (Alg. 4).  d_rays: device float[n][8]; d_hits: device
  * sc_hit[n]; d_counts: device uint32[n][2] or NULL.  mode SC_CLOSEST or
  * SC_ANY.  cull != 0 applies subspace culling (Sec. 3.1.2): the image must
- * be SC_LAYOUT_MASKED with grid_res > 0; cull == 0 runs the plain traversal
+ * be SC_LAYOUT_MASKED[_COMPACT] with grid_res > 0; cull == 0 runs the plain traversal
  * on any layout.  d_work: device workspace of >= sc_trace_workspace_bytes()
  * bytes (reset by this call).  Asynchronous on `stream`.
  */

@@ -10,17 +10,18 @@
 
 namespace sct {
 KernelFn get_kernel_plain(int mode);
-KernelFn get_kernel_r4(int cull, int mode, int lutv);
-KernelFn get_kernel_r6(int cull, int mode, int lutv);
-KernelFn get_kernel_r8(int cull, int mode, int lutv);
+KernelFn get_kernel_r4(int cull, int mode, int lutv, int scales);
+KernelFn get_kernel_r6(int cull, int mode, int lutv, int scales);
+KernelFn get_kernel_r8(int cull, int mode, int lutv, int scales);
 }  // namespace sct
 
 using namespace sc;
 
 namespace {
 
-constexpr int kBlock = 128;
+constexpr int kBlock = sct::kBlock;
 constexpr size_t kWorkBytes = 256;
+constexpr int kDefaultRefill = 8;
 
 #define CUDA_OK(call)                                                        \
   do {                                                                       \
@@ -51,10 +52,11 @@ DevInfo device_info() {
 sct::KernelFn pick_kernel(const sc_dbvh* d, int mode, int cull, int lutv) {
   if (!cull) return sct::get_kernel_plain(mode);
   int c = d->lay.compress ? 2 : 1;
+  const int sc = d->lay.scales;
   switch (d->lay.R) {
-    case 4: return sct::get_kernel_r4(c, mode, lutv);
-    case 6: return sct::get_kernel_r6(c, mode, lutv);
-    case 8: return sct::get_kernel_r8(c, mode, lutv);
+    case 4: return sct::get_kernel_r4(c, mode, lutv, sc);
+    case 6: return sct::get_kernel_r6(c, mode, lutv, sc);
+    case 8: return sct::get_kernel_r8(c, mode, lutv, sc);
   }
   fail(SC_ERR_UNSUPPORTED, "no kernel for R = %d", d->lay.R);
 }
@@ -70,16 +72,17 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
       (reinterpret_cast<uintptr_t>(d_counts) & 7) || (reinterpret_cast<uintptr_t>(d_work) & 15))
     fail(SC_ERR_ARG, "sc_trace: rays/hits/workspace must be 16-byte aligned, counts 8-byte");
   if (mode != SC_CLOSEST && mode != SC_ANY) fail(SC_ERR_ARG, "sc_trace: bad mode %d", mode);
-  if (cull && (d->lay.layout != SC_LAYOUT_MASKED || d->lay.R == 0))
-    fail(SC_ERR_STATE, "sc_trace: culling needs an image uploaded with SC_LAYOUT_MASKED");
+  if (cull && d->lay.R == 0)
+    fail(SC_ERR_STATE, "sc_trace: culling needs an image uploaded with a masked layout");
   if (d->stack_need > sct::kStack)
     fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
          sct::kStack);
-  sc_trace_opts o{0, 0, SC_LUT_AUTO};
+  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0};
   if (opts) o = *opts;
   if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
-  int lutv = (o.lut_mode == SC_LUT_SHARED) ? 1 : 0;
-  if (o.lut_mode == SC_LUT_AUTO) lutv = (d->lay.R == 4) ? 0 : 1;
+  if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
+  if (o.lut_mode < SC_LUT_AUTO || o.lut_mode > SC_LUT_SHARED) fail(SC_ERR_ARG, "bad lut_mode");
+  const int lutv = (o.lut_mode == SC_LUT_SHARED) ? 1 : 0;
   sct::KernelFn k = pick_kernel(d, mode, cull ? 1 : 0, lutv);
   CUDA_OK(cudaMemsetAsync(d_work, 0, kWorkBytes, st));
   if (n == 0) return;
@@ -96,12 +99,13 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   const uint8_t* base = d->base;
   p.nodes = reinterpret_cast<const float4*>(base + d->lay.off_nodes);
   p.node_f4 = d->lay.node_bytes / 16;
+  p.mask_off_f4 = d->lay.mask_off / 16;
   p.tris = reinterpret_cast<const float4*>(base + d->lay.off_tris);
   p.lut = d->lay.R ? reinterpret_cast<const uint4*>(base + d->lay.off_lut) : nullptr;
   p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
   p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
   p.rays = reinterpret_cast<const float4*>(d_rays);
-  p.hits = reinterpret_cast<sct::Hit*>(d_hits);
+  p.hits = reinterpret_cast<float4*>(d_hits);
   p.counts = reinterpret_cast<uint2*>(d_counts);
   p.work = reinterpret_cast<unsigned*>(d_work);
   p.n = n;
@@ -109,6 +113,7 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   p.num_tris = d->ntri;
   p.root_slot = d->root_slot;
   p.has_root = d->has_root;
+  p.refill = o.refill ? o.refill : kDefaultRefill;
   k<<<(unsigned)grid, kBlock, 0, st>>>(p);
   CUDA_OK(cudaGetLastError());
 }

@@ -1,22 +1,26 @@
 // trace_kernel.cuh — persistent-warp BVH2 traversal with subspace culling
-// for sm_103a (templates; instantiated by trace_r*.cu).
+// for sm_103a (templates; instantiated by trace_r*.cu / trace_plain.cu).
 //
-// One thread traces one ray at a time; each warp takes batches of 32 ray
-// indices from a global counter (one atomicAdd per batch, broadcast by
-// shuffle) until the rays run out.  Per visited inner node the thread loads
-// the 64-byte child-pair record with four 128-bit read-only loads, runs the
-// two slab tests, and for every child the ray's box segment hits it runs the
-// culling test of Sec. 3.1.2: the clipped segment ends p0 = o + tn*d and
-// p1 = o + tf*d are quantised to cells (Alg. 1), the ray mask for the
-// (begin, end) cell pair is looked up, and the child survives iff the AND
-// with its object mask is non-zero (Alg. 4).  Traversal order: if both
-// children survive the nearer (smaller tn) is visited next and the other is
-// pushed with its tn; a popped entry with tn > current closest t is dropped.
+// Work distribution: each warp keeps 32 rays in flight.  Whenever enough of
+// its lanes have finished (ballot), the warp takes that many new ray indices
+// from a global counter with one atomicAdd and hands them to the idle lanes,
+// so lanes do not wait for the slowest ray of a batch.
 //
-// Every floating-point test op is written with explicit round-to-nearest
-// intrinsics (__fadd_rn, __fmul_rn, ...), so no multiply-add contraction can
-// change a decision: the op sequence is the canonical one a CPU reference
-// performs in IEEE float.
+// Per step a lane either visits one inner node or tests the triangles of one
+// leaf.  An inner-node visit loads the child-pair record with 128-bit
+// read-only loads, runs the two slab tests and, for every child whose box the
+// ray segment hits, the culling test of Sec. 3.1.2: the clipped segment ends
+// p0 = o + tn*d and p1 = o + tf*d are quantised to cells (Alg. 1), the ray
+// mask of the (begin, end) cell pair is looked up, and the child survives
+// iff the AND with its object mask is non-zero (Alg. 4).  Order: if both
+// children survive, the one with the smaller entry distance is visited next
+// and the other is pushed with its entry distance; a popped entry whose
+// distance exceeds the current closest hit is dropped.
+//
+// Every floating-point test op is an explicit round-to-nearest intrinsic
+// (__fadd_rn, __fmul_rn, ...), so no multiply-add contraction can change a
+// decision: the op sequence is the canonical one a CPU reference performs in
+// IEEE float, which makes hits and per-ray test counts reproducible.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,26 +29,23 @@
 namespace sct {
 
 constexpr uint32_t kLeaf = 0x80000000u;
+constexpr uint32_t kMetaFull = 0x100u;   // child mask is all ones: the test cannot cull
 constexpr float kRobust = 1.00000047683715820f;  // 1 + 4 * 2^-23 >= 1 + 2 gamma_3
 constexpr int kStack = 64;
+constexpr int kBlock = 128;
 
 enum { ST_OK = 0, ST_STACK = 1, ST_BAD_NODE = 2 };
-
-struct __align__(16) Hit {
-  float t;
-  int id;
-  float u, v;
-};
 
 struct Params {
   const float4* nodes;
   int node_f4;              // node stride in float4 units
+  int mask_off_f4;          // first object mask inside a record (float4 units)
   const float4* tris;       // 3 float4 per triangle
-  const uint4* lut;         // full ray-mask table (mask stride bytes per entry)
+  const uint4* lut;         // full ray-mask table (mask-stride bytes per entry)
   const uint2* pair;        // factored 2-D table, R^4 x 64 bits
   const uint4* clut;        // compression LUT
   const float4* rays;       // 2 float4 per ray
-  Hit* hits;
+  float4* hits;             // {t, id bits, u, v}
   uint2* counts;            // or nullptr
   unsigned* work;           // [0] ray counter, [1] status
   long long n;
@@ -52,6 +53,7 @@ struct Params {
   long long num_tris;
   uint32_t root_slot;
   int has_root;
+  int refill;               // refill when at least this many lanes are idle
 };
 
 // A slot may be followed only if it stays inside the image and, for an
@@ -66,42 +68,41 @@ __device__ __forceinline__ bool slot_ok(uint32_t s, long long parent, const Para
   return (long long)s > parent && (long long)s < p.num_nodes;
 }
 
-__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
-__device__ __forceinline__ uint4 ldg4u(const uint4* p) { return __ldg(p); }
-
-// Alg. 1 on one axis, with a clamp at 0 and a floor on the extent.
-template <int R>
-__device__ __forceinline__ int cell_of(float p, float lo, float hi) {
-  const float ext = __fsub_rn(hi, lo);
-  const float s = __fdiv_rn((float)R, fmaxf(ext, 1e-30f));
-  float q = __fmul_rn(__fsub_rn(p, lo), s);
-  q = fminf(fmaxf(q, -1.0f), (float)R);
-  int i = (int)floorf(q);
-  i = i < 0 ? 0 : i;
-  return i > R - 1 ? R - 1 : i;
-}
-
-// Object mask words of child c of a node record (uncompressed layout).
 template <int R>
 struct MaskTraits {
   static constexpr int kStrideBytes = (R == 4) ? 8 : (R == 6 ? 32 : 64);
   static constexpr int kQuads = kStrideBytes / 16;  // 0 for R = 4
-  static constexpr int kR3 = R * R * R;
+  static constexpr int kWords = (R * R * R + 31) / 32;
 };
 
-// AND of two masks in global memory (16-B aligned, zero padded) != 0.
+// Alg. 1 on one axis: min(floor(s * (p - lo)), R-1), clamped at 0, with
+// s = R / max(extent, 1e-30).  The saturating float-to-int conversion
+// (cvt.rmi) gives the same index as clamping q to [-1, R] first.
+template <int R>
+__device__ __forceinline__ int cell_q(float p, float lo, float s) {
+  const float q = __fmul_rn(__fsub_rn(p, lo), s);
+  const int i = __float2int_rd(q);
+  return min(max(i, 0), R - 1);
+}
+
+template <int R>
+__device__ __forceinline__ float scale_of(float lo, float hi) {
+  return __fdiv_rn((float)R, fmaxf(__fsub_rn(hi, lo), 1e-30f));
+}
+
+// AND of two masks in global memory (aligned, zero padded) != 0.
 template <int R>
 __device__ __forceinline__ bool masks_overlap(const void* a, const void* b) {
   if constexpr (R == 4) {
-    uint2 x = __ldg(reinterpret_cast<const uint2*>(a));
-    uint2 y = __ldg(reinterpret_cast<const uint2*>(b));
+    const uint2 x = __ldg(reinterpret_cast<const uint2*>(a));
+    const uint2 y = __ldg(reinterpret_cast<const uint2*>(b));
     return ((x.x & y.x) | (x.y & y.y)) != 0u;
   } else {
     unsigned acc = 0;
 #pragma unroll
     for (int q = 0; q < MaskTraits<R>::kQuads; ++q) {
-      uint4 x = ldg4u(reinterpret_cast<const uint4*>(a) + q);
-      uint4 y = ldg4u(reinterpret_cast<const uint4*>(b) + q);
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(a) + q);
+      const uint4 y = __ldg(reinterpret_cast<const uint4*>(b) + q);
       acc |= (x.x & y.x) | (x.y & y.y) | (x.z & y.z) | (x.w & y.w);
     }
     return acc != 0u;
@@ -123,7 +124,7 @@ struct SmemLut {
 template <int R>
 __device__ void stage_lut(SmemLut<R>& s, const uint2* pair) {
   for (int i = threadIdx.x; i < R * R * R * R; i += blockDim.x) {
-    uint2 v = pair[i];
+    const uint2 v = pair[i];
     s.P[i] = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
   }
   for (int m = threadIdx.x; m < (1 << R); m += blockDim.x) {
@@ -137,17 +138,20 @@ __device__ void stage_lut(SmemLut<R>& s, const uint2* pair) {
   }
 }
 
-// R^2-bit slice z of a dense R^3-bit mask held in W words.
+// R^2-bit slice z of a dense R^3-bit mask held in W (+1 zero) words.
 template <int R>
 __device__ __forceinline__ unsigned long long mask_slice(const uint32_t* w, int z) {
   constexpr int S = R * R;
+  constexpr int W = MaskTraits<R>::kWords;
   const int bit = S * z;
   const int wi = bit >> 5, sh = bit & 31;
-  unsigned long long lo = w[wi];
-  unsigned long long hi = (wi + 1 < (R * R * R + 31) / 32) ? w[wi + 1] : 0u;
-  unsigned long long hh = (wi + 2 < (R * R * R + 31) / 32) ? w[wi + 2] : 0u;
+  const unsigned long long lo = w[wi];
+  const unsigned long long hi = (wi + 1 < W) ? w[wi + 1] : 0u;
   unsigned long long v = (lo | (hi << 32)) >> sh;
-  if (sh + S > 64) v |= hh << (64 - sh);
+  if (sh + S > 64) {
+    const unsigned long long hh = (wi + 2 < W) ? w[wi + 2] : 0u;
+    v |= hh << (64 - sh);
+  }
   if constexpr (S == 64) {
     return v;
   } else {
@@ -157,7 +161,24 @@ __device__ __forceinline__ unsigned long long mask_slice(const uint32_t* w, int 
 
 template <int R>
 __device__ __forceinline__ bool overlap_factored(const SmemLut<R>& s, const int* cb,
-                                                 const int* ce, const uint32_t* obj) {
+                                                 const int* ce, const uint8_t* objp) {
+  constexpr int W = MaskTraits<R>::kWords;
+  uint32_t w[W + 1];
+  if constexpr (R == 4) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(objp));
+    w[0] = q.x;
+    w[1] = q.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < MaskTraits<R>::kQuads; ++i) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(objp) + i);
+      if (4 * i + 0 < W) w[4 * i + 0] = q.x;
+      if (4 * i + 1 < W) w[4 * i + 1] = q.y;
+      if (4 * i + 2 < W) w[4 * i + 2] = q.z;
+      if (4 * i + 3 < W) w[4 * i + 3] = q.w;
+    }
+  }
+  w[W] = 0u;
   auto pidx = [](int ba, int bb, int ea, int eb) { return ((ba * R + bb) * R + ea) * R + eb; };
   const unsigned long long pxy = s.P[pidx(cb[0], cb[1], ce[0], ce[1])];
   const unsigned long long pyz = s.P[pidx(cb[1], cb[2], ce[1], ce[2])];
@@ -165,211 +186,245 @@ __device__ __forceinline__ bool overlap_factored(const SmemLut<R>& s, const int*
   const int z0 = min(cb[2], ce[2]), z1 = max(cb[2], ce[2]);
   constexpr unsigned long long m = (1ULL << R) - 1ULL;
   for (int z = z0; z <= z1; ++z) {
-    unsigned long long ray = pxy & s.rows[(pyz >> (R * z)) & m] & s.cols[(pxz >> (R * z)) & m];
-    if (ray & mask_slice<R>(obj, z)) return true;
+    const unsigned long long ray =
+        pxy & s.rows[(pyz >> (R * z)) & m] & s.cols[(pxz >> (R * z)) & m];
+    if (ray & mask_slice<R>(w, z)) return true;
   }
   return false;
 }
 
-// LUT variants: 0 = full table in global memory (one 8/32/64-byte entry per
-// lookup, served by L1/L2), 1 = factored tables in shared memory.
-template <int R, int CULL, int MODE, int LUTV>
-__global__ void __launch_bounds__(128) trace_kernel(Params p) {
-  constexpr int R3 = (R > 0) ? R * R * R : 1;
-  constexpr int W = (R3 + 31) / 32;
-  constexpr int MB = (R > 0) ? MaskTraits<(R > 0 ? R : 4)>::kStrideBytes : 8;
-  __shared__ SmemLut<(R > 0 ? R : 4)> slut;
+// Moeller-Trumbore, canonical op order.  Returns true and t, u, v on accept.
+__device__ __forceinline__ bool tri_test(const float4 A, const float4 E1, const float4 E2,
+                                         float ox, float oy, float oz, float dx, float dy,
+                                         float dz, float tmin, float tcur, float& t, float& u,
+                                         float& v) {
+  const float px = __fsub_rn(__fmul_rn(dy, E2.z), __fmul_rn(dz, E2.y));
+  const float py = __fsub_rn(__fmul_rn(dz, E2.x), __fmul_rn(dx, E2.z));
+  const float pz = __fsub_rn(__fmul_rn(dx, E2.y), __fmul_rn(dy, E2.x));
+  const float det =
+      __fadd_rn(__fadd_rn(__fmul_rn(E1.x, px), __fmul_rn(E1.y, py)), __fmul_rn(E1.z, pz));
+  if (det == 0.0f) return false;
+  const float inv = __fdiv_rn(1.0f, det);
+  const float sx = __fsub_rn(ox, A.x), sy = __fsub_rn(oy, A.y), sz = __fsub_rn(oz, A.z);
+  u = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(sx, px), __fmul_rn(sy, py)), __fmul_rn(sz, pz)),
+                inv);
+  if (u < 0.0f || u > 1.0f) return false;
+  const float qx = __fsub_rn(__fmul_rn(sy, E1.z), __fmul_rn(sz, E1.y));
+  const float qy = __fsub_rn(__fmul_rn(sz, E1.x), __fmul_rn(sx, E1.z));
+  const float qz = __fsub_rn(__fmul_rn(sx, E1.y), __fmul_rn(sy, E1.x));
+  v = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, qx), __fmul_rn(dy, qy)), __fmul_rn(dz, qz)),
+                inv);
+  if (v < 0.0f || __fadd_rn(u, v) > 1.0f) return false;
+  t = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(E2.x, qx), __fmul_rn(E2.y, qy)), __fmul_rn(E2.z, qz)),
+                inv);
+  return t > tmin && t < tcur;
+}
+
+struct RayState {
+  float ox, oy, oz, dx, dy, dz, ix, iy, iz, tmin, tcur;
+  float ht, hu, hv;
+  int hid;
+  unsigned ntest, ttest;
+  int sp;
+  uint32_t cur;
+  bool have;  // `cur` is the next slot to visit (else pop)
+};
+
+// CULL: 0 plain, 1 uncompressed masks, 2 compressed masks.  MODE: 0 closest,
+// 1 any.  LUTV: 0 full table in global memory (one entry per lookup through
+// L1/L2), 1 factored tables in shared memory.  SCALES: 1 = the per-child
+// Alg. 1 scales R/extent are precomputed in the node record, 0 = divided.
+template <int R, int CULL, int MODE, int LUTV, int SCALES>
+__global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
+  constexpr int RR = (R > 0 ? R : 4);
+  constexpr int R3 = RR * RR * RR;
+  constexpr int MB = MaskTraits<RR>::kStrideBytes;
+  __shared__ SmemLut<RR> slut;
   if constexpr (CULL != 0 && LUTV == 1) {
-    stage_lut<R>(slut, p.pair);
+    stage_lut<RR>(slut, p.pair);
     __syncthreads();
   }
-  const int lane = threadIdx.x & 31;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint2 stack[kStack];
+  RayState s;
+  s.have = false;
+  long long rid = -1;
+  bool active = false;
+  bool exhausted = false;
   for (;;) {
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&p.work[0], 32u);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if ((long long)base >= p.n) break;
-    const long long rid = (long long)base + lane;
-    if (rid < p.n) {
-      const float4 ra = __ldg(&p.rays[2 * rid]);
-      const float4 rb = __ldg(&p.rays[2 * rid + 1]);
-      const float ox = ra.x, oy = ra.y, oz = ra.z, tmin = ra.w;
-      const float dx = rb.x, dy = rb.y, dz = rb.z;
-      const float ix = __fdiv_rn(1.0f, dx), iy = __fdiv_rn(1.0f, dy), iz = __fdiv_rn(1.0f, dz);
-      float tcur = rb.w;
-      float ht = __int_as_float(0x7f800000), hu = 0.0f, hv = 0.0f;
-      int hid = -1;
-      unsigned ntest = 0, ttest = 0;
-      uint2 stack[kStack];
-      int sp = 0;
-      uint32_t cur = p.root_slot;
-      bool have = p.has_root != 0;
-      bool done = false;
-      while (!done) {
-        if (have) {
-          if (cur & kLeaf) {
-            const int first = (int)(cur & 0x0FFFFFFFu);
-            const int cnt = (int)((cur >> 28) & 7u) + 1;
-            for (int i = 0; i < cnt; ++i) {
-              const float4* tp = p.tris + 3 * (long long)(first + i);
-              const float4 A = ldg4(tp), E1 = ldg4(tp + 1), E2 = ldg4(tp + 2);
-              ++ttest;
-              // Moeller-Trumbore, canonical op order
-              const float px = __fsub_rn(__fmul_rn(dy, E2.z), __fmul_rn(dz, E2.y));
-              const float py = __fsub_rn(__fmul_rn(dz, E2.x), __fmul_rn(dx, E2.z));
-              const float pz = __fsub_rn(__fmul_rn(dx, E2.y), __fmul_rn(dy, E2.x));
-              const float det = __fadd_rn(__fadd_rn(__fmul_rn(E1.x, px), __fmul_rn(E1.y, py)),
-                                          __fmul_rn(E1.z, pz));
-              if (det == 0.0f) continue;
-              const float inv = __fdiv_rn(1.0f, det);
-              const float sx = __fsub_rn(ox, A.x), sy = __fsub_rn(oy, A.y), sz = __fsub_rn(oz, A.z);
-              const float u = __fmul_rn(
-                  __fadd_rn(__fadd_rn(__fmul_rn(sx, px), __fmul_rn(sy, py)), __fmul_rn(sz, pz)), inv);
-              if (u < 0.0f || u > 1.0f) continue;
-              const float qx = __fsub_rn(__fmul_rn(sy, E1.z), __fmul_rn(sz, E1.y));
-              const float qy = __fsub_rn(__fmul_rn(sz, E1.x), __fmul_rn(sx, E1.z));
-              const float qz = __fsub_rn(__fmul_rn(sx, E1.y), __fmul_rn(sy, E1.x));
-              const float v = __fmul_rn(
-                  __fadd_rn(__fadd_rn(__fmul_rn(dx, qx), __fmul_rn(dy, qy)), __fmul_rn(dz, qz)), inv);
-              if (v < 0.0f || __fadd_rn(u, v) > 1.0f) continue;
-              const float t = __fmul_rn(
-                  __fadd_rn(__fadd_rn(__fmul_rn(E2.x, qx), __fmul_rn(E2.y, qy)), __fmul_rn(E2.z, qz)),
-                  inv);
-              if (!(t > tmin && t < tcur)) continue;
-              ht = t;
-              hu = u;
-              hv = v;
-              hid = __float_as_int(A.w);
-              if (MODE == 1) {
-                done = true;
-                break;
-              }
-              tcur = t;
+    // ---- refill idle lanes with new rays
+    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (idle != 0u && !exhausted && (__popc(idle) >= p.refill || idle == 0xffffffffu)) {
+      const int leader = __ffs(idle) - 1;
+      unsigned base = 0;
+      if ((int)lane == leader) base = atomicAdd(&p.work[0], (unsigned)__popc(idle));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if ((long long)base + __popc(idle) >= p.n) exhausted = true;
+      if (!active) {
+        const long long r = (long long)base + __popc(idle & lt_mask);
+        if (r < p.n) {
+          rid = r;
+          active = true;
+          const float4 ra = __ldg(&p.rays[2 * r]);
+          const float4 rb = __ldg(&p.rays[2 * r + 1]);
+          s.ox = ra.x; s.oy = ra.y; s.oz = ra.z; s.tmin = ra.w;
+          s.dx = rb.x; s.dy = rb.y; s.dz = rb.z; s.tcur = rb.w;
+          s.ix = __fdiv_rn(1.0f, s.dx);
+          s.iy = __fdiv_rn(1.0f, s.dy);
+          s.iz = __fdiv_rn(1.0f, s.dz);
+          s.ht = __int_as_float(0x7f800000);
+          s.hu = 0.0f;
+          s.hv = 0.0f;
+          s.hid = -1;
+          s.ntest = 0;
+          s.ttest = 0;
+          s.sp = 0;
+          s.cur = p.root_slot;
+          s.have = p.has_root != 0;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (!active) continue;
+    // ---- one traversal step
+    bool done = false;
+    if (s.have) {
+      if (s.cur & kLeaf) {
+        const int first = (int)(s.cur & 0x0FFFFFFFu);
+        const int cnt = (int)((s.cur >> 28) & 7u) + 1;
+        for (int i = 0; i < cnt; ++i) {
+          const float4* tp = p.tris + 3 * (long long)(first + i);
+          const float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
+          ++s.ttest;
+          float t, u, v;
+          if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
+            s.ht = t;
+            s.hu = u;
+            s.hv = v;
+            s.hid = __float_as_int(A.w);
+            if (MODE == 1) {
+              done = true;
+              break;
             }
-            have = false;
-            continue;
+            s.tcur = t;
           }
-          const float4* nd = p.nodes + (long long)cur * p.node_f4;
-          const float4 f0 = ldg4(nd), f1 = ldg4(nd + 1), f2 = ldg4(nd + 2);
-          const uint4 f3 = ldg4u(reinterpret_cast<const uint4*>(nd + 3));
-          ntest += 2;
-          const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-          const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-          const float o[3] = {ox, oy, oz}, inv[3] = {ix, iy, iz};
-          float tn[2], tf[2];
-          bool hit[2];
+        }
+        s.have = false;
+      } else {
+        const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
+        const float4 f0 = __ldg(nd), f1 = __ldg(nd + 1), f2 = __ldg(nd + 2);
+        const uint4 f3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+        s.ntest += 2;
+        const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
+        const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
+        const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+        float tn[2], tf[2];
+        bool hit[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float* lo = c ? lo1 : lo0;
+          const float* hi = c ? hi1 : hi0;
+          float a0[3], a1[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
+            a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
+          }
+          tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
+                        fmaxf(fminf(a0[2], a1[2]), s.tmin));
+          tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
+                        fminf(fmaxf(a0[2], a1[2]), s.tcur));
+          hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
+        }
+        if constexpr (CULL != 0) {
+          const float d[3] = {s.dx, s.dy, s.dz};
+          float sc[2][3];
+          if constexpr (SCALES) {
+            const float4 f4 = __ldg(nd + 4), f5 = __ldg(nd + 5);
+            sc[0][0] = f4.x; sc[0][1] = f4.y; sc[0][2] = f4.z;
+            sc[1][0] = f4.w; sc[1][1] = f5.x; sc[1][2] = f5.y;
+          }
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
+            const unsigned meta = c ? f3.w : f3.z;
+            if (!hit[c] || (meta & kMetaFull)) continue;
             const float* lo = c ? lo1 : lo0;
             const float* hi = c ? hi1 : hi0;
-            float a0[3], a1[3];
+            int cb[3], ce[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-              a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
-              a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
-            }
-            tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
-                          fmaxf(fminf(a0[2], a1[2]), tmin));
-            tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
-                          fminf(fmaxf(a0[2], a1[2]), tcur));
-            hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
-          }
-          if constexpr (CULL != 0) {
-            const float d[3] = {dx, dy, dz};
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              if (!hit[c]) continue;
-              const float* lo = c ? lo1 : lo0;
-              const float* hi = c ? hi1 : hi0;
-              int cb[3], ce[3];
-#pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                const float p0 = __fadd_rn(o[k], __fmul_rn(tn[c], d[k]));
-                const float p1 = __fadd_rn(o[k], __fmul_rn(tf[c], d[k]));
-                cb[k] = cell_of<R>(p0, lo[k], hi[k]);
-                ce[k] = cell_of<R>(p1, lo[k], hi[k]);
-              }
-              const uint8_t* obj;
-              if constexpr (CULL == 1) {
-                obj = reinterpret_cast<const uint8_t*>(nd + 4) + c * MB;
+              float sk;
+              if constexpr (SCALES) {
+                sk = sc[c][k];
               } else {
-                const unsigned idx = (c ? f3.w : f3.z) & 0xFFu;
-                obj = reinterpret_cast<const uint8_t*>(p.clut) + idx * MB;
+                sk = scale_of<RR>(lo[k], hi[k]);
               }
-              if constexpr (LUTV == 0) {
-                const int beg = cb[0] + R * cb[1] + R * R * cb[2];
-                const int end = ce[0] + R * ce[1] + R * R * ce[2];
-                const uint8_t* rm = reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
-                hit[c] = masks_overlap<R>(rm, obj);
-              } else {
-                uint32_t w[W + 1];
-                if constexpr (R == 4) {
-                  const uint2 q = __ldg(reinterpret_cast<const uint2*>(obj));
-                  w[0] = q.x;
-                  w[1] = q.y;
-                } else {
-#pragma unroll
-                  for (int i = 0; i < MB / 16; ++i) {
-                    const uint4 q = ldg4u(reinterpret_cast<const uint4*>(obj) + i);
-                    if (4 * i + 0 < W) w[4 * i + 0] = q.x;
-                    if (4 * i + 1 < W) w[4 * i + 1] = q.y;
-                    if (4 * i + 2 < W) w[4 * i + 2] = q.z;
-                    if (4 * i + 3 < W) w[4 * i + 3] = q.w;
-                  }
-                }
-                w[W] = 0u;
-                hit[c] = overlap_factored<R>(slut, cb, ce, w);
-              }
+              const float p0 = __fadd_rn(o[k], __fmul_rn(tn[c], d[k]));
+              const float p1 = __fadd_rn(o[k], __fmul_rn(tf[c], d[k]));
+              cb[k] = cell_q<RR>(p0, lo[k], sk);
+              ce[k] = cell_q<RR>(p1, lo[k], sk);
             }
-          }
-          const uint32_t s0 = f3.x, s1 = f3.y;
-          if ((hit[0] && !slot_ok(s0, (long long)cur, p)) ||
-              (hit[1] && !slot_ok(s1, (long long)cur, p))) {
-            atomicOr(&p.work[1], (unsigned)ST_BAD_NODE);
-            done = true;
-            continue;
-          }
-          if (hit[0] && hit[1]) {
-            const int nr = tn[1] < tn[0] ? 1 : 0;
-            if (sp < kStack) {
-              stack[sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
-              ++sp;
+            const uint8_t* obj;
+            if constexpr (CULL == 1) {
+              obj = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB;
             } else {
-              atomicOr(&p.work[1], (unsigned)ST_STACK);
-              done = true;
+              obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
             }
-            cur = nr ? s1 : s0;
-          } else if (hit[0]) {
-            cur = s0;
-          } else if (hit[1]) {
-            cur = s1;
-          } else {
-            have = false;
+            if constexpr (LUTV == 0) {
+              const int beg = cb[0] + RR * cb[1] + RR * RR * cb[2];
+              const int end = ce[0] + RR * ce[1] + RR * RR * ce[2];
+              const uint8_t* rm =
+                  reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
+              hit[c] = masks_overlap<RR>(rm, obj);
+            } else {
+              hit[c] = overlap_factored<RR>(slut, cb, ce, obj);
+            }
           }
-          continue;
         }
-        while (sp > 0) {
-          --sp;
-          if (__uint_as_float(stack[sp].y) > tcur) continue;
-          cur = stack[sp].x;
-          have = true;
-          break;
+        const uint32_t s0 = f3.x, s1 = f3.y;
+        if ((hit[0] && !slot_ok(s0, (long long)s.cur, p)) ||
+            (hit[1] && !slot_ok(s1, (long long)s.cur, p))) {
+          atomicOr(&p.work[1], (unsigned)ST_BAD_NODE);
+          done = true;
+        } else if (hit[0] && hit[1]) {
+          const int nr = tn[1] < tn[0] ? 1 : 0;
+          if (s.sp < kStack) {
+            stack[s.sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
+            ++s.sp;
+            s.cur = nr ? s1 : s0;
+          } else {
+            atomicOr(&p.work[1], (unsigned)ST_STACK);
+            done = true;
+          }
+        } else if (hit[0]) {
+          s.cur = s0;
+        } else if (hit[1]) {
+          s.cur = s1;
+        } else {
+          s.have = false;
         }
-        if (!have) done = true;
       }
-      Hit h;
-      h.t = ht;
-      h.id = hid;
-      h.u = hu;
-      h.v = hv;
-      reinterpret_cast<float4*>(p.hits)[rid] =
-          make_float4(h.t, __int_as_float(h.id), h.u, h.v);
-      if (p.counts) p.counts[rid] = make_uint2(ntest, ttest);
+    }
+    if (!done && !s.have) {
+      while (s.sp > 0) {
+        --s.sp;
+        if (__uint_as_float(stack[s.sp].y) > s.tcur) continue;
+        s.cur = stack[s.sp].x;
+        s.have = true;
+        break;
+      }
+      if (!s.have) done = true;
+    }
+    if (done) {
+      p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+      if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
+      active = false;
+      s.have = false;
     }
   }
 }
 
-// Launch entry for one variant.
 typedef void (*KernelFn)(Params);
 
 }  // namespace sct

@@ -5,7 +5,7 @@
 namespace sct {
 
 KernelFn get_kernel_plain(int mode) {
-  return mode ? trace_kernel<0, 0, 1, 0> : trace_kernel<0, 0, 0, 0>;
+  return mode ? trace_kernel<0, 0, 1, 0, 0> : trace_kernel<0, 0, 0, 0, 0>;
 }
 
 }  // namespace sct

@@ -83,14 +83,20 @@ void raylut_full(int R, uint32_t* out);
 //   f2 = {lo1.z, hi1.x, hi1.y, hi1.z}  f3 = {slot0, slot1, meta0, meta1}
 // slot: inner -> child node index (>= 0); leaf -> 0x80000000 |
 // (count-1) << 28 | first triangle position.  meta: compression LUT index.
-// Masked, uncompressed: the two masks follow at +64 and +64+mask_stride.
+// meta bit 8: the child's (decoded) mask is all ones, so its culling test
+// cannot remove it.  SC_LAYOUT_MASKED stores the scales R / max(extent,
+// 1e-30) of both children at +64 (six floats, two pad); the two uncompressed
+// masks follow at mask_off and mask_off + mask_stride.
 constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr uint32_t kMetaFull = 0x100u;
 constexpr int kMaxLeafTris = 8;
 constexpr int64_t kMaxTris = int64_t(1) << 28;
 
 struct ImageLayout {
   int layout = 0;          // SC_LAYOUT_*
   int R = 0, W = 0, mstride = 0, compress = 0, K = 0;
+  int scales = 0;          // per-child Alg. 1 scales stored at +64
+  int mask_off = 64;       // first object mask inside a node record
   int node_bytes = 64;
   size_t off_nodes = 0, off_tris = 0, off_lut = 0, off_pair = 0, off_clut = 0;
   size_t total = 0;

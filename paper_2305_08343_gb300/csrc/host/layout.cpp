@@ -1,13 +1,16 @@
 // layout.cpp — the device image of a BVH (node records, triangles, tables).
 //
 // Nodes are child pairs of 64 bytes (four 16-byte vectors, one 128-bit load
-// each); in the masked uncompressed layout the two R^3-bit object masks
-// follow in the same record (mask_stride bytes each, zero padded), so a node
-// is 80 / 128 / 192 bytes at R = 4 / 6 / 8 and stays 16-byte aligned.  In the
-// compressed layout the 1-byte LUT index of each child sits in the fourth
-// vector (Sec. 3.2.4: the index replaces the mask), so the node stays 64 B.
+// each).  The masked layout adds the two children's Alg. 1 scales
+// R / extent (32 bytes) and, uncompressed, the two R^3-bit object masks
+// (mask_stride bytes each, zero padded): 112 / 160 / 224 bytes at
+// R = 4 / 6 / 8; compressed, the 1-byte LUT index of each child sits in the
+// fourth vector (Sec. 3.2.4: the index replaces the mask) and the node is
+// 96 bytes.  The compact masked layout omits the scales (80 / 128 / 192 and
+// 64 bytes).  Records stay 16-byte aligned.
 // Triangles are 48 bytes in leaf order: {v0, id}, {e1 = v1 - v0}, {e2 =
 // v2 - v0}.  Every region starts on a 256-byte boundary.
+#include <cmath>
 #include <cstring>
 
 #include "internal.h"
@@ -15,6 +18,13 @@
 namespace sc {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static bool full_mask(const uint32_t* m, int R) {
+  const int R3 = R * R * R;
+  for (int i = 0; i < R3; ++i)
+    if (!((m[i >> 5] >> (i & 31)) & 1u)) return false;
+  return true;
+}
 
 uint32_t root_slot_word(const Bvh& b) {
   if (b.root_count > 0)
@@ -30,14 +40,16 @@ static uint32_t slot_word(int32_t child, int32_t count) {
 ImageLayout image_layout(const Bvh& b, int layout) {
   ImageLayout L;
   L.layout = layout;
-  if (layout == SC_LAYOUT_MASKED) {
+  if (layout == SC_LAYOUT_MASKED || layout == SC_LAYOUT_MASKED_COMPACT) {
     if (b.R <= 0) fail(SC_ERR_STATE, "masked layout requested for a BVH built without masks");
     L.R = b.R;
     L.W = mask_words(b.R);
     L.mstride = mask_stride(b.R);
     L.compress = b.compress;
     L.K = b.K;
-    L.node_bytes = b.compress ? 64 : 64 + 2 * L.mstride;
+    L.scales = layout == SC_LAYOUT_MASKED ? 1 : 0;
+    L.mask_off = L.scales ? 96 : 64;
+    L.node_bytes = b.compress ? L.mask_off : L.mask_off + 2 * L.mstride;
   } else if (layout != SC_LAYOUT_PLAIN) {
     fail(SC_ERR_ARG, "unknown layout %d", layout);
   }
@@ -84,11 +96,24 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
     uint32_t* u = reinterpret_cast<uint32_t*>(rec + 48);
     u[0] = slot_word(b.child[2 * n], b.count[2 * n]);
     u[1] = slot_word(b.child[2 * n + 1], b.count[2 * n + 1]);
-    u[2] = (L.R > 0 && L.compress) ? b.cidx[2 * n] : 0u;
-    u[3] = (L.R > 0 && L.compress) ? b.cidx[2 * n + 1] : 0u;
-    if (L.R > 0 && !L.compress) {
-      for (int c = 0; c < 2; ++c)
-        std::memcpy(rec + 64 + c * L.mstride, &b.masks[((size_t)n * 2 + c) * L.W], 4 * L.W);
+    u[2] = u[3] = 0u;
+    if (L.R > 0) {
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t* m = L.compress ? &b.clut[(size_t)b.cidx[2 * n + c] * L.W]
+                                       : &b.masks[((size_t)n * 2 + c) * L.W];
+        uint32_t meta = L.compress ? (uint32_t)b.cidx[2 * n + c] : 0u;
+        if (full_mask(m, L.R)) meta |= kMetaFull;
+        u[2 + c] = meta;
+        if (!L.compress) std::memcpy(rec + L.mask_off + c * L.mstride, m, 4 * L.W);
+      }
+      if (L.scales) {
+        float* sc = reinterpret_cast<float*>(rec + 64);
+        for (int c = 0; c < 2; ++c)
+          for (int k = 0; k < 3; ++k) {
+            const float* bx = &b.box[12 * n + 6 * c];
+            sc[3 * c + k] = (float)L.R / std::fmax(bx[3 + k] - bx[k], 1e-30f);
+          }
+      }
     }
   });
   parallel_for(b.ntri, resolve_threads(0), 65536, [&](int64_t k) {

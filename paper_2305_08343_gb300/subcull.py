@@ -17,7 +17,7 @@ from . import _build
 SC_OK = 0
 SC_SCENE_HAIR, SC_SCENE_SOUP = 0, 1
 SC_RAYS_PINHOLE, SC_RAYS_RANDOM = 0, 1
-SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED = 0, 1
+SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED, SC_LAYOUT_MASKED_COMPACT = 0, 1, 2
 SC_CLOSEST, SC_ANY = 0, 1
 SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED = 0, 1, 2
 STATUS_NAMES = {0: "SC_OK", -1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_NOMEM",
@@ -54,7 +54,8 @@ class sc_bvh_info(C.Structure):
 
 
 class sc_trace_opts(C.Structure):
-    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int)]
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int),
+                ("refill", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -260,8 +261,8 @@ def sc_bvh_upload(bvh: Bvh, layout: int, stream=None) -> DeviceBVH:
     return DeviceBVH(bvh, layout, stream=stream)
 
 
-def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO):
-    return sc_trace_opts(block, blocks_per_sm, lut_mode)
+def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO, refill=0):
+    return sc_trace_opts(block, blocks_per_sm, lut_mode, refill)
 
 
 def sc_trace(dbvh: DeviceBVH, rays, hits, counts, mode: int, cull: int, work,

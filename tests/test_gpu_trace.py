@@ -29,12 +29,12 @@ def _need_gpu():
         pytest.fail("CUDA device required for -m gpu tests")
 
 
-def gpu_trace(bvh, rays, mode, cull, lut_mode=sc.SC_LUT_AUTO, layout=None):
+def gpu_trace(bvh, rays, mode, cull, lut_mode=sc.SC_LUT_AUTO, layout=None, refill=0):
     _need_gpu()
     lay = layout if layout is not None else (sc.SC_LAYOUT_MASKED if cull else sc.SC_LAYOUT_PLAIN)
     d = sc.DeviceBVH(bvh, lay)
     r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
-    hits, counts = sc.trace(d, r, mode, cull, opts=sc._opts(lut_mode=lut_mode))
+    hits, counts = sc.trace(d, r, mode, cull, opts=sc._opts(lut_mode=lut_mode, refill=refill))
     torch.cuda.synchronize()
     t, i, u, v = sc.split_hits(hits)
     return dict(t=t.copy(), id=i.copy(), uv=np.stack([u, v], 1),
@@ -89,12 +89,23 @@ def test_hair65k_parity_culled_and_plain(c1, comp):
 @pytest.mark.parametrize("R", [4, 6, 8])
 @pytest.mark.parametrize("comp", [0, 1])
 @pytest.mark.parametrize("lut", [sc.SC_LUT_GLOBAL, sc.SC_LUT_SHARED])
-def test_resolutions_and_lut_modes(hair_small, R, comp, lut):
+@pytest.mark.parametrize("layout", [sc.SC_LAYOUT_MASKED, sc.SC_LAYOUT_MASKED_COMPACT])
+def test_resolutions_lut_modes_layouts(hair_small, R, comp, lut, layout):
     tris, rays = hair_small
     b = sc.sc_bvh_build(tris, R, comp)
-    g = gpu_trace(b, rays, 0, 1, lut_mode=lut)
+    g = gpu_trace(b, rays, 0, 1, lut_mode=lut, layout=layout)
     o = oracle_trace(tris, rays, R, comp, 0, 1)
-    assert_parity(g, o, f"R={R} comp={comp} lut={lut}")
+    assert_parity(g, o, f"R={R} comp={comp} lut={lut} layout={layout}")
+
+
+@pytest.mark.parametrize("refill", [1, 4, 16, 32])
+def test_refill_threshold_does_not_change_results(hair_small, refill):
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, 6, 1)
+    o = oracle_trace(tris, rays, 6, 1, 0, 1)
+    assert_parity(gpu_trace(b, rays, 0, 1, refill=refill), o, f"refill={refill}")
+    assert_parity(gpu_trace(b, rays, 0, 0, refill=refill), oracle_trace(tris, rays, 0, 0, 0, 0),
+                  f"plain refill={refill}")
 
 
 @pytest.mark.parametrize("mode", [0, 1])
