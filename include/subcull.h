@@ -221,6 +221,32 @@ sc_status sc_trace_host(const sc_dbvh* d, const float* h_rays, int64_t n,
                         sc_hit* d_hits_buf, uint32_t* d_counts_buf,
                         void* d_work, size_t work_bytes, void* stream);
 
+/*
+ * sc_trace for callers that cannot allocate device memory.  Some hosts own
+ * all of the GPU's memory through their own allocator (a renderer or a
+ * framework with a caching pool) and fail or stall on an extra cudaMalloc,
+ * which may also synchronize the whole device; such callers cannot create
+ * the workspace sc_trace takes.  This entry point allocates nothing: the
+ * ray counter and status word live in a static device array of 256 bytes
+ * that every GPU loading this library holds until exit.  (The paper has no
+ * counterpart: this is an interface convenience.)
+ *
+ * Arguments as for sc_trace, without the workspace: the caller still passes
+ * the image, rays, hits and (optional) counts.  The call clears the scratch,
+ * launches the trace on `stream`, waits for it and returns the device
+ * status (SC_ERR_STACK / SC_ERR_STATE as sc_status_poll would).  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialized by the caller.  Returns
+ * SC_ERR_UNSUPPORTED if the trace ever needed more scratch than the array
+ * holds; no cudaMalloc, cudaFree or allocating library routine is called.
+ */
+sc_status sc_trace_noalloc(const sc_dbvh* d, const float* d_rays, int64_t n,
+                           sc_hit* d_hits, uint32_t* d_counts, int mode,
+                           int cull, const sc_trace_opts* opts, void* stream);
+
 /* Synchronizes `stream` and returns the device status word of d_work
    (SC_OK, or SC_ERR_STACK if a ray's stack overflowed). */
 sc_status sc_status_poll(const void* d_work, void* stream);

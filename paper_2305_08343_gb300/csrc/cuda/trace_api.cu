@@ -120,6 +120,37 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch for sc_trace_noalloc: the ray counter and device status word that
+// sc_trace keeps in a caller-provided workspace live here instead.  Every GPU
+// that loads this library holds these bytes until the process exits.  Host
+// code must not pass `g_noalloc_scratch` itself to a kernel (on the host it
+// names a stand-in, not device memory); its device address is looked up once
+// per device with cudaGetSymbolAddress, with that device current.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+void* noalloc_scratch_address() {
+  int dev = 0;
+  CUDA_OK(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::vector<void*> addr;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      fail(SC_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+}  // namespace
+
 #define SC_TRY \
   try {        \
     clear_error();
@@ -200,6 +231,29 @@ sc_status sc_trace_host(const sc_dbvh* d, const float* h_rays, int64_t n, sc_hit
       CUDA_OK(cudaMemcpyAsync(h_counts, d_counts_buf, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
   }
   CUDA_OK(cudaStreamSynchronize(st));
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_trace_noalloc(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hits,
+                           uint32_t* d_counts, int mode, int cull, const sc_trace_opts* opts,
+                           void* stream) {
+  SC_TRY
+  const size_t need = kWorkBytes;
+  if (need > kNoallocScratchBytes)
+    fail(SC_ERR_UNSUPPORTED,
+         "sc_trace_noalloc: the trace needs %zu bytes of scratch, the static area holds %zu", need,
+         kNoallocScratchBytes);
+  void* scratch = noalloc_scratch_address();
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch_trace(d, d_rays, n, d_hits, d_counts, mode, cull, opts, scratch, kNoallocScratchBytes,
+               st);
+  unsigned word[2] = {0, 0};
+  CUDA_OK(cudaMemcpyAsync(word, scratch, sizeof(word), cudaMemcpyDeviceToHost, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  if (word[1] & sct::ST_STACK) fail(SC_ERR_STACK, "device: a traversal stack overflowed");
+  if (word[1] & sct::ST_BAD_NODE)
+    fail(SC_ERR_STATE, "device: the BVH image holds an invalid child reference");
   return SC_OK;
   SC_CATCH
 }

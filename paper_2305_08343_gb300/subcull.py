@@ -93,6 +93,8 @@ def lib():
             "sc_trace_host": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, C.c_int,
                                         P(sc_trace_opts), vp, vp, vp, vp, C.c_size_t, vp]),
             "sc_status_poll": (C.c_int, [vp, vp]),
+            "sc_trace_noalloc": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, C.c_int,
+                                           P(sc_trace_opts), vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -290,6 +292,18 @@ def sc_trace_host(dbvh: DeviceBVH, h_rays, h_hits, h_counts, mode: int, cull: in
                                C.c_void_p(d_hits.data_ptr()),
                                C.c_void_p(d_counts.data_ptr()) if d_counts is not None else None,
                                C.c_void_p(work.data_ptr()), work.numel(), _stream_ptr(stream)))
+
+
+def sc_trace_noalloc(dbvh: DeviceBVH, rays, hits, counts, mode: int, cull: int,
+                     opts: sc_trace_opts | None = None, stream=None):
+    """sc_trace without a workspace (static device scratch); blocks until the
+    trace has finished and raises on a device-side error."""
+    n = rays.shape[0]
+    o = opts or _opts()
+    _check(lib().sc_trace_noalloc(dbvh.handle, C.c_void_p(rays.data_ptr()), n,
+                                  C.c_void_p(hits.data_ptr()),
+                                  C.c_void_p(counts.data_ptr()) if counts is not None else None,
+                                  mode, cull, C.byref(o), _stream_ptr(stream)))
 
 
 def sc_status_poll(work, stream=None):
