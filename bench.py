@@ -37,11 +37,14 @@ WORKLOADS = {
     "hair1m_comp": ("as hair1m with LUT-compressed masks (256 entries, 8-bit index)",
                     dict(strands=32768, ground=True, seed=2), (1920, 1080), 6, 1),
     "hair12m": ("12,100,000 thin hair triangles (378,125 strands x 16 x 2), seed 4; 1920x1080 "
-                "pinhole primary rays + one diffuse bounce wave; R=6 LUT-compressed masks, L=3",
+                "pinhole primary rays + two diffuse bounce waves; R=6 LUT-compressed masks, L=3",
                 dict(strands=378125, ground=False, seed=4), (1920, 1080), 6, 1),
     "hair65k": ("65,536 hair triangles (2,048 strands), seed 1; 256x256 pinhole rays; R=6 "
                 "uncompressed", dict(strands=2048, ground=False, seed=1), (256, 256), 6, 0),
 }
+
+
+WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1}
 
 
 def load_peaks():
@@ -197,6 +200,20 @@ METRIC = "Mrays/s closest-hit, culled vs plain, 1 GB300, identical hits; node+tr
 
 # ------------------------------------------------------------------ gb300 --
 
+def _sorted_waves(bufs, sizes):
+    """Per wave: (path ids, hit records as int32 [m,4], counts [m,2]) sorted by
+    path id (queue order differs between runs)."""
+    import torch
+    out = []
+    for w, m in enumerate(sizes):
+        m = int(m)
+        path = bufs.path[w][:m]
+        order = torch.argsort(path, stable=True)
+        out.append((path[order], bufs.hits[w][:m].view(torch.int32)[order],
+                    bufs.counts[w][:m][order] if bufs.counts[w] is not None else None))
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -214,6 +231,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     desc, tris, rays_np, R, comp = make_inputs(args.workload)
+    bounces = args.bounces if args.bounces >= 0 else WORKLOAD_BOUNCES.get(args.workload, 1)
     t0 = time.perf_counter()
     bvh = sc.sc_bvh_build(tris, R, comp)
     build_s = time.perf_counter() - t0
@@ -222,31 +240,60 @@ def run_gpu(args):
     d_plain = sc.DeviceBVH(bvh, sc.SC_LAYOUT_PLAIN)
     n = rays_np.shape[0]
     rays = torch.from_numpy(rays_np).to(dev)
-    hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
-    hits_plain = torch.empty((n, 4), dtype=torch.float32, device=dev)
-    counts = torch.empty((n, 2), dtype=torch.int32, device=dev)
-    counts_plain = torch.empty((n, 2), dtype=torch.int32, device=dev)
-    work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
+    opts = sc._opts(lut_mode=args.lut, refill=args.refill)
+    seed = 2305
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
-    opts = sc._opts(lut_mode=args.lut, refill=args.refill)
 
-    # reference pass with counts (untimed): identical hits and tests per ray
-    sc.sc_trace(d_masked, rays, hits, counts, 0, 1, work, opts)
-    sc.sc_trace(d_plain, rays, hits_plain, counts_plain, 0, 0, work, opts)
-    sc.sc_status_poll(work)
-    # compare the 16-byte records bitwise (a miss stores id -1, a NaN pattern as float)
-    same = bool(torch.equal(hits.view(torch.int32), hits_plain.view(torch.int32)))
-    cnt_c = counts.double().mean(0).tolist()
-    cnt_p = counts_plain.double().mean(0).tolist()
-    le = bool((counts <= counts_plain).all().item())
+    # reference passes with counts (untimed): wave sizes, identical hits, tests per ray
+    ref_c = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
+    ref_p = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
+    _, sizes = sc.trace_waves(d_masked, rays, bounces, seed, 1, ref_c, opts)
+    _, sizes_p = sc.trace_waves(d_plain, rays, bounces, seed, 0, ref_p, opts)
+    wc, wpl = _sorted_waves(ref_c, sizes), _sorted_waves(ref_p, sizes_p)
+    same = bool(np.array_equal(sizes, sizes_p)) and all(
+        torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(wc, wpl))
+    le = all(bool((a[2] <= b[2]).all().item()) for a, b in zip(wc, wpl))
+    cat_c = torch.cat([x[2] for x in wc]).double()
+    cat_p = torch.cat([x[2] for x in wpl]).double()
+    cnt_c, cnt_p = cat_c.mean(0).tolist(), cat_p.mean(0).tolist()
+    rays_per_step = int(np.sum(sizes))
+    del ref_c, ref_p, wc, wpl, cat_c, cat_p
 
-    def timed(dbvh, cull, out_hits):
+    bufs_c = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
+    bufs_p = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
+
+    def capture(dbvh, cull, bufs):
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, opts)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, opts)
+        return g
+
+    graphs = None
+    try:
+        graphs = (capture(d_masked, 1, bufs_c), capture(d_plain, 0, bufs_p))
+    except Exception as e:  # report, then time eager launches
+        graphs = None
+        graph_error = str(e)
+
+    def step(i_graph, dbvh, cull, bufs):
+        if graphs is not None:
+            graphs[i_graph].replay()
+        else:
+            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, opts)
+
+    def timed(i_graph, dbvh, cull, bufs):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         for _ in range(args.warmup):
             flush.zero_()
-            sc.sc_trace(dbvh, rays, out_hits, None, 0, cull, work, opts)
+            step(i_graph, dbvh, cull, bufs)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -254,46 +301,72 @@ def run_gpu(args):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            sc.sc_trace(dbvh, rays, out_hits, None, 0, cull, work, opts)
+            step(i_graph, dbvh, cull, bufs)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms
+        return [a.elapsed_time(b) for a, b in ev]
 
     with ClockSampler(local) as clk:
-        ms_cull = timed(d_masked, 1, hits)
-        ms_plain = timed(d_plain, 0, hits_plain)
-    sc.sc_status_poll(work)
+        ms_cull = timed(0, d_masked, 1, bufs_c)
+        ms_plain = timed(1, d_plain, 0, bufs_p)
+    sc.sc_waves_poll(bufs_c.ws, bounces)
+    sc.sc_waves_poll(bufs_p.ws, bounces)
     tot_cull = float(np.sum(ms_cull))
     if dist:
         t = torch.tensor([tot_cull], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_cull = float(t.item())
-    rays_total = n * args.steps * world
-    value = rays_total / (tot_cull * 1e-3) / 1e6
-    plain_value = n * args.steps / (float(np.sum(ms_plain)) * 1e-3) / 1e6
+    value = rays_per_step * args.steps * world / (tot_cull * 1e-3) / 1e6
+    plain_value = rays_per_step * args.steps / (float(np.sum(ms_plain)) * 1e-3) / 1e6
 
-    # end to end through the C-ABI with host buffers (H2D rays, D2H hits)
+    # primary wave alone (single-batch sc_trace), for context
+    hits1 = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    prim = {}
+    for name, dbvh, cull in (("culled", d_masked, 1), ("plain", d_plain, 0)):
+        for _ in range(2):
+            sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, opts)
+        flush.zero_()
+        ev[0].record(stream)
+        for _ in range(3):
+            sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, opts)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        prim[name] = 3 * n / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e6
+
+    # end to end through the public API: pinned host rays -> device, the wave
+    # pipeline, every wave's hit buffer -> pinned host
     h_rays = torch.from_numpy(rays_np).pin_memory()
-    h_hits = torch.empty((n, 4), dtype=torch.float32).pin_memory()
-    d_rays_buf = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    h_hits = [torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in range(bounces + 1)]
+    d_rays = torch.empty((n, 8), dtype=torch.float32, device=dev)
+
+    def e2e_step():
+        d_rays.copy_(h_rays, non_blocking=True)
+        sc.sc_trace_waves(d_masked, d_rays, bounces, seed, 1, bufs_c.outs(), bufs_c.ws, opts)
+        for w in range(bounces + 1):
+            h_hits[w].copy_(bufs_c.hits[w], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
     for _ in range(args.warmup):
-        sc.sc_trace_host(d_masked, h_rays, h_hits, None, 0, 1, d_rays_buf, hits, None, work, opts)
-    torch.cuda.synchronize()
+        e2e_step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        sc.sc_trace_host(d_masked, h_rays, h_hits, None, 0, 1, d_rays_buf, hits, None, work, opts)
+        e2e_step()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": n * args.steps / e2e_s / 1e6, "unit": "Mrays/s",
-           "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 16}
+    e2e = {"value": rays_per_step * args.steps / e2e_s / 1e6, "unit": "Mrays/s",
+           "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 16 * (bounces + 1)}
 
-    # roofline of the traversal kernel: algorithmic bytes per ray
+    # roofline of the wave kernel: algorithmic bytes per ray (ray 32 + hit 16
+    # + path 4 + node records + 48-B triangles; spawned rays add 32 + 4)
     node_bytes = ((96 if args.layout == 1 else 64) +
                   (0 if comp else 2 * {4: 8, 6: 32, 8: 64}[R]))
-    b_ray = 32 + 16 + (cnt_c[0] / 2.0) * node_bytes + cnt_c[1] * 48
-    per_launch_bytes = b_ray * n
+    spawned = float(np.sum(sizes[1:])) / rays_per_step
+    b_ray = (32 + 16 + 4 + (cnt_c[0] / 2.0) * node_bytes + cnt_c[1] * 48
+             + spawned * (32 + 4))
+    per_launch_bytes = b_ray * rays_per_step
     avg_ms = float(np.mean(ms_cull))
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peaks = load_peaks()
@@ -301,7 +374,7 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured" if peaks else "fallback",
-                "bytes_per_ray": b_ray}
+                "bytes_per_ray": b_ray, "kernel": "waves_kernel (culled)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -312,33 +385,39 @@ def run_gpu(args):
             ob.compress(256, 8)
             cull_mode = 2
         thr = cpu_count()
-        v, sample, dt, ref = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0)
+        v, sample, dt, _ = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0)
         cpu = {"value": v / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{sample} primary rays evenly spaced over the {n}, culled closest hit, "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s on {thr} threads (oracle's own BVH and masks)"}
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms_cull)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "rays_per_step": n,
-                   "grid_res": R, "compressed": bool(comp), "L": 3, "lut_mode": args.lut,
+        "config": {"workload": args.workload, "description": desc, "primary_rays": n,
+                   "bounces": bounces, "rays_per_step": rays_per_step,
+                   "wave_sizes": [int(x) for x in sizes], "grid_res": R,
+                   "compressed": bool(comp), "L": 3, "lut_mode": args.lut,
                    "layout": args.layout, "refill": args.refill,
+                   "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "plain_mrays_s": plain_value, "speedup_vs_plain": value / world / plain_value,
+        "primary_only_mrays_s": prim,
         "identical_hits": same, "culled_counts_le_plain": le,
         "tests_per_ray": {"culled": {"node": cnt_c[0], "tri": cnt_c[1],
                                      "node_plus_tri": cnt_c[0] + cnt_c[1]},
                           "plain": {"node": cnt_p[0], "tri": cnt_p[1],
                                     "node_plus_tri": cnt_p[0] + cnt_p[1]}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
         "build_s": build_s, "bvh": {"nodes": info.num_nodes, "max_depth": info.max_depth,
                                     "ms_bvh": info.ms_bvh, "ms_masks": info.ms_masks,
                                     "ms_compress": info.ms_compress},
     }
+    if graphs is None:
+        line["config"]["cuda_graph_error"] = graph_error
     if rank == 0:
         print(json.dumps(line))
     if dist:
@@ -357,6 +436,7 @@ def main():
     ap.add_argument("--layout", type=int, default=1, help="1 masked (scales stored), 2 compact")
     ap.add_argument("--refill", type=int, default=0, help="idle lanes before a warp refills")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bounces", type=int, default=-1, help="bounce waves (-1: workload's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -247,6 +247,41 @@ sc_status sc_trace_noalloc(const sc_dbvh* d, const float* d_rays, int64_t n,
                            sc_hit* d_hits, uint32_t* d_counts, int mode,
                            int cull, const sc_trace_opts* opts, void* stream);
 
+/* ------------------------------------------------------------- waves --- */
+/* Primary rays plus diffuse bounce waves in one persistent (cooperative)
+   launch.  The paper's workload is path tracing (Sec. 4); here every
+   closest hit of wave w spawns one cosine-weighted bounce ray (random bits
+   from the hash of Jarzynski & Olano 2020 keyed by seed, path id and
+   bounce) into the queue of wave w+1, so later waves hold only spawned
+   rays; a bounded grid barrier separates the waves.  Capturable in a CUDA
+   graph (the launch is a cooperative kernel node). */
+#define SC_MAX_BOUNCES 4
+
+typedef struct {
+  sc_hit* hits;     /* device sc_hit[n0]: wave entries in queue order      */
+  int32_t* path;    /* device int32[n0] or NULL: primary ray of each entry */
+  uint32_t* counts; /* device uint32[n0][2] or NULL                        */
+} sc_wave_out;
+
+/* Workspace bytes sc_trace_waves needs for n0 primary rays (two ray queues,
+   their path ids and the control words). */
+size_t sc_trace_waves_workspace_bytes(int64_t n0);
+
+/* d_rays: device float[n0][8] primary rays; outs: host array of bounces+1
+   sc_wave_out (each buffer sized for n0 entries); d_ws: device workspace,
+   256-byte aligned, >= sc_trace_waves_workspace_bytes(n0); cull as in
+   sc_trace (closest hit only).  Asynchronous; wave sizes and the device
+   status come from sc_waves_poll. */
+sc_status sc_trace_waves(const sc_dbvh* d, const float* d_rays, int64_t n0,
+                         int bounces, uint32_t seed, int cull,
+                         const sc_wave_out* outs, const sc_trace_opts* opts,
+                         void* d_ws, size_t ws_bytes, void* stream);
+
+/* Synchronizes `stream`; sizes (host uint32[bounces+1]) receives the number
+   of rays of each bounce wave (sizes[0] = 0: wave 0 is the n0 primaries).
+   Returns SC_ERR_TIMEOUT / SC_ERR_STACK / SC_ERR_STATE on device errors. */
+sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* stream);
+
 /* Synchronizes `stream` and returns the device status word of d_work
    (SC_OK, or SC_ERR_STACK if a ray's stack overflowed). */
 sc_status sc_status_poll(const void* d_work, void* stream);

@@ -87,6 +87,9 @@ def lib():
             "or_ray_tri": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f), _P(f)]),
             "or_slab": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f)]),
             "or_cell": (C.c_int, [f, f, f, C.c_int]),
+            "or_pcg_hash": (u32, [u32]),
+            "or_bounce_hash": (u32, [u32, u32, u32, u32]),
+            "or_bounce": (C.c_int, [_P(f), f, _P(f), u32, u32, u32, _P(f)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -318,3 +321,34 @@ def slab(ray8, box6, tcur=np.inf):
 
 def cell(p: float, lo: float, hi: float, R: int) -> int:
     return int(lib().or_cell(float(p), float(lo), float(hi), R))
+
+
+# -------------------------------------------------------------- bounce rays --
+
+def pcg_hash(v: int) -> int:
+    return int(lib().or_pcg_hash(v & 0xFFFFFFFF))
+
+
+def bounce(ray8, t: float, tri9, seed: int, rid: int, bounce_idx: int):
+    """One diffuse bounce ray (float32[8]) or None for a degenerate triangle."""
+    r, tr = _f32(ray8).reshape(8), _f32(tri9).reshape(9)
+    out = np.zeros(8, np.float32)
+    ok = lib().or_bounce(_ptr(r, C.c_float), float(t), _ptr(tr, C.c_float), seed & 0xFFFFFFFF,
+                         rid & 0xFFFFFFFF, bounce_idx, _ptr(out, C.c_float))
+    return out if ok else None
+
+
+def bounce_wave(rays, hit_t, hit_id, tris, seed: int, bounce_idx: int, path=None):
+    """Bounce rays for every hit of a wave, in ray order.  The random stream of
+    a ray is keyed by its path id (the primary ray it descends from), so it
+    does not depend on the order of a wave.  Returns (rays, path ids)."""
+    path = np.arange(len(hit_id)) if path is None else np.asarray(path)
+    out, par = [], []
+    for i in np.nonzero(hit_id >= 0)[0]:
+        b = bounce(rays[i], float(hit_t[i]), tris[hit_id[i]], seed, int(path[i]), bounce_idx)
+        if b is not None:
+            out.append(b)
+            par.append(int(path[i]))
+    if not out:
+        return np.zeros((0, 8), np.float32), np.zeros(0, np.int64)
+    return np.stack(out), np.asarray(par, np.int64)

@@ -1041,3 +1041,77 @@ void or_brute(const float* tris, int64_t ntri, const float* rays, int64_t n,
     if (t2) t2[i] = second;
   }
 }
+
+/* --------------------------------------------- diffuse bounce rays (waves) --- */
+/*
+ * Not part of the paper (its path tracer is unspecified beyond "path tracing
+ * with 16 samples per pixel", Sec. 4): the wave workloads spawn one
+ * cosine-weighted diffuse bounce per hit.  Random numbers come from a
+ * counter-based hash, the PCG-based hash of Jarzynski & Olano, "Hash
+ * Functions for GPU Rendering" (JCGT 9(3), 2020), restated from its
+ * definition: state = v * 747796405 + 2891336453; word = ((state >>
+ * ((state >> 28) + 4)) ^ state) * 277803737; result = (word >> 22) ^ word.
+ */
+uint32_t or_pcg_hash(uint32_t v) {
+  uint32_t state = v * 747796405u + 2891336453u;
+  uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+uint32_t or_bounce_hash(uint32_t seed, uint32_t rid, uint32_t bounce, uint32_t k) {
+  return or_pcg_hash(or_pcg_hash(or_pcg_hash(seed ^ (bounce << 24)) + rid) + k);
+}
+
+/*
+ * Bounce ray from a hit: origin o + t*d; geometric normal cross(e1, e2)
+ * turned against d and normalised; an orthonormal frame from cross products;
+ * a point of the unit disk by rejection (at most 64 tries, else the centre)
+ * lifted to the hemisphere (Malley's method gives a cosine-weighted
+ * direction); tmin = 1e-4, tmax = +inf.  Float ops only, each correctly
+ * rounded (sqrt included), so the GPU produces the same bits.  Returns 0 for
+ * a degenerate triangle (no bounce).
+ */
+int or_bounce(const float* ray8, float t, const float* tri9, uint32_t seed,
+              uint32_t rid, uint32_t bounce, float* out8) {
+  float o[3] = {ray8[0], ray8[1], ray8[2]}, d[3] = {ray8[4], ray8[5], ray8[6]};
+  float p[3], e1[3], e2[3], n[3];
+  for (int k = 0; k < 3; ++k) {
+    p[k] = o[k] + t * d[k];
+    e1[k] = tri9[3 + k] - tri9[k];
+    e2[k] = tri9[6 + k] - tri9[k];
+  }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  if ((n[0] * d[0] + n[1] * d[1]) + n[2] * d[2] > 0.0f) {
+    n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
+  }
+  float l2 = (n[0] * n[0] + n[1] * n[1]) + n[2] * n[2];
+  if (!(l2 > 0.0f)) return 0;
+  float l = sqrtf(l2);
+  for (int k = 0; k < 3; ++k) n[k] = n[k] / l;
+  float a[3] = {0.0f, 0.0f, 0.0f};
+  if (fabsf(n[0]) > 0.9f) a[1] = 1.0f; else a[0] = 1.0f;
+  float t1[3] = {a[1] * n[2] - a[2] * n[1], a[2] * n[0] - a[0] * n[2],
+                 a[0] * n[1] - a[1] * n[0]};
+  float m = sqrtf((t1[0] * t1[0] + t1[1] * t1[1]) + t1[2] * t1[2]);
+  for (int k = 0; k < 3; ++k) t1[k] = t1[k] / m;
+  float t2[3] = {n[1] * t1[2] - n[2] * t1[1], n[2] * t1[0] - n[0] * t1[2],
+                 n[0] * t1[1] - n[1] * t1[0]};
+  float x = 0.0f, y = 0.0f, r2 = 0.0f;
+  for (uint32_t k = 0; k < 64; ++k) {
+    float u1 = (float)(or_bounce_hash(seed, rid, bounce, 2 * k) >> 8) * 5.9604644775390625e-08f;
+    float u2 = (float)(or_bounce_hash(seed, rid, bounce, 2 * k + 1) >> 8) * 5.9604644775390625e-08f;
+    float xx = 2.0f * u1 - 1.0f, yy = 2.0f * u2 - 1.0f;
+    float rr = xx * xx + yy * yy;
+    if (rr < 1.0f) { x = xx; y = yy; r2 = rr; break; }
+  }
+  float z = sqrtf(1.0f - r2);
+  for (int k = 0; k < 3; ++k) {
+    out8[k] = p[k];
+    out8[4 + k] = (x * t1[k] + y * t2[k]) + z * n[k];
+  }
+  out8[3] = 1e-4f;
+  out8[7] = INFINITY;
+  return 1;
+}

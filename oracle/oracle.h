@@ -87,6 +87,14 @@ int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
 void or_brute(const float* tris, int64_t ntri, const float* rays, int64_t n,
               int mode, float* hit_t, int32_t* hit_id, float* t2);
 
+/* Diffuse bounce rays of the wave workloads (not in the paper): counter-based
+   hash (Jarzynski & Olano 2020) and a cosine-weighted direction about the
+   geometric normal.  Returns 0 (no ray) for a degenerate triangle. */
+uint32_t or_pcg_hash(uint32_t v);
+uint32_t or_bounce_hash(uint32_t seed, uint32_t rid, uint32_t bounce, uint32_t k);
+int or_bounce(const float* ray8, float t, const float* tri9, uint32_t seed,
+              uint32_t rid, uint32_t bounce, float* out8);
+
 /* Single ray-triangle test and slab test, exposed for pins. */
 int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
                float* u, float* v);

@@ -13,6 +13,10 @@ KernelFn get_kernel_plain(int mode);
 KernelFn get_kernel_r4(int cull, int mode, int lutv, int scales);
 KernelFn get_kernel_r6(int cull, int mode, int lutv, int scales);
 KernelFn get_kernel_r8(int cull, int mode, int lutv, int scales);
+WaveKernelFn get_waves_plain();
+WaveKernelFn get_waves_r4(int cull, int scales);
+WaveKernelFn get_waves_r6(int cull, int scales);
+WaveKernelFn get_waves_r8(int cull, int scales);
 }  // namespace sct
 
 using namespace sc;
@@ -108,6 +112,7 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   p.hits = reinterpret_cast<float4*>(d_hits);
   p.counts = reinterpret_cast<uint2*>(d_counts);
   p.work = reinterpret_cast<unsigned*>(d_work);
+  p.status = p.work + 1;
   p.n = n;
   p.num_nodes = d->nn;
   p.num_tris = d->ntri;
@@ -116,6 +121,115 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   p.refill = o.refill ? o.refill : kDefaultRefill;
   k<<<(unsigned)grid, kBlock, 0, st>>>(p);
   CUDA_OK(cudaGetLastError());
+}
+
+size_t waves_ws_bytes(int64_t n0) {
+  const size_t q = (size_t)(n0 > 0 ? n0 : 1);
+  return 256 + 2 * (q * 32 + 255) / 256 * 256 + 2 * (q * 4 + 255) / 256 * 256;
+}
+
+void fill_params(const sc_dbvh* d, sct::Params& p) {
+  const uint8_t* base = d->base;
+  p.nodes = reinterpret_cast<const float4*>(base + d->lay.off_nodes);
+  p.node_f4 = d->lay.node_bytes / 16;
+  p.mask_off_f4 = d->lay.mask_off / 16;
+  p.tris = reinterpret_cast<const float4*>(base + d->lay.off_tris);
+  p.lut = d->lay.R ? reinterpret_cast<const uint4*>(base + d->lay.off_lut) : nullptr;
+  p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
+  p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
+  p.num_nodes = d->nn;
+  p.num_tris = d->ntri;
+  p.root_slot = d->root_slot;
+  p.has_root = d->has_root;
+}
+
+void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces, uint32_t seed,
+                  int cull, const sc_wave_out* outs, const sc_trace_opts* opts, void* d_ws,
+                  size_t ws_bytes, cudaStream_t st) {
+  if (!d) fail(SC_ERR_ARG, "sc_trace_waves: NULL device BVH");
+  if (n0 < 0 || n0 > (int64_t)0x7FFFFF00) fail(SC_ERR_ARG, "sc_trace_waves: n0 out of range");
+  if (bounces < 0 || bounces + 1 > sct::kMaxWaves)
+    fail(SC_ERR_ARG, "sc_trace_waves: bounces must be 0..%d", sct::kMaxWaves - 1);
+  if (!outs) fail(SC_ERR_ARG, "sc_trace_waves: NULL outputs");
+  for (int w = 0; w <= bounces; ++w) {
+    if (n0 > 0 && !outs[w].hits) fail(SC_ERR_ARG, "sc_trace_waves: wave %d has no hit buffer", w);
+    if ((reinterpret_cast<uintptr_t>(outs[w].hits) & 15) ||
+        (reinterpret_cast<uintptr_t>(outs[w].counts) & 7) ||
+        (reinterpret_cast<uintptr_t>(outs[w].path) & 3))
+      fail(SC_ERR_ARG, "sc_trace_waves: misaligned output of wave %d", w);
+  }
+  if (n0 > 0 && !d_rays) fail(SC_ERR_ARG, "sc_trace_waves: NULL rays");
+  if (reinterpret_cast<uintptr_t>(d_rays) & 15) fail(SC_ERR_ARG, "rays must be 16-byte aligned");
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255) || ws_bytes < waves_ws_bytes(n0))
+    fail(SC_ERR_ARG, "sc_trace_waves: workspace must be 256-byte aligned and >= %zu bytes",
+         waves_ws_bytes(n0));
+  if (cull && d->lay.R == 0) fail(SC_ERR_STATE, "sc_trace_waves: culling needs a masked image");
+  if (d->stack_need > sct::kStack)
+    fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
+         sct::kStack);
+  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0};
+  if (opts) o = *opts;
+  if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
+  if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
+  sct::WaveKernelFn k = nullptr;
+  if (!cull) {
+    k = sct::get_waves_plain();
+  } else {
+    const int c = d->lay.compress ? 2 : 1, sc = d->lay.scales;
+    switch (d->lay.R) {
+      case 4: k = sct::get_waves_r4(c, sc); break;
+      case 6: k = sct::get_waves_r6(c, sc); break;
+      case 8: k = sct::get_waves_r8(c, sc); break;
+      default: fail(SC_ERR_UNSUPPORTED, "no wave kernel for R = %d", d->lay.R);
+    }
+  }
+  CUDA_OK(cudaMemsetAsync(d_ws, 0, 256, st));
+  if (n0 == 0) return;
+  sct::WaveParams wp;
+  std::memset(&wp, 0, sizeof(wp));
+  fill_params(d, wp.p);
+  wp.p.work = reinterpret_cast<unsigned*>(d_ws);
+  wp.p.status = wp.p.work + sct::WW_STATUS;
+  wp.p.refill = o.refill ? o.refill : kDefaultRefill;
+  wp.p.n = n0;
+  uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
+  const size_t q = (size_t)n0;
+  size_t off = 256;
+  for (int i = 0; i < 2; ++i) {
+    wp.qrays[i] = reinterpret_cast<float4*>(ws + off);
+    off += (q * 32 + 255) / 256 * 256;
+  }
+  for (int i = 0; i < 2; ++i) {
+    wp.qpath[i] = reinterpret_cast<int*>(ws + off);
+    off += (q * 4 + 255) / 256 * 256;
+  }
+  wp.rays0 = reinterpret_cast<const float4*>(d_rays);
+  wp.n0 = n0;
+  for (int w = 0; w <= bounces; ++w) {
+    wp.hits[w] = reinterpret_cast<float4*>(outs[w].hits);
+    wp.path[w] = outs[w].path;
+    wp.counts[w] = reinterpret_cast<uint2*>(outs[w].counts);
+  }
+  wp.bounces = bounces;
+  wp.seed = seed;
+  wp.timeout_ns = 2000000000ULL;
+  DevInfo di = device_info();
+  int per_sm = 0;
+  CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, kBlock, 0));
+  if (per_sm < 1) fail(SC_ERR_CUDA, "wave kernel cannot be resident");
+  if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(di.sms * per_sm));
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUDA_OK(cudaLaunchKernelEx(&cfg, k, wp));
 }
 
 }  // namespace
@@ -253,6 +367,36 @@ sc_status sc_trace_noalloc(const sc_dbvh* d, const float* d_rays, int64_t n, sc_
   CUDA_OK(cudaStreamSynchronize(st));
   if (word[1] & sct::ST_STACK) fail(SC_ERR_STACK, "device: a traversal stack overflowed");
   if (word[1] & sct::ST_BAD_NODE)
+    fail(SC_ERR_STATE, "device: the BVH image holds an invalid child reference");
+  return SC_OK;
+  SC_CATCH
+}
+
+size_t sc_trace_waves_workspace_bytes(int64_t n0) { return waves_ws_bytes(n0); }
+
+sc_status sc_trace_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces,
+                         uint32_t seed, int cull, const sc_wave_out* outs,
+                         const sc_trace_opts* opts, void* d_ws, size_t ws_bytes, void* stream) {
+  SC_TRY
+  launch_waves(d, d_rays, n0, bounces, seed, cull, outs, opts, d_ws, ws_bytes,
+               reinterpret_cast<cudaStream_t>(stream));
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* stream) {
+  SC_TRY
+  if (!d_ws || !sizes || bounces < 0 || bounces + 1 > sct::kMaxWaves)
+    fail(SC_ERR_ARG, "sc_waves_poll: bad argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned w[sct::WW_WORDS];
+  CUDA_OK(cudaMemcpyAsync(w, d_ws, sizeof(w), cudaMemcpyDeviceToHost, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  for (int i = 0; i <= bounces; ++i) sizes[i] = i == 0 ? 0u : w[sct::WW_SIZE + i];
+  const unsigned status = w[sct::WW_STATUS];
+  if (status & sct::ST_TIMEOUT) fail(SC_ERR_TIMEOUT, "device: a wave barrier timed out");
+  if (status & sct::ST_STACK) fail(SC_ERR_STACK, "device: a traversal stack overflowed");
+  if (status & sct::ST_BAD_NODE)
     fail(SC_ERR_STATE, "device: the BVH image holds an invalid child reference");
   return SC_OK;
   SC_CATCH

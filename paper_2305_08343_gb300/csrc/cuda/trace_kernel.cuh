@@ -47,7 +47,8 @@ struct Params {
   const float4* rays;       // 2 float4 per ray
   float4* hits;             // {t, id bits, u, v}
   uint2* counts;            // or nullptr
-  unsigned* work;           // [0] ray counter, [1] status
+  unsigned* work;           // ray counter(s) / control words
+  unsigned* status;         // device status word (ST_* bits)
   long long n;
   long long num_nodes;      // inner nodes in the image
   long long num_tris;
@@ -122,7 +123,7 @@ struct SmemLut {
 };
 
 template <int R>
-__device__ void stage_lut(SmemLut<R>& s, const uint2* pair) {
+__device__ __forceinline__ void stage_lut(SmemLut<R>& s, const uint2* pair) {
   for (int i = threadIdx.x; i < R * R * R * R; i += blockDim.x) {
     const uint2 v = pair[i];
     s.P[i] = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
@@ -224,11 +225,191 @@ struct RayState {
   float ox, oy, oz, dx, dy, dz, ix, iy, iz, tmin, tcur;
   float ht, hu, hv;
   int hid;
+  int hpos;   // leaf position of the accepted triangle (for bounce normals)
   unsigned ntest, ttest;
   int sp;
   uint32_t cur;
   bool have;  // `cur` is the next slot to visit (else pop)
 };
+
+__device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const float4 rb,
+                                         const Params& p) {
+  s.ox = ra.x; s.oy = ra.y; s.oz = ra.z; s.tmin = ra.w;
+  s.dx = rb.x; s.dy = rb.y; s.dz = rb.z; s.tcur = rb.w;
+  s.ix = __fdiv_rn(1.0f, s.dx);
+  s.iy = __fdiv_rn(1.0f, s.dy);
+  s.iz = __fdiv_rn(1.0f, s.dz);
+  s.ht = __int_as_float(0x7f800000);
+  s.hu = 0.0f;
+  s.hv = 0.0f;
+  s.hid = -1;
+  s.hpos = -1;
+  s.ntest = 0;
+  s.ttest = 0;
+  s.sp = 0;
+  s.cur = p.root_slot;
+  s.have = p.has_root != 0;
+}
+
+// One traversal step of one ray: either the triangles of one leaf or one
+// inner node, then a pop if nothing is left to visit.  Returns true when the
+// ray has finished (or was stopped by a recorded device error).
+template <int R, int CULL, int MODE, int LUTV, int SCALES>
+__device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* stack,
+                                           const SmemLut<(R > 0 ? R : 4)>& slut) {
+  constexpr int RR = (R > 0 ? R : 4);
+  constexpr int R3 = RR * RR * RR;
+  constexpr int MB = MaskTraits<RR>::kStrideBytes;
+  bool done = false;
+  if (s.have) {
+    if (s.cur & kLeaf) {
+      const int first = (int)(s.cur & 0x0FFFFFFFu);
+      const int cnt = (int)((s.cur >> 28) & 7u) + 1;
+      for (int i = 0; i < cnt; ++i) {
+        const float4* tp = p.tris + 3 * (long long)(first + i);
+        const float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
+        ++s.ttest;
+        float t, u, v;
+        if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
+          s.ht = t;
+          s.hu = u;
+          s.hv = v;
+          s.hid = __float_as_int(A.w);
+          s.hpos = first + i;
+          if (MODE == 1) {
+            done = true;
+            break;
+          }
+          s.tcur = t;
+        }
+      }
+      s.have = false;
+    } else {
+      const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
+      const float4 f0 = __ldg(nd), f1 = __ldg(nd + 1), f2 = __ldg(nd + 2);
+      const uint4 f3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+      s.ntest += 2;
+      const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
+      const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
+      const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+      float tn[2], tf[2];
+      bool hit[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float* lo = c ? lo1 : lo0;
+        const float* hi = c ? hi1 : hi0;
+        float a0[3], a1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
+          a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
+        }
+        tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
+                      fmaxf(fminf(a0[2], a1[2]), s.tmin));
+        tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
+                      fminf(fmaxf(a0[2], a1[2]), s.tcur));
+        hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
+      }
+      if constexpr (CULL != 0) {
+        const float d[3] = {s.dx, s.dy, s.dz};
+        float sc[2][3];
+        if constexpr (SCALES) {
+          const float4 f4 = __ldg(nd + 4), f5 = __ldg(nd + 5);
+          sc[0][0] = f4.x; sc[0][1] = f4.y; sc[0][2] = f4.z;
+          sc[1][0] = f4.w; sc[1][1] = f5.x; sc[1][2] = f5.y;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const unsigned meta = c ? f3.w : f3.z;
+          if (!hit[c] || (meta & kMetaFull)) continue;
+          const float* lo = c ? lo1 : lo0;
+          const float* hi = c ? hi1 : hi0;
+          int cb[3], ce[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            float sk;
+            if constexpr (SCALES) {
+              sk = sc[c][k];
+            } else {
+              sk = scale_of<RR>(lo[k], hi[k]);
+            }
+            const float p0 = __fadd_rn(o[k], __fmul_rn(tn[c], d[k]));
+            const float p1 = __fadd_rn(o[k], __fmul_rn(tf[c], d[k]));
+            cb[k] = cell_q<RR>(p0, lo[k], sk);
+            ce[k] = cell_q<RR>(p1, lo[k], sk);
+          }
+          const uint8_t* obj;
+          if constexpr (CULL == 1) {
+            obj = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB;
+          } else {
+            obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
+          }
+          if constexpr (LUTV == 0) {
+            const int beg = cb[0] + RR * cb[1] + RR * RR * cb[2];
+            const int end = ce[0] + RR * ce[1] + RR * RR * ce[2];
+            const uint8_t* rm =
+                reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
+            hit[c] = masks_overlap<RR>(rm, obj);
+          } else {
+            hit[c] = overlap_factored<RR>(slut, cb, ce, obj);
+          }
+        }
+      }
+      const uint32_t s0 = f3.x, s1 = f3.y;
+      if ((hit[0] && !slot_ok(s0, (long long)s.cur, p)) ||
+          (hit[1] && !slot_ok(s1, (long long)s.cur, p))) {
+        atomicOr(p.status, (unsigned)ST_BAD_NODE);
+        done = true;
+      } else if (hit[0] && hit[1]) {
+        const int nr = tn[1] < tn[0] ? 1 : 0;
+        if (s.sp < kStack) {
+          stack[s.sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
+          ++s.sp;
+          s.cur = nr ? s1 : s0;
+        } else {
+          atomicOr(p.status, (unsigned)ST_STACK);
+          done = true;
+        }
+      } else if (hit[0]) {
+        s.cur = s0;
+      } else if (hit[1]) {
+        s.cur = s1;
+      } else {
+        s.have = false;
+      }
+    }
+  }
+  if (!done && !s.have) {
+    while (s.sp > 0) {
+      --s.sp;
+      if (__uint_as_float(stack[s.sp].y) > s.tcur) continue;
+      s.cur = stack[s.sp].x;
+      s.have = true;
+      break;
+    }
+    if (!s.have) done = true;
+  }
+  return done;
+}
+
+// Warp-level ray fetch: once at least `refill` lanes are idle (or all are),
+// the warp takes that many ray indices with one atomicAdd; returns the index
+// for this lane (or -1).  `exhausted` turns warp-uniformly true once the
+// counter has passed n.
+__device__ __forceinline__ long long warp_fetch(bool active, unsigned* counter, long long n,
+                                                int refill, bool& exhausted) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned idle = __ballot_sync(0xffffffffu, !active);
+  if (idle == 0u || exhausted || (__popc(idle) < refill && idle != 0xffffffffu)) return -1;
+  const int leader = __ffs(idle) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(counter, (unsigned)__popc(idle));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if ((long long)base + __popc(idle) >= n) exhausted = true;
+  if (active) return -1;
+  const long long r = (long long)base + __popc(idle & ((1u << lane) - 1u));
+  return r < n ? r : -1;
+}
 
 // CULL: 0 plain, 1 uncompressed masks, 2 compressed masks.  MODE: 0 closest,
 // 1 any.  LUTV: 0 full table in global memory (one entry per lookup through
@@ -237,194 +418,234 @@ struct RayState {
 template <int R, int CULL, int MODE, int LUTV, int SCALES>
 __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
   constexpr int RR = (R > 0 ? R : 4);
-  constexpr int R3 = RR * RR * RR;
-  constexpr int MB = MaskTraits<RR>::kStrideBytes;
   __shared__ SmemLut<RR> slut;
   if constexpr (CULL != 0 && LUTV == 1) {
     stage_lut<RR>(slut, p.pair);
     __syncthreads();
   }
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned lt_mask = (1u << lane) - 1u;
   uint2 stack[kStack];
   RayState s;
   s.have = false;
   long long rid = -1;
-  bool active = false;
-  bool exhausted = false;
+  bool active = false, exhausted = false;
   for (;;) {
-    // ---- refill idle lanes with new rays
-    const unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (idle != 0u && !exhausted && (__popc(idle) >= p.refill || idle == 0xffffffffu)) {
-      const int leader = __ffs(idle) - 1;
-      unsigned base = 0;
-      if ((int)lane == leader) base = atomicAdd(&p.work[0], (unsigned)__popc(idle));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if ((long long)base + __popc(idle) >= p.n) exhausted = true;
-      if (!active) {
-        const long long r = (long long)base + __popc(idle & lt_mask);
-        if (r < p.n) {
-          rid = r;
-          active = true;
-          const float4 ra = __ldg(&p.rays[2 * r]);
-          const float4 rb = __ldg(&p.rays[2 * r + 1]);
-          s.ox = ra.x; s.oy = ra.y; s.oz = ra.z; s.tmin = ra.w;
-          s.dx = rb.x; s.dy = rb.y; s.dz = rb.z; s.tcur = rb.w;
-          s.ix = __fdiv_rn(1.0f, s.dx);
-          s.iy = __fdiv_rn(1.0f, s.dy);
-          s.iz = __fdiv_rn(1.0f, s.dz);
-          s.ht = __int_as_float(0x7f800000);
-          s.hu = 0.0f;
-          s.hv = 0.0f;
-          s.hid = -1;
-          s.ntest = 0;
-          s.ttest = 0;
-          s.sp = 0;
-          s.cur = p.root_slot;
-          s.have = p.has_root != 0;
-        }
-      }
+    const long long r = warp_fetch(active, &p.work[0], p.n, p.refill, exhausted);
+    if (r >= 0) {
+      rid = r;
+      active = true;
+      ray_init(s, __ldg(&p.rays[2 * r]), __ldg(&p.rays[2 * r + 1]), p);
     }
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
-    // ---- one traversal step
-    bool done = false;
-    if (s.have) {
-      if (s.cur & kLeaf) {
-        const int first = (int)(s.cur & 0x0FFFFFFFu);
-        const int cnt = (int)((s.cur >> 28) & 7u) + 1;
-        for (int i = 0; i < cnt; ++i) {
-          const float4* tp = p.tris + 3 * (long long)(first + i);
-          const float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
-          ++s.ttest;
-          float t, u, v;
-          if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
-            s.ht = t;
-            s.hu = u;
-            s.hv = v;
-            s.hid = __float_as_int(A.w);
-            if (MODE == 1) {
-              done = true;
-              break;
-            }
-            s.tcur = t;
-          }
-        }
-        s.have = false;
-      } else {
-        const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
-        const float4 f0 = __ldg(nd), f1 = __ldg(nd + 1), f2 = __ldg(nd + 2);
-        const uint4 f3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
-        s.ntest += 2;
-        const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-        const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-        const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
-        float tn[2], tf[2];
-        bool hit[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const float* lo = c ? lo1 : lo0;
-          const float* hi = c ? hi1 : hi0;
-          float a0[3], a1[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
-            a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
-          }
-          tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
-                        fmaxf(fminf(a0[2], a1[2]), s.tmin));
-          tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
-                        fminf(fmaxf(a0[2], a1[2]), s.tcur));
-          hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
-        }
-        if constexpr (CULL != 0) {
-          const float d[3] = {s.dx, s.dy, s.dz};
-          float sc[2][3];
-          if constexpr (SCALES) {
-            const float4 f4 = __ldg(nd + 4), f5 = __ldg(nd + 5);
-            sc[0][0] = f4.x; sc[0][1] = f4.y; sc[0][2] = f4.z;
-            sc[1][0] = f4.w; sc[1][1] = f5.x; sc[1][2] = f5.y;
-          }
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const unsigned meta = c ? f3.w : f3.z;
-            if (!hit[c] || (meta & kMetaFull)) continue;
-            const float* lo = c ? lo1 : lo0;
-            const float* hi = c ? hi1 : hi0;
-            int cb[3], ce[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              float sk;
-              if constexpr (SCALES) {
-                sk = sc[c][k];
-              } else {
-                sk = scale_of<RR>(lo[k], hi[k]);
-              }
-              const float p0 = __fadd_rn(o[k], __fmul_rn(tn[c], d[k]));
-              const float p1 = __fadd_rn(o[k], __fmul_rn(tf[c], d[k]));
-              cb[k] = cell_q<RR>(p0, lo[k], sk);
-              ce[k] = cell_q<RR>(p1, lo[k], sk);
-            }
-            const uint8_t* obj;
-            if constexpr (CULL == 1) {
-              obj = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB;
-            } else {
-              obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
-            }
-            if constexpr (LUTV == 0) {
-              const int beg = cb[0] + RR * cb[1] + RR * RR * cb[2];
-              const int end = ce[0] + RR * ce[1] + RR * RR * ce[2];
-              const uint8_t* rm =
-                  reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
-              hit[c] = masks_overlap<RR>(rm, obj);
-            } else {
-              hit[c] = overlap_factored<RR>(slut, cb, ce, obj);
-            }
-          }
-        }
-        const uint32_t s0 = f3.x, s1 = f3.y;
-        if ((hit[0] && !slot_ok(s0, (long long)s.cur, p)) ||
-            (hit[1] && !slot_ok(s1, (long long)s.cur, p))) {
-          atomicOr(&p.work[1], (unsigned)ST_BAD_NODE);
-          done = true;
-        } else if (hit[0] && hit[1]) {
-          const int nr = tn[1] < tn[0] ? 1 : 0;
-          if (s.sp < kStack) {
-            stack[s.sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
-            ++s.sp;
-            s.cur = nr ? s1 : s0;
-          } else {
-            atomicOr(&p.work[1], (unsigned)ST_STACK);
-            done = true;
-          }
-        } else if (hit[0]) {
-          s.cur = s0;
-        } else if (hit[1]) {
-          s.cur = s1;
-        } else {
-          s.have = false;
-        }
-      }
-    }
-    if (!done && !s.have) {
-      while (s.sp > 0) {
-        --s.sp;
-        if (__uint_as_float(stack[s.sp].y) > s.tcur) continue;
-        s.cur = stack[s.sp].x;
-        s.have = true;
-        break;
-      }
-      if (!s.have) done = true;
-    }
-    if (done) {
+    if (trace_step<R, CULL, MODE, LUTV, SCALES>(p, s, stack, slut)) {
       p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
-      s.have = false;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ waves --
+
+constexpr int kMaxWaves = 5;  // primary + up to 4 bounces
+
+// Control words at the head of the wave workspace (uint32 indices).
+enum {
+  WW_FETCH = 0,        // [0, kMaxWaves): ray counters of each wave
+  WW_SIZE = 8,         // [8, 8 + kMaxWaves): rays appended to each wave
+  WW_STATUS = 16,
+  WW_BAR_COUNT = 24,
+  WW_BAR_GEN = 25,
+  WW_WORDS = 64
+};
+enum { ST_TIMEOUT = 4 };
+
+struct WaveParams {
+  Params p;                    // image, status word (p.work = control words), refill
+  const float4* rays0;         // primary rays
+  long long n0;
+  float4* qrays[2];            // bounce-ray queues (scratch), n0 rays each
+  int* qpath[2];               // path id of each queued ray
+  float4* hits[kMaxWaves];     // per wave: {t, id, u, v}
+  int* path[kMaxWaves];        // per wave: path id (primary ray index)
+  uint2* counts[kMaxWaves];    // per wave, optional
+  int bounces;
+  unsigned seed;
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The
+// wait is bounded: after timeout_ns the block records ST_TIMEOUT and
+// returns false, so a kernel can never hang here.
+__device__ __forceinline__ bool grid_barrier(unsigned* w, unsigned long long timeout_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = &w[WW_BAR_GEN];
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&w[WW_BAR_COUNT], 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&w[WW_BAR_COUNT], 0u);
+      __threadfence();
+      atomicAdd(&w[WW_BAR_GEN], 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        if (global_ns() - t0 > timeout_ns) {
+          atomicOr(&w[WW_STATUS], (unsigned)ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Diffuse bounce ray from a hit (same canonical op sequence as the CPU
+// reference): origin o + t d; geometric normal cross(e1, e2) turned against
+// d and normalised; frame by cross products; unit-disk point by rejection
+// (<= 64 tries, else the centre) lifted to the hemisphere.  Random bits:
+// hash of (seed, path id, bounce, k) after Jarzynski & Olano (JCGT 2020).
+__device__ __forceinline__ unsigned pcg_hash(unsigned v) {
+  const unsigned state = v * 747796405u + 2891336453u;
+  const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+__device__ __forceinline__ bool make_bounce(const RayState& s, const float4 E1, const float4 E2,
+                                            unsigned seed, unsigned path, unsigned bounce,
+                                            float4& r0, float4& r1) {
+  const float px = __fadd_rn(s.ox, __fmul_rn(s.ht, s.dx));
+  const float py = __fadd_rn(s.oy, __fmul_rn(s.ht, s.dy));
+  const float pz = __fadd_rn(s.oz, __fmul_rn(s.ht, s.dz));
+  float nx = __fsub_rn(__fmul_rn(E1.y, E2.z), __fmul_rn(E1.z, E2.y));
+  float ny = __fsub_rn(__fmul_rn(E1.z, E2.x), __fmul_rn(E1.x, E2.z));
+  float nz = __fsub_rn(__fmul_rn(E1.x, E2.y), __fmul_rn(E1.y, E2.x));
+  if (__fadd_rn(__fadd_rn(__fmul_rn(nx, s.dx), __fmul_rn(ny, s.dy)), __fmul_rn(nz, s.dz)) > 0.0f) {
+    nx = -nx; ny = -ny; nz = -nz;
+  }
+  const float l2 = __fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)), __fmul_rn(nz, nz));
+  if (!(l2 > 0.0f)) return false;
+  const float l = __fsqrt_rn(l2);
+  nx = __fdiv_rn(nx, l); ny = __fdiv_rn(ny, l); nz = __fdiv_rn(nz, l);
+  const float ax = fabsf(nx) > 0.9f ? 0.0f : 1.0f, ay = fabsf(nx) > 0.9f ? 1.0f : 0.0f, az = 0.0f;
+  float t1x = __fsub_rn(__fmul_rn(ay, nz), __fmul_rn(az, ny));
+  float t1y = __fsub_rn(__fmul_rn(az, nx), __fmul_rn(ax, nz));
+  float t1z = __fsub_rn(__fmul_rn(ax, ny), __fmul_rn(ay, nx));
+  const float m = __fsqrt_rn(
+      __fadd_rn(__fadd_rn(__fmul_rn(t1x, t1x), __fmul_rn(t1y, t1y)), __fmul_rn(t1z, t1z)));
+  t1x = __fdiv_rn(t1x, m); t1y = __fdiv_rn(t1y, m); t1z = __fdiv_rn(t1z, m);
+  const float t2x = __fsub_rn(__fmul_rn(ny, t1z), __fmul_rn(nz, t1y));
+  const float t2y = __fsub_rn(__fmul_rn(nz, t1x), __fmul_rn(nx, t1z));
+  const float t2z = __fsub_rn(__fmul_rn(nx, t1y), __fmul_rn(ny, t1x));
+  const unsigned key = pcg_hash(pcg_hash(seed ^ (bounce << 24)) + path);
+  float x = 0.0f, y = 0.0f, r2 = 0.0f;
+  for (unsigned k = 0; k < 64; ++k) {
+    const float u1 = __fmul_rn((float)(pcg_hash(key + 2 * k) >> 8), 5.9604644775390625e-08f);
+    const float u2 = __fmul_rn((float)(pcg_hash(key + 2 * k + 1) >> 8), 5.9604644775390625e-08f);
+    const float xx = __fsub_rn(__fmul_rn(2.0f, u1), 1.0f);
+    const float yy = __fsub_rn(__fmul_rn(2.0f, u2), 1.0f);
+    const float rr = __fadd_rn(__fmul_rn(xx, xx), __fmul_rn(yy, yy));
+    if (rr < 1.0f) {
+      x = xx; y = yy; r2 = rr;
+      break;
+    }
+  }
+  const float z = __fsqrt_rn(__fsub_rn(1.0f, r2));
+  r0 = make_float4(px, py, pz, 1e-4f);
+  r1 = make_float4(__fadd_rn(__fadd_rn(__fmul_rn(x, t1x), __fmul_rn(y, t2x)), __fmul_rn(z, nx)),
+                   __fadd_rn(__fadd_rn(__fmul_rn(x, t1y), __fmul_rn(y, t2y)), __fmul_rn(z, ny)),
+                   __fadd_rn(__fadd_rn(__fmul_rn(x, t1z), __fmul_rn(y, t2z)), __fmul_rn(z, nz)),
+                   __int_as_float(0x7f800000));
+  return true;
+}
+
+// All waves in one cooperative persistent launch: wave 0 traces the primary
+// rays; every hit of wave w < bounces appends its bounce ray to the queue of
+// wave w + 1 (warp-aggregated atomicAdd, so the queue holds only spawned
+// rays: compacted); a bounded grid barrier separates the waves.
+template <int R, int CULL, int LUTV, int SCALES>
+__global__ void __launch_bounds__(kBlock) waves_kernel(WaveParams wp) {
+  constexpr int RR = (R > 0 ? R : 4);
+  __shared__ SmemLut<RR> slut;
+  const Params& p = wp.p;
+  if constexpr (CULL != 0 && LUTV == 1) {
+    stage_lut<RR>(slut, p.pair);
+    __syncthreads();
+  }
+  const unsigned lane = threadIdx.x & 31u;
+  uint2 stack[kStack];
+  for (int w = 0; w <= wp.bounces; ++w) {
+    const long long n =
+        (w == 0) ? wp.n0 : (long long)(*(volatile unsigned*)&p.work[WW_SIZE + w]);
+    const float4* rays = (w == 0) ? wp.rays0 : wp.qrays[w & 1];
+    const int* qpath = (w == 0) ? nullptr : wp.qpath[w & 1];
+    RayState s;
+    s.have = false;
+    long long rid = -1;
+    bool active = false, exhausted = false;
+    for (;;) {
+      const long long r = warp_fetch(active, &p.work[WW_FETCH + w], n, p.refill, exhausted);
+      if (r >= 0) {
+        rid = r;
+        active = true;
+        // queued rays were written by other SMs in this launch: read them
+        // through L2 (ld.global.cg), never through the read-only / L1 path
+        ray_init(s, __ldcg(&rays[2 * r]), __ldcg(&rays[2 * r + 1]), p);
+      }
+      if (!__any_sync(0xffffffffu, active)) break;
+      const bool done = active && trace_step<R, CULL, 0, LUTV, SCALES>(p, s, stack, slut);
+      if (!__any_sync(0xffffffffu, done)) continue;
+      bool spawn = false;
+      float4 b0, b1;
+      unsigned pid = 0;
+      if (done) {
+        pid = qpath ? (unsigned)__ldcg(&qpath[rid]) : (unsigned)rid;
+        wp.hits[w][rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+        if (wp.path[w]) wp.path[w][rid] = (int)pid;
+        if (wp.counts[w]) wp.counts[w][rid] = make_uint2(s.ntest, s.ttest);
+        if (w < wp.bounces && s.hid >= 0) {
+          const float4* tp = p.tris + 3 * (long long)s.hpos;
+          spawn = make_bounce(s, __ldg(tp + 1), __ldg(tp + 2), wp.seed, pid, (unsigned)(w + 1),
+                              b0, b1);
+        }
+        active = false;
+      }
+      const unsigned sm = __ballot_sync(0xffffffffu, spawn);
+      if (sm) {
+        const int leader = __ffs(sm) - 1;
+        unsigned base = 0;
+        if ((int)lane == leader) base = atomicAdd(&p.work[WW_SIZE + w + 1], (unsigned)__popc(sm));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (spawn) {
+          const unsigned pos = base + __popc(sm & ((1u << lane) - 1u));
+          float4* q = wp.qrays[(w + 1) & 1];
+          q[2 * pos] = b0;
+          q[2 * pos + 1] = b1;
+          wp.qpath[(w + 1) & 1][pos] = (int)pid;
+        }
+      }
+    }
+    if (w < wp.bounces) {
+      __threadfence();
+      if (!grid_barrier(p.work, wp.timeout_ns)) return;
     }
   }
 }
 
 typedef void (*KernelFn)(Params);
+typedef void (*WaveKernelFn)(WaveParams);
 
 }  // namespace sct

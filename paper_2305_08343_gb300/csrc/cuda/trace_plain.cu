@@ -8,4 +8,6 @@ KernelFn get_kernel_plain(int mode) {
   return mode ? trace_kernel<0, 0, 1, 0, 0> : trace_kernel<0, 0, 0, 0, 0>;
 }
 
+WaveKernelFn get_waves_plain() { return waves_kernel<0, 0, 0, 0>; }
+
 }  // namespace sct

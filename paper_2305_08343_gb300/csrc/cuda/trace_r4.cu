@@ -1,6 +1,7 @@
 // trace_r4.cu — culled traversal variants for R = 4 (object masks of
 // 4^3 bits): {uncompressed, compressed} x {closest, any} x {global table,
-// shared-memory factored table} x {scales divided, scales stored}.
+// shared-memory factored table} x {scales divided, scales stored}; and the
+// wave pipeline kernels (global table).
 #include "trace_kernel.cuh"
 
 namespace sct {
@@ -13,5 +14,12 @@ KernelFn get_kernel_r4(int cull, int mode, int lutv, int scales) {
   return table[cull - 1][mode][lutv][scales];
 }
 #undef SCT_V
+
+WaveKernelFn get_waves_r4(int cull, int scales) {
+  static const WaveKernelFn table[2][2] = {
+      {waves_kernel<4, 1, 0, 0>, waves_kernel<4, 1, 0, 1>},
+      {waves_kernel<4, 2, 0, 0>, waves_kernel<4, 2, 0, 1>}};
+  return table[cull - 1][scales];
+}
 
 }  // namespace sct

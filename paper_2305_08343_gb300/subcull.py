@@ -53,6 +53,13 @@ class sc_bvh_info(C.Structure):
                 ("ms_bvh", C.c_double), ("ms_masks", C.c_double), ("ms_compress", C.c_double)]
 
 
+class sc_wave_out(C.Structure):
+    _fields_ = [("hits", C.c_void_p), ("path", C.c_void_p), ("counts", C.c_void_p)]
+
+
+SC_MAX_BOUNCES = 4
+
+
 class sc_trace_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int),
                 ("refill", C.c_int)]
@@ -95,6 +102,10 @@ def lib():
             "sc_status_poll": (C.c_int, [vp, vp]),
             "sc_trace_noalloc": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, C.c_int,
                                            P(sc_trace_opts), vp]),
+            "sc_trace_waves_workspace_bytes": (C.c_size_t, [i64]),
+            "sc_trace_waves": (C.c_int, [vp, vp, i64, C.c_int, C.c_uint32, C.c_int,
+                                         P(sc_wave_out), P(sc_trace_opts), vp, C.c_size_t, vp]),
+            "sc_waves_poll": (C.c_int, [vp, C.c_int, u32p, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -332,3 +343,63 @@ def split_hits(hits):
     h = hits.cpu().numpy() if hasattr(hits, "cpu") else np.asarray(hits)
     h = np.ascontiguousarray(h, dtype=np.float32)
     return h[:, 0], h[:, 1].view(np.int32), h[:, 2], h[:, 3]
+
+
+# ------------------------------------------------------------------ waves --
+
+def sc_trace_waves_workspace_bytes(n0: int) -> int:
+    return int(lib().sc_trace_waves_workspace_bytes(n0))
+
+
+def sc_trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, outs, ws,
+                   opts: sc_trace_opts | None = None, stream=None):
+    """outs: list of bounces+1 (hits float32[n0,4], path int32[n0] | None,
+    counts int32[n0,2] | None) device tensors; ws: uint8 device tensor."""
+    n0 = rays.shape[0]
+    arr = (sc_wave_out * (bounces + 1))()
+    for w, (h, pth, cnt) in enumerate(outs):
+        arr[w].hits = h.data_ptr()
+        arr[w].path = pth.data_ptr() if pth is not None else None
+        arr[w].counts = cnt.data_ptr() if cnt is not None else None
+    o = opts or _opts()
+    _check(lib().sc_trace_waves(dbvh.handle, C.c_void_p(rays.data_ptr()), n0, bounces,
+                                seed & 0xFFFFFFFF, cull, arr, C.byref(o),
+                                C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+
+
+def sc_waves_poll(ws, bounces: int, stream=None):
+    sizes = np.zeros(bounces + 1, np.uint32)
+    _check(lib().sc_waves_poll(C.c_void_p(ws.data_ptr()), bounces, _ptr(sizes, C.c_uint32),
+                               _stream_ptr(stream)))
+    return sizes
+
+
+class WaveBuffers:
+    """Device outputs and workspace for sc_trace_waves (torch-owned)."""
+
+    def __init__(self, n0: int, bounces: int, with_counts: bool = True, device="cuda"):
+        import torch
+        self.n0, self.bounces = n0, bounces
+        self.hits = [torch.empty((n0, 4), dtype=torch.float32, device=device)
+                     for _ in range(bounces + 1)]
+        self.path = [torch.empty(n0, dtype=torch.int32, device=device) for _ in range(bounces + 1)]
+        self.counts = [torch.empty((n0, 2), dtype=torch.int32, device=device) if with_counts
+                       else None for _ in range(bounces + 1)]
+        nb = sc_trace_waves_workspace_bytes(n0)
+        # 256-byte aligned view into a slightly larger buffer
+        self._raw = torch.empty(nb + 256, dtype=torch.uint8, device=device)
+        off = (-self._raw.data_ptr()) % 256
+        self.ws = self._raw[off:off + nb]
+
+    def outs(self):
+        return list(zip(self.hits, self.path, self.counts))
+
+
+def trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, buffers=None,
+                opts=None, stream=None):
+    """Runs the wave pipeline; returns (buffers, wave sizes)."""
+    b = buffers or WaveBuffers(rays.shape[0], bounces, device=rays.device)
+    sc_trace_waves(dbvh, rays, bounces, seed, cull, b.outs(), b.ws, opts, stream)
+    sizes = sc_waves_poll(b.ws, bounces, stream)
+    sizes[0] = rays.shape[0]
+    return b, sizes

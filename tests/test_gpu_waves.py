@@ -1,0 +1,98 @@
+"""The wave pipeline (primary rays + diffuse bounce waves in one cooperative
+launch) against the CPU oracle: the oracle traces the primaries, spawns the
+bounce rays of every hit with the same generator (keyed by path id) and
+traces them; the GPU waves, keyed by path id, must hold the same rays'
+results: hit ids and per-ray counts exact, t within 1e-6 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_08343_gb300 import scenegen as sg
+from paper_2305_08343_gb300 import subcull as sc
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _oracle_waves(tris, rays, bounces, seed, R, comp, cull):
+    ob = oracle.OracleBVH(tris)
+    if R:
+        ob.build_masks(R, 3)
+        if comp:
+            ob.compress(256, 8)
+    mode = (2 if comp else 1) if cull else 0
+    waves = []
+    cur, path = rays, np.arange(len(rays))
+    for w in range(bounces + 1):
+        o = ob.trace(cur, 0, mode)
+        waves.append(dict(path=path, **o))
+        if w < bounces:
+            cur, path = oracle.bounce_wave(cur, o["t"], o["id"], tris, seed, w + 1, path)
+    return waves
+
+
+def _gpu_waves(tris, rays, bounces, seed, R, comp, cull):
+    b = sc.sc_bvh_build(tris, R, comp)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED if cull else sc.SC_LAYOUT_PLAIN)
+    r = torch.from_numpy(rays).cuda()
+    bufs, sizes = sc.trace_waves(d, r, bounces, seed, cull)
+    torch.cuda.synchronize()
+    out = []
+    for w in range(bounces + 1):
+        m = int(sizes[w])
+        t, i, u, v = sc.split_hits(bufs.hits[w][:m])
+        path = bufs.path[w][:m].cpu().numpy()
+        cnt = bufs.counts[w][:m].cpu().numpy().view(np.uint32)
+        order = np.argsort(path, kind="stable")
+        out.append(dict(path=path[order], t=t[order], id=i[order], counts=cnt[order]))
+    return out
+
+
+@pytest.mark.parametrize("cull,comp", [(0, 0), (1, 0), (1, 1)])
+def test_waves_match_oracle(cull, comp):
+    tris = sg.hair(400, 16, True, seed=31)
+    rays = sg.pinhole(64, 48)
+    g = _gpu_waves(tris, rays, 2, 1234, 6, comp, cull)
+    o = _oracle_waves(tris, rays, 2, 1234, 6, comp, cull)
+    for w in range(3):
+        op = o[w]["path"]
+        assert np.array_equal(g[w]["path"], np.sort(op)), f"wave {w}: different rays"
+        order = np.argsort(op, kind="stable")
+        assert np.array_equal(g[w]["id"], o[w]["id"][order]), f"wave {w}: hit ids differ"
+        assert np.array_equal(g[w]["counts"], o[w]["counts"][order]), f"wave {w}: counts differ"
+        assert np.array_equal(g[w]["t"], o[w]["t"][order])
+    assert len(o[1]["path"]) > 100 and len(o[2]["path"]) > 10
+
+
+def test_waves_culled_equals_plain_and_sizes():
+    tris = sg.hair(800, 16, True, seed=32)
+    rays = sg.pinhole(96, 64)
+    a = _gpu_waves(tris, rays, 3, 99, 6, 1, 1)
+    b = _gpu_waves(tris, rays, 3, 99, 6, 1, 0)
+    for w in range(4):
+        assert np.array_equal(a[w]["path"], b[w]["path"])
+        assert np.array_equal(a[w]["id"], b[w]["id"]) and np.array_equal(a[w]["t"], b[w]["t"])
+        assert (a[w]["counts"] <= b[w]["counts"]).all()
+    # each wave is compacted: only hits of the previous wave spawn rays
+    for w in range(1, 4):
+        assert len(a[w]["path"]) == int((b[w - 1]["id"] >= 0).sum())
+
+
+def test_waves_edge_cases():
+    tris = sg.hair(50, 16, False, seed=33)
+    b = sc.sc_bvh_build(tris, 6, 0)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    # no bounces: same as a plain trace
+    rays = sg.pinhole(40, 24)
+    r = torch.from_numpy(rays).cuda()
+    bufs, sizes = sc.trace_waves(d, r, 0, 1, 1)
+    h, c = sc.trace(d, r, 0, 1)
+    assert torch.equal(bufs.hits[0].view(torch.int32), h.view(torch.int32))
+    # rays that all miss: empty bounce waves
+    miss = rays.copy()
+    miss[:, 4:7] = [0, 1, 0]
+    miss[:, :3] = [0, 5, 0]
+    bufs, sizes = sc.trace_waves(d, torch.from_numpy(miss).cuda(), 2, 1, 1)
+    assert sizes.tolist() == [len(miss), 0, 0]
+    with pytest.raises(sc.SubcullError):
+        sc.trace_waves(d, r, sc.SC_MAX_BOUNCES + 1, 1, 1)
