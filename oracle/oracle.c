@@ -903,8 +903,11 @@ typedef struct {
  * child order nor pop rule): the root box is not tested; visiting an inner
  * node costs two slab tests (node_tests += 2); if both children survive, the
  * one with the smaller entry distance is visited next (tie: child 0) and the
- * other is pushed with its entry distance; a popped entry whose entry
- * distance exceeds the current closest hit is dropped without a test; leaf
+ * other is pushed with its entry distance; a popped entry is dropped
+ * without a test unless it would still pass the (widened) slab test, i.e.
+ * unless tn <= tcur * (1 + 2 gamma_3) -- the same bound the slab test uses,
+ * so a child is kept or dropped the same way whether it is reached directly
+ * or through the stack; leaf
  * triangles are tested in order (tri_tests += 1 each).  Any-hit stops at the
  * first accepted triangle.
  */
@@ -970,7 +973,7 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
     }
     while (sp > 0) {
       --sp;
-      if (stack[sp].tn > tcur) continue;
+      if (stack[sp].tn > tcur * ROBUST) continue;
       cur_child = stack[sp].child;
       cur_count = stack[sp].count;
       have = 1;

@@ -14,8 +14,8 @@
 // mask of the (begin, end) cell pair is looked up, and the child survives
 // iff the AND with its object mask is non-zero (Alg. 4).  Order: if both
 // children survive, the one with the smaller entry distance is visited next
-// and the other is pushed with its entry distance; a popped entry whose
-// distance exceeds the current closest hit is dropped.
+// and the other is pushed with its entry distance; a popped entry is dropped
+// unless it would still pass the widened slab test (tn <= tcur * kRobust).
 //
 // Every floating-point test op is an explicit round-to-nearest intrinsic
 // (__fadd_rn, __fmul_rn, ...), so no multiply-add contraction can change a
@@ -382,7 +382,9 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
   if (!done && !s.have) {
     while (s.sp > 0) {
       --s.sp;
-      if (__uint_as_float(stack[s.sp].y) > s.tcur) continue;
+      // same widened bound as the slab test: a child is kept or dropped
+      // alike whether it is reached directly or through the stack
+      if (__uint_as_float(stack[s.sp].y) > __fmul_rn(s.tcur, kRobust)) continue;
       s.cur = stack[s.sp].x;
       s.have = true;
       break;
