@@ -118,7 +118,7 @@ def cpu_count():
         return os.cpu_count() or 1
 
 
-def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s):
+def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, stride=1):
     """Times the oracle's traversal (threads split the rays statically) on a
     sample of rays sized to roughly budget_s seconds of CPU time."""
     import oracle  # noqa: F401  (the oracle package; CPU baseline only)
@@ -126,7 +126,7 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s):
     # calibrate on a small sample
     m = min(n, 512)
     t0 = time.perf_counter()
-    ob.trace(rays[:m], 0, cull)
+    ob.trace(rays[:m], 0, cull, skip_bits=skip_bits, stride=stride)
     per_ray = (time.perf_counter() - t0) / m
     sample = int(min(n, max(threads * 256, budget_s * threads / max(per_ray, 1e-9))))
     idx = np.linspace(0, n - 1, sample).astype(np.int64)
@@ -136,7 +136,7 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s):
                mask_tests=np.zeros(sample, np.uint32))
     bounds = np.linspace(0, sample, threads + 1).astype(np.int64)
     ts = [threading.Thread(target=ob.trace, args=(sub, 0, cull, int(bounds[i]),
-                                                   int(bounds[i + 1]), out))
+                                                   int(bounds[i + 1]), out, skip_bits, stride))
           for i in range(threads)]
     t0 = time.perf_counter()
     for t in ts:
@@ -231,9 +231,12 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     desc, tris, rays_np, R, comp = make_inputs(args.workload)
+    if args.R:
+        R = args.R
     bounces = args.bounces if args.bounces >= 0 else WORKLOAD_BOUNCES.get(args.workload, 1)
     t0 = time.perf_counter()
-    bvh = sc.sc_bvh_build(tris, R, comp)
+    bvh = sc.sc_bvh_build(tris, R, comp, skip_bits=args.skip_bits, L=args.L,
+                          test_stride=args.stride)
     build_s = time.perf_counter() - t0
     info = bvh.info()
     d_masked = sc.DeviceBVH(bvh, args.layout)
@@ -242,6 +245,18 @@ def run_gpu(args):
     rays = torch.from_numpy(rays_np).to(dev)
     opts = sc._opts(lut_mode=args.lut, refill=args.refill)
     seed = 2305
+    if args.primary_only:
+        # a few single-batch traces (culled, then plain) and nothing else:
+        # the command used for ncu captures of trace_kernel
+        hits = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
+        for dbvh, cull in ((d_masked, 1), (d_plain, 0)):
+            for _ in range(max(1, args.steps)):
+                sc.sc_trace(dbvh, rays, hits, None, 0, cull, work, opts)
+        sc.sc_status_poll(work)
+        torch.cuda.synchronize()
+        print(json.dumps({"primary_only": True, "workload": args.workload, "rays": n}))
+        return 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
@@ -326,7 +341,8 @@ def run_gpu(args):
     work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     prim = {}
-    for name, dbvh, cull in (("culled", d_masked, 1), ("plain", d_plain, 0)):
+    for name, dbvh, cull in (("culled", d_masked, 1), ("plain", d_plain, 0),
+                             ("plain_kernel_on_masked_image", d_masked, 0)):
         for _ in range(2):
             sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, opts)
         flush.zero_()
@@ -379,13 +395,14 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
-        ob = oracle.OracleBVH(tris).build_masks(R, 3)
+        ob = oracle.OracleBVH(tris).build_masks(R, args.L)
         cull_mode = 1
         if comp:
             ob.compress(256, 8)
             cull_mode = 2
         thr = cpu_count()
-        v, sample, dt, _ = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0)
+        v, sample, dt, _ = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0,
+                                             args.skip_bits or R ** 3, args.stride)
         cpu = {"value": v / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{sample} primary rays evenly spaced over the {n}, culled closest hit, "
                          f"{dt:.1f} s on {thr} threads (oracle's own BVH and masks)"}
@@ -398,8 +415,9 @@ def run_gpu(args):
         "config": {"workload": args.workload, "description": desc, "primary_rays": n,
                    "bounces": bounces, "rays_per_step": rays_per_step,
                    "wave_sizes": [int(x) for x in sizes], "grid_res": R,
-                   "compressed": bool(comp), "L": 3, "lut_mode": args.lut,
+                   "compressed": bool(comp), "L": args.L, "lut_mode": args.lut,
                    "layout": args.layout, "refill": args.refill,
+                   "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -437,6 +455,14 @@ def main():
     ap.add_argument("--refill", type=int, default=0, help="idle lanes before a warp refills")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bounces", type=int, default=-1, help="bounce waves (-1: workload's)")
+    ap.add_argument("--R", type=int, default=0, help="mask resolution (0: workload's)")
+    ap.add_argument("--L", type=int, default=3, help="mask approximation depth (Sec. 3.2.1)")
+    ap.add_argument("--stride", type=int, default=1,
+                    help="test inner children only at depths that are multiples of this")
+    ap.add_argument("--primary-only", action="store_true",
+                    help="only a few single-batch traces (for ncu captures)")
+    ap.add_argument("--skip-bits", type=int, default=0,
+                    help="keep children with >= this many mask bits untested (0: R^3)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

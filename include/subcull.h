@@ -102,6 +102,13 @@ typedef struct {
   int chunk_bits; /* requirement-LUT chunk b (Sec. 3.2.3), default 8        */
   double eps_rel; /* voxel dilation / max(1, |scene coord|), default 2^-16  */
   int threads;    /* host threads, 0 = all                                  */
+  int skip_bits;  /* device images: children whose (decoded) mask has at
+                     least this many bits set are kept without a mask test;
+                     0 = R^3 (only all-ones masks, whose test cannot fail:
+                     the paper's method).  Any value gives the same hits. */
+  int test_stride; /* device images: inner children are tested only at
+                      depths that are multiples of this (0 or 1 = every
+                      level, the paper's method); leaves are always tested */
 } sc_build_opts;
 
 void sc_build_opts_default(sc_build_opts* o);
@@ -165,7 +172,8 @@ typedef struct sc_dbvh sc_dbvh;
    into d_buf: device memory of >= nbytes bytes, 256-byte aligned, owned by
    the caller.  The image holds 16-B aligned nodes (fetched with 128-bit
    loads), 48-B triangles {v0,id}{e1}{e2} in leaf order, the ray-mask
-   tables and the compression LUT.  *out is a host-side view of d_buf;
+   tables, the compression LUT and (compressed) the bit table of every ray
+   mask against every LUT entry.  *out is a host-side view of d_buf;
    destroying it does not touch d_buf. */
 sc_status sc_bvh_upload(const sc_bvh* b, int layout, void* d_buf, size_t nbytes,
                         void* stream, sc_dbvh** out);
@@ -180,14 +188,19 @@ typedef struct {
 
 enum { SC_CLOSEST = 0, SC_ANY = 1 };
 
-enum { SC_LUT_AUTO = 0, SC_LUT_GLOBAL = 1, SC_LUT_SHARED = 2 };
+enum { SC_LUT_AUTO = 0, SC_LUT_GLOBAL = 1, SC_LUT_SHARED = 2, SC_LUT_BITTABLE = 3 };
 
 typedef struct {
   int block;         /* threads per block: 0 (= 128) or 128               */
   int blocks_per_sm; /* persistent blocks per SM, 0 = occupancy maximum    */
   int lut_mode;      /* ray-mask lookup: SC_LUT_GLOBAL = full table through
-                        L1/L2; SC_LUT_SHARED = factored tables in shared
-                        memory; SC_LUT_AUTO picks per resolution          */
+                        L1/L2; SC_LUT_SHARED = shared memory (R = 4: the
+                        whole 32-KB table and the LUT; R = 6, 8: factored
+                        per-axis-pair tables, single-batch traces only);
+                        SC_LUT_BITTABLE (compressed images) = the
+                        precomputed bit table of Sec. 3.2.2, one bit per
+                        (ray mask, LUT entry); SC_LUT_AUTO = bit table when
+                        compressed, else the full table                    */
   int refill;        /* a warp fetches new rays once this many of its lanes
                         are idle (1..32), 0 = default                     */
 } sc_trace_opts;

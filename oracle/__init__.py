@@ -82,11 +82,13 @@ def lib():
             "or_bvh_compress": (C.c_int, [vp, C.c_int, C.c_int]),
             "or_bvh_get_clut": (None, [vp, _P(u32), _P(u8)]),
             "or_trace_range": (C.c_int, [vp, _P(f), _P(f), i64, i64, C.c_int, C.c_int,
-                                         _P(f), _P(i32), _P(f), _P(u32), _P(u32)]),
+                                         C.c_int, C.c_int, _P(f), _P(i32), _P(f), _P(u32),
+                                         _P(u32)]),
             "or_brute": (None, [_P(f), i64, _P(f), i64, C.c_int, _P(f), _P(i32), _P(f)]),
             "or_ray_tri": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f), _P(f)]),
             "or_slab": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f)]),
             "or_cell": (C.c_int, [f, f, f, C.c_int]),
+            "or_cell_t": (C.c_int, [f, f, f, f, f, C.c_int]),
             "or_pcg_hash": (u32, [u32]),
             "or_bounce_hash": (u32, [u32, u32, u32, u32]),
             "or_bounce": (C.c_int, [_P(f), f, _P(f), u32, u32, u32, _P(f)]),
@@ -264,9 +266,15 @@ class OracleBVH:
         return c[: self.K], idx[: self.num_nodes]
 
     def trace(self, rays: np.ndarray, mode: int = 0, cull: int = 0,
-              r_begin: int = 0, r_end: int | None = None, out=None):
+              r_begin: int = 0, r_end: int | None = None, out=None, skip_bits: int | None = None,
+              stride: int = 1):
         """Alg. 4.  cull: 0 plain, 1 uncompressed masks, 2 compressed masks.
+        skip_bits: children whose mask has at least this many bits set are
+        kept untested (default R^3: only all-ones masks); stride: inner
+        children are tested only at depths that are multiples of it.
         Returns dict(t, id, uv, counts[n,2], mask_tests)."""
+        if skip_bits is None:
+            skip_bits = max(self.R, 1) ** 3
         rays = _f32(rays).reshape(-1, 8)
         n = rays.shape[0]
         r_end = n if r_end is None else r_end
@@ -276,7 +284,8 @@ class OracleBVH:
                        counts=np.zeros((n, 2), np.uint32),
                        mask_tests=np.zeros(n, np.uint32))
         rc = lib().or_trace_range(self._h, _ptr(self.tris, C.c_float), _ptr(rays, C.c_float),
-                                  r_begin, r_end, mode, cull, _ptr(out["t"], C.c_float),
+                                  r_begin, r_end, mode, cull, skip_bits, stride,
+                                  _ptr(out["t"], C.c_float),
                                   _ptr(out["id"], C.c_int32), _ptr(out["uv"], C.c_float),
                                   _ptr(out["counts"], C.c_uint32),
                                   _ptr(out["mask_tests"], C.c_uint32))
@@ -321,6 +330,10 @@ def slab(ray8, box6, tcur=np.inf):
 
 def cell(p: float, lo: float, hi: float, R: int) -> int:
     return int(lib().or_cell(float(p), float(lo), float(hi), R))
+
+
+def cell_t(t: float, o: float, d: float, lo: float, hi: float, R: int) -> int:
+    return int(lib().or_cell_t(float(t), float(o), float(d), float(lo), float(hi), R))
 
 
 # -------------------------------------------------------------- bounce rays --

@@ -421,6 +421,7 @@ struct OrBvh {
   int32_t* count; /* [nn][2] */
   float* box;     /* [nn][2][6] */
   int32_t* perm;  /* [ntri] */
+  int32_t* ndepth; /* [nn] depth of the slot each node fills (root node 0) */
   int max_depth;
   /* masks */
   int R, L, W;
@@ -469,6 +470,7 @@ static int64_t new_node(OrBvh* b) {
     b->child = (int32_t*)realloc(b->child, sizeof(int32_t) * 2 * b->cap);
     b->count = (int32_t*)realloc(b->count, sizeof(int32_t) * 2 * b->cap);
     b->box = (float*)realloc(b->box, sizeof(float) * 12 * b->cap);
+    b->ndepth = (int32_t*)realloc(b->ndepth, sizeof(int32_t) * b->cap);
   }
   return b->nnodes++;
 }
@@ -571,6 +573,7 @@ static void build_range(BuildCtx* x, int64_t begin, int64_t end, int depth,
     mid = begin + n / 2;
   }
   int64_t node = new_node(b);
+  b->ndepth[node] = depth;
   *s_child = (int32_t)node;
   *s_count = 0;
   int32_t c0, n0, c1, n1;
@@ -624,6 +627,7 @@ void or_bvh_free(OrBvh* b) {
   free(b->clut);
   free(b->cidx);
   free(b->raylut);
+  free(b->ndepth);
   free(b);
 }
 
@@ -872,18 +876,33 @@ int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
 }
 
 /* Culling test of one child (Sec. 3.1.2 and the red part of Alg. 4): the
-   clipped segment's ends p0 = o + tn*d and p1 = o + tf*d are turned into
-   cells (Alg. 1), the ray mask is looked up, and the child survives iff the
-   AND with its object mask is non-zero. */
+   clipped segment's ends at tn and tf are turned into cells (Alg. 1, see
+   or_cell_t), the ray mask is looked up, and the child survives iff the AND
+   with its object mask is non-zero. */
+/* Cell of the point at parameter t on axis k.  Alg. 1 maps p = o + t d to
+   floor(R/extent * (p - lower)); the traversal evaluates the same quantity
+   in the ray parameter, q(t) = s (o - lower) + t (s d) with s = R / extent,
+   as one fused multiply-add (one rounding): fmaf(t, s*d, s*(o - lower)).
+   Clamped to [0, R-1] like or_cell.  The eps dilation of the object masks
+   absorbs the difference in rounding. */
+int or_cell_t(float t, float o, float d, float lo, float hi, int R) {
+  float ext = hi - lo;
+  float s = (float)R / fmaxf(ext, 1e-30f);
+  float q = fmaf(t, d * s, (o - lo) * s);
+  q = fminf(fmaxf(q, -1.0f), (float)R);
+  int i = (int)floorf(q);
+  if (i < 0) i = 0;
+  if (i > R - 1) i = R - 1;
+  return i;
+}
+
 static int cull_pass(const OrBvh* b, const ORay* r, const float* bx, float tn,
                      float tf, const uint32_t* objmask) {
   int R = b->R, W = b->W, R3 = R * R * R;
   int cb[3], ce[3];
   for (int k = 0; k < 3; ++k) {
-    float p0 = r->o[k] + tn * r->d[k];
-    float p1 = r->o[k] + tf * r->d[k];
-    cb[k] = or_cell(p0, bx[k], bx[3 + k], R);
-    ce[k] = or_cell(p1, bx[k], bx[3 + k], R);
+    cb[k] = or_cell_t(tn, r->o[k], r->d[k], bx[k], bx[3 + k], R);
+    ce[k] = or_cell_t(tf, r->o[k], r->d[k], bx[k], bx[3 + k], R);
   }
   int beg = cell_bit(R, cb[0], cb[1], cb[2]);
   int end = cell_bit(R, ce[0], ce[1], ce[2]);
@@ -909,10 +928,17 @@ typedef struct {
  * so a child is kept or dropped the same way whether it is reached directly
  * or through the stack; leaf
  * triangles are tested in order (tri_tests += 1 each).  Any-hit stops at the
- * first accepted triangle.
+ * first accepted triangle.  A child whose object mask has at least skip_bits
+ * bits set is kept without a test (skip_bits = R^3: only an all-ones mask,
+ * whose test cannot fail -- the paper's method exactly; smaller values skip
+ * dense masks, which rarely cull), and an inner child at depth d is tested
+ * only when d is a multiple of `stride` (1: every level, the paper's
+ * method).  Skipping a test only keeps a child, so hits are the same for
+ * every setting.
  */
 static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
-                      int mode, int cull, StackEntry* stack, float* hit_t,
+                      int mode, int cull, int skip_bits, int stride, StackEntry* stack,
+                      float* hit_t,
                       int32_t* hit_id, float* hit_uv, uint32_t* counts,
                       uint32_t* mtests) {
   ORay r;
@@ -947,10 +973,12 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
       if (cull) {
         for (int c = 0; c < 2; ++c) {
           if (!hit[c]) continue;
-          ++mtest;
           const uint32_t* om =
               cull == 2 ? b->clut + (size_t)b->cidx[2 * m + c] * b->W
                         : b->masks + ((size_t)m * 2 + c) * b->W;
+          if (popcount_mask(om, b->W) >= skip_bits) continue; /* kept untested */
+          if (b->count[2 * m + c] == 0 && (b->ndepth[m] + 1) % stride != 0) continue;
+          ++mtest;
           hit[c] = cull_pass(b, &r, b->box + 12 * m + 6 * c, tn[c], tf[c], om);
         }
       }
@@ -992,8 +1020,9 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
 
 int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
                    int64_t r_begin, int64_t r_end, int mode, int cull,
-                   float* hit_t, int32_t* hit_id, float* hit_uv,
+                   int skip_bits, int stride, float* hit_t, int32_t* hit_id, float* hit_uv,
                    uint32_t* counts, uint32_t* mask_tests) {
+  if (stride < 1) return -3;
   if (cull && !b->masks) return -1;
   if (cull == 2 && !b->clut) return -2;
   if (cull && !b->raylut) {
@@ -1006,7 +1035,8 @@ int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
   StackEntry* stack =
       (StackEntry*)malloc(sizeof(StackEntry) * (size_t)(b->max_depth + 4));
   for (int64_t i = r_begin; i < r_end; ++i)
-    trace_one(b, tris, rays + 8 * i, mode, cull, stack, hit_t + i, hit_id + i,
+    trace_one(b, tris, rays + 8 * i, mode, cull, skip_bits, stride, stack, hit_t + i,
+              hit_id + i,
               hit_uv + 2 * i, counts + 2 * i, mask_tests ? mask_tests + i : NULL);
   free(stack);
   return 0;
@@ -1015,7 +1045,8 @@ int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
 int or_trace(const OrBvh* b, const float* tris, const float* rays, int64_t n,
              int mode, int cull, float* hit_t, int32_t* hit_id, float* hit_uv,
              uint32_t* counts, uint32_t* mask_tests) {
-  return or_trace_range(b, tris, rays, 0, n, mode, cull, hit_t, hit_id, hit_uv,
+  int R3 = b->R * b->R * b->R;
+  return or_trace_range(b, tris, rays, 0, n, mode, cull, R3, 1, hit_t, hit_id, hit_uv,
                         counts, mask_tests);
 }
 

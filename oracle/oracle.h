@@ -76,11 +76,15 @@ void or_bvh_get_clut(const OrBvh* b, uint32_t* clut, uint8_t* idx);
 int or_trace(const OrBvh* b, const float* tris, const float* rays, int64_t n,
              int mode, int cull, float* hit_t, int32_t* hit_id, float* hit_uv,
              uint32_t* counts, uint32_t* mask_tests);
-/* The same, for rays [r_begin, r_end) only (threads may split the rays). */
+/* The same, for rays [r_begin, r_end) only (threads may split the rays).
+   Test selection: children whose mask has >= skip_bits bits set are kept
+   untested (R^3: only all-ones masks), and inner children are tested only
+   at depths that are multiples of `stride` (1: every level).  skip_bits =
+   R^3 and stride = 1 is the paper's method. */
 int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
                    int64_t r_begin, int64_t r_end, int mode, int cull,
-                   float* hit_t, int32_t* hit_id, float* hit_uv,
-                   uint32_t* counts, uint32_t* mask_tests);
+                   int skip_bits, int stride, float* hit_t, int32_t* hit_id,
+                   float* hit_uv, uint32_t* counts, uint32_t* mask_tests);
 
 /* Brute force over all ray x triangle pairs, same ray-triangle test.
    t2: second smallest accepted t (or +inf), for near-tie detection. */
@@ -101,6 +105,7 @@ int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
 int or_slab(const float* ray8, const float* box6, float tcur, float* tn,
             float* tf);
 int or_cell(float p, float lo, float hi, int R);
+int or_cell_t(float t, float o, float d, float lo, float hi, int R);
 
 #ifdef __cplusplus
 }

@@ -14,9 +14,9 @@ KernelFn get_kernel_r4(int cull, int mode, int lutv, int scales);
 KernelFn get_kernel_r6(int cull, int mode, int lutv, int scales);
 KernelFn get_kernel_r8(int cull, int mode, int lutv, int scales);
 WaveKernelFn get_waves_plain();
-WaveKernelFn get_waves_r4(int cull, int scales);
-WaveKernelFn get_waves_r6(int cull, int scales);
-WaveKernelFn get_waves_r8(int cull, int scales);
+WaveKernelFn get_waves_r4(int cull, int lutv, int scales);
+WaveKernelFn get_waves_r6(int cull, int lutv, int scales);
+WaveKernelFn get_waves_r8(int cull, int lutv, int scales);
 }  // namespace sct
 
 using namespace sc;
@@ -53,6 +53,22 @@ DevInfo device_info() {
   return cache[dev];
 }
 
+// Ray-mask lookup variant: 0 full table (global), 1 shared memory (the full
+// table at R = 4, the factored tables otherwise), 2 bit table (compressed
+// images only).  AUTO: the bit table when compressed, else the full table
+// (shared-memory tables take the L1 capacity the node fetches need).
+int lut_variant(const sc_dbvh* d, int lut_mode) {
+  switch (lut_mode) {
+    case SC_LUT_AUTO: return d->lay.compress ? 2 : 0;
+    case SC_LUT_GLOBAL: return 0;
+    case SC_LUT_SHARED: return 1;
+    case SC_LUT_BITTABLE:
+      if (!d->lay.compress) fail(SC_ERR_ARG, "the bit table needs a compressed image");
+      return 2;
+  }
+  fail(SC_ERR_ARG, "bad lut_mode %d", lut_mode);
+}
+
 sct::KernelFn pick_kernel(const sc_dbvh* d, int mode, int cull, int lutv) {
   if (!cull) return sct::get_kernel_plain(mode);
   int c = d->lay.compress ? 2 : 1;
@@ -85,8 +101,7 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   if (opts) o = *opts;
   if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
-  if (o.lut_mode < SC_LUT_AUTO || o.lut_mode > SC_LUT_SHARED) fail(SC_ERR_ARG, "bad lut_mode");
-  const int lutv = (o.lut_mode == SC_LUT_SHARED) ? 1 : 0;
+  const int lutv = lut_variant(d, o.lut_mode);
   sct::KernelFn k = pick_kernel(d, mode, cull ? 1 : 0, lutv);
   CUDA_OK(cudaMemsetAsync(d_work, 0, kWorkBytes, st));
   if (n == 0) return;
@@ -108,6 +123,7 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   p.lut = d->lay.R ? reinterpret_cast<const uint4*>(base + d->lay.off_lut) : nullptr;
   p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
   p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
+  p.bits = d->lay.compress ? reinterpret_cast<const uint32_t*>(base + d->lay.off_bits) : nullptr;
   p.rays = reinterpret_cast<const float4*>(d_rays);
   p.hits = reinterpret_cast<float4*>(d_hits);
   p.counts = reinterpret_cast<uint2*>(d_counts);
@@ -137,6 +153,7 @@ void fill_params(const sc_dbvh* d, sct::Params& p) {
   p.lut = d->lay.R ? reinterpret_cast<const uint4*>(base + d->lay.off_lut) : nullptr;
   p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
   p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
+  p.bits = d->lay.compress ? reinterpret_cast<const uint32_t*>(base + d->lay.off_bits) : nullptr;
   p.num_nodes = d->nn;
   p.num_tris = d->ntri;
   p.root_slot = d->root_slot;
@@ -171,15 +188,17 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   if (opts) o = *opts;
   if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
+  int lutv = lut_variant(d, o.lut_mode);
+  if (lutv == 1 && d->lay.R != 4) lutv = 0;  // factored tables: single-batch kernel only
   sct::WaveKernelFn k = nullptr;
   if (!cull) {
     k = sct::get_waves_plain();
   } else {
     const int c = d->lay.compress ? 2 : 1, sc = d->lay.scales;
     switch (d->lay.R) {
-      case 4: k = sct::get_waves_r4(c, sc); break;
-      case 6: k = sct::get_waves_r6(c, sc); break;
-      case 8: k = sct::get_waves_r8(c, sc); break;
+      case 4: k = sct::get_waves_r4(c, lutv, sc); break;
+      case 6: k = sct::get_waves_r6(c, lutv, sc); break;
+      case 8: k = sct::get_waves_r8(c, lutv, sc); break;
       default: fail(SC_ERR_UNSUPPORTED, "no wave kernel for R = %d", d->lay.R);
     }
   }

@@ -44,6 +44,7 @@ struct Params {
   const uint4* lut;         // full ray-mask table (mask-stride bytes per entry)
   const uint2* pair;        // factored 2-D table, R^4 x 64 bits
   const uint4* clut;        // compression LUT
+  const uint32_t* bits;     // compressed: [R^6][8] words, bit j of row = ray mask AND LUT entry j
   const float4* rays;       // 2 float4 per ray
   float4* hits;             // {t, id bits, u, v}
   uint2* counts;            // or nullptr
@@ -76,14 +77,13 @@ struct MaskTraits {
   static constexpr int kWords = (R * R * R + 31) / 32;
 };
 
-// Alg. 1 on one axis: min(floor(s * (p - lo)), R-1), clamped at 0, with
-// s = R / max(extent, 1e-30).  The saturating float-to-int conversion
-// (cvt.rmi) gives the same index as clamping q to [-1, R] first.
+// Alg. 1 on one axis, evaluated in the ray parameter: the cell coordinate
+// of o + t d is q = s (o - lo) + t (s d), s = R / max(extent, 1e-30), one
+// fused multiply-add.  The saturating float-to-unsigned conversion (cvt.rmi,
+// negatives and NaN to 0) and a min give floor(q) clamped to [0, R-1].
 template <int R>
-__device__ __forceinline__ int cell_q(float p, float lo, float s) {
-  const float q = __fmul_rn(__fsub_rn(p, lo), s);
-  const int i = __float2int_rd(q);
-  return min(max(i, 0), R - 1);
+__device__ __forceinline__ int cell_of_q(float q) {
+  return (int)min(__float2uint_rd(q), (unsigned)(R - 1));
 }
 
 template <int R>
@@ -122,6 +122,23 @@ struct SmemLut {
   unsigned long long cols[1 << R];  // x-set -> R^2 bits (one per row)
 };
 
+// R = 4 only: the whole ray-mask table (4,096 entries of 64 bits, 32 KB) and
+// the compression LUT (256 x 64 bits) fit in shared memory, so a culling
+// test needs no global-memory lookup on the step's critical path.
+struct SmemFull4 {
+  uint2 lut[4096];
+  uint2 clut[256];
+};
+
+__device__ __forceinline__ void stage_full4(SmemFull4& s, const uint4* lut, const uint4* clut) {
+  const uint2* l = reinterpret_cast<const uint2*>(lut);
+  for (int i = threadIdx.x; i < 4096; i += blockDim.x) s.lut[i] = l[i];
+  if (clut) {
+    const uint2* c = reinterpret_cast<const uint2*>(clut);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s.clut[i] = c[i];
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void stage_lut(SmemLut<R>& s, const uint2* pair) {
   for (int i = threadIdx.x; i < R * R * R * R; i += blockDim.x) {
@@ -138,6 +155,20 @@ __device__ __forceinline__ void stage_lut(SmemLut<R>& s, const uint2* pair) {
     s.cols[m] = c;
   }
 }
+
+// Shared-memory tables of each lookup variant (nothing for the global ones).
+template <int R, int LUTV>
+struct SharedTables {
+  int unused;
+};
+template <int R>
+struct SharedTables<R, 1> {
+  SmemLut<R> f;
+};
+template <>
+struct SharedTables<4, 3> {
+  SmemFull4 full;
+};
 
 // R^2-bit slice z of a dense R^3-bit mask held in W (+1 zero) words.
 template <int R>
@@ -221,6 +252,15 @@ __device__ __forceinline__ bool tri_test(const float4 A, const float4 E1, const 
   return t > tmin && t < tcur;
 }
 
+template <int R, int LUTV>
+__device__ __forceinline__ void stage_tables(SharedTables<R, LUTV>& sh, const Params& p) {
+  if constexpr (LUTV == 1) {
+    stage_lut<R>(sh.f, p.pair);
+  } else if constexpr (LUTV == 3) {
+    stage_full4(sh.full, p.lut, p.clut);
+  }
+}
+
 struct RayState {
   float ox, oy, oz, dx, dy, dz, ix, iy, iz, tmin, tcur;
   float ht, hu, hv;
@@ -256,7 +296,7 @@ __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const flo
 // ray has finished (or was stopped by a recorded device error).
 template <int R, int CULL, int MODE, int LUTV, int SCALES>
 __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* stack,
-                                           const SmemLut<(R > 0 ? R : 4)>& slut) {
+                                           const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
   constexpr int RR = (R > 0 ? R : 4);
   constexpr int R3 = RR * RR * RR;
   constexpr int MB = MaskTraits<RR>::kStrideBytes;
@@ -333,25 +373,44 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
             } else {
               sk = scale_of<RR>(lo[k], hi[k]);
             }
-            const float p0 = __fadd_rn(o[k], __fmul_rn(tn[c], d[k]));
-            const float p1 = __fadd_rn(o[k], __fmul_rn(tf[c], d[k]));
-            cb[k] = cell_q<RR>(p0, lo[k], sk);
-            ce[k] = cell_q<RR>(p1, lo[k], sk);
+            const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk);
+            const float b = __fmul_rn(d[k], sk);
+            cb[k] = cell_of_q<RR>(__fmaf_rn(tn[c], b, a));
+            ce[k] = cell_of_q<RR>(__fmaf_rn(tf[c], b, a));
           }
-          const uint8_t* obj;
-          if constexpr (CULL == 1) {
-            obj = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB;
+          const int beg = cb[0] + RR * cb[1] + RR * RR * cb[2];
+          const int end = ce[0] + RR * ce[1] + RR * RR * ce[2];
+          if constexpr (LUTV == 3) {
+            // R = 4: table and LUT from shared memory
+            const uint2 rm = sh.full.lut[beg * R3 + end];
+            uint2 om;
+            if constexpr (CULL == 1) {
+              om = __ldg(reinterpret_cast<const uint2*>(nd + p.mask_off_f4) + c);
+            } else {
+              om = sh.full.clut[meta & 0xFFu];
+            }
+            hit[c] = ((rm.x & om.x) | (rm.y & om.y)) != 0u;
+          } else if constexpr (CULL == 2 && LUTV == 2) {
+            // Sec. 3.2.2: precomputed bit table (ray-mask row, LUT entry)
+            const unsigned j = meta & 0xFFu;
+            const uint32_t word = __ldg(p.bits + (size_t)(beg * R3 + end) * 8 + (j >> 5));
+            hit[c] = (word >> (j & 31u)) & 1u;
           } else {
-            obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
-          }
-          if constexpr (LUTV == 0) {
-            const int beg = cb[0] + RR * cb[1] + RR * RR * cb[2];
-            const int end = ce[0] + RR * ce[1] + RR * RR * ce[2];
-            const uint8_t* rm =
-                reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
-            hit[c] = masks_overlap<RR>(rm, obj);
-          } else {
-            hit[c] = overlap_factored<RR>(slut, cb, ce, obj);
+            const uint8_t* obj;
+            if constexpr (CULL == 1) {
+              obj = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB;
+            } else {
+              obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
+            }
+            if constexpr (LUTV == 0 || LUTV == 2) {
+              const uint8_t* rm =
+                  reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
+              hit[c] = masks_overlap<RR>(rm, obj);
+            } else {
+              if constexpr (LUTV == 1) {
+                hit[c] = overlap_factored<RR>(sh.f, cb, ce, obj);
+              }
+            }
           }
         }
       }
@@ -415,14 +474,17 @@ __device__ __forceinline__ long long warp_fetch(bool active, unsigned* counter, 
 
 // CULL: 0 plain, 1 uncompressed masks, 2 compressed masks.  MODE: 0 closest,
 // 1 any.  LUTV: 0 full table in global memory (one entry per lookup through
-// L1/L2), 1 factored tables in shared memory.  SCALES: 1 = the per-child
-// Alg. 1 scales R/extent are precomputed in the node record, 0 = divided.
+// L1/L2), 1 factored tables in shared memory, 2 (compressed only) the
+// precomputed bit table of Sec. 3.2.2 (one bit per ray mask and LUT entry),
+// 3 (R = 4 only) the full table and the LUT in shared memory.
+// SCALES: 1 = the per-child Alg. 1 scales R/extent are precomputed in the
+// node record, 0 = divided.
 template <int R, int CULL, int MODE, int LUTV, int SCALES>
 __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
   constexpr int RR = (R > 0 ? R : 4);
-  __shared__ SmemLut<RR> slut;
-  if constexpr (CULL != 0 && LUTV == 1) {
-    stage_lut<RR>(slut, p.pair);
+  __shared__ SharedTables<RR, LUTV> sh;
+  if constexpr (CULL != 0) {
+    stage_tables(sh, p);
     __syncthreads();
   }
   uint2 stack[kStack];
@@ -439,7 +501,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
     }
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
-    if (trace_step<R, CULL, MODE, LUTV, SCALES>(p, s, stack, slut)) {
+    if (trace_step<R, CULL, MODE, LUTV, SCALES>(p, s, stack, sh)) {
       p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
@@ -450,6 +512,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
 // ------------------------------------------------------------------ waves --
 
 constexpr int kMaxWaves = 5;  // primary + up to 4 bounces
+constexpr int kWaveMinBlocks = 8;  // register bound of the wave kernel (<= 72 / thread)
 
 // Control words at the head of the wave workspace (uint32 indices).
 enum {
@@ -526,16 +589,19 @@ __device__ __forceinline__ unsigned pcg_hash(unsigned v) {
   return (word >> 22u) ^ word;
 }
 
-__device__ __forceinline__ bool make_bounce(const RayState& s, const float4 E1, const float4 E2,
-                                            unsigned seed, unsigned path, unsigned bounce,
-                                            float4& r0, float4& r1) {
-  const float px = __fadd_rn(s.ox, __fmul_rn(s.ht, s.dx));
-  const float py = __fadd_rn(s.oy, __fmul_rn(s.ht, s.dy));
-  const float pz = __fadd_rn(s.oz, __fmul_rn(s.ht, s.dz));
+// Scalars by value (not the ray state by reference): the call is out of
+// line, and taking the state's address would pin it in local memory.
+static __device__ __noinline__ bool make_bounce(float ox, float oy, float oz, float dx, float dy,
+                                                float dz, float ht, const float4 E1,
+                                                const float4 E2, unsigned seed, unsigned path,
+                                                unsigned bounce, float4& r0, float4& r1) {
+  const float px = __fadd_rn(ox, __fmul_rn(ht, dx));
+  const float py = __fadd_rn(oy, __fmul_rn(ht, dy));
+  const float pz = __fadd_rn(oz, __fmul_rn(ht, dz));
   float nx = __fsub_rn(__fmul_rn(E1.y, E2.z), __fmul_rn(E1.z, E2.y));
   float ny = __fsub_rn(__fmul_rn(E1.z, E2.x), __fmul_rn(E1.x, E2.z));
   float nz = __fsub_rn(__fmul_rn(E1.x, E2.y), __fmul_rn(E1.y, E2.x));
-  if (__fadd_rn(__fadd_rn(__fmul_rn(nx, s.dx), __fmul_rn(ny, s.dy)), __fmul_rn(nz, s.dz)) > 0.0f) {
+  if (__fadd_rn(__fadd_rn(__fmul_rn(nx, dx), __fmul_rn(ny, dy)), __fmul_rn(nz, dz)) > 0.0f) {
     nx = -nx; ny = -ny; nz = -nz;
   }
   const float l2 = __fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)), __fmul_rn(nz, nz));
@@ -579,12 +645,12 @@ __device__ __forceinline__ bool make_bounce(const RayState& s, const float4 E1, 
 // wave w + 1 (warp-aggregated atomicAdd, so the queue holds only spawned
 // rays: compacted); a bounded grid barrier separates the waves.
 template <int R, int CULL, int LUTV, int SCALES>
-__global__ void __launch_bounds__(kBlock) waves_kernel(WaveParams wp) {
+__global__ void __launch_bounds__(kBlock, kWaveMinBlocks) waves_kernel(WaveParams wp) {
   constexpr int RR = (R > 0 ? R : 4);
-  __shared__ SmemLut<RR> slut;
+  __shared__ SharedTables<RR, LUTV> sh;
   const Params& p = wp.p;
-  if constexpr (CULL != 0 && LUTV == 1) {
-    stage_lut<RR>(slut, p.pair);
+  if constexpr (CULL != 0) {
+    stage_tables(sh, p);
     __syncthreads();
   }
   const unsigned lane = threadIdx.x & 31u;
@@ -608,7 +674,7 @@ __global__ void __launch_bounds__(kBlock) waves_kernel(WaveParams wp) {
         ray_init(s, __ldcg(&rays[2 * r]), __ldcg(&rays[2 * r + 1]), p);
       }
       if (!__any_sync(0xffffffffu, active)) break;
-      const bool done = active && trace_step<R, CULL, 0, LUTV, SCALES>(p, s, stack, slut);
+      const bool done = active && trace_step<R, CULL, 0, LUTV, SCALES>(p, s, stack, sh);
       if (!__any_sync(0xffffffffu, done)) continue;
       bool spawn = false;
       float4 b0, b1;
@@ -620,8 +686,8 @@ __global__ void __launch_bounds__(kBlock) waves_kernel(WaveParams wp) {
         if (wp.counts[w]) wp.counts[w][rid] = make_uint2(s.ntest, s.ttest);
         if (w < wp.bounces && s.hid >= 0) {
           const float4* tp = p.tris + 3 * (long long)s.hpos;
-          spawn = make_bounce(s, __ldg(tp + 1), __ldg(tp + 2), wp.seed, pid, (unsigned)(w + 1),
-                              b0, b1);
+          spawn = make_bounce(s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.ht, __ldg(tp + 1),
+                              __ldg(tp + 2), wp.seed, pid, (unsigned)(w + 1), b0, b1);
         }
         active = false;
       }

@@ -1,25 +1,30 @@
 // trace_r8.cu — culled traversal variants for R = 8 (object masks of
 // 8^3 bits): {uncompressed, compressed} x {closest, any} x {global table,
-// shared-memory factored table} x {scales divided, scales stored}; and the
-// wave pipeline kernels (global table).
+// shared-memory factored table, bit table (compressed)} x {scales divided,
+// scales stored}; and the wave pipeline kernels.
 #include "trace_kernel.cuh"
 
 namespace sct {
 
 #define SCT_V(C, M, L) {trace_kernel<8, C, M, L, 0>, trace_kernel<8, C, M, L, 1>}
 KernelFn get_kernel_r8(int cull, int mode, int lutv, int scales) {
-  static const KernelFn table[2][2][2][2] = {
-      {{SCT_V(1, 0, 0), SCT_V(1, 0, 1)}, {SCT_V(1, 1, 0), SCT_V(1, 1, 1)}},
-      {{SCT_V(2, 0, 0), SCT_V(2, 0, 1)}, {SCT_V(2, 1, 0), SCT_V(2, 1, 1)}}};
-  return table[cull - 1][mode][lutv][scales];
+  static const KernelFn unc[2][2][2] = {
+      {SCT_V(1, 0, 0), SCT_V(1, 0, 1)}, {SCT_V(1, 1, 0), SCT_V(1, 1, 1)}};
+  static const KernelFn comp[2][3][2] = {
+      {SCT_V(2, 0, 0), SCT_V(2, 0, 1), SCT_V(2, 0, 2)},
+      {SCT_V(2, 1, 0), SCT_V(2, 1, 1), SCT_V(2, 1, 2)}};
+  if (cull == 1) return unc[mode][lutv == 1 ? 1 : 0][scales];
+  return comp[mode][lutv][scales];
 }
 #undef SCT_V
 
-WaveKernelFn get_waves_r8(int cull, int scales) {
-  static const WaveKernelFn table[2][2] = {
-      {waves_kernel<8, 1, 0, 0>, waves_kernel<8, 1, 0, 1>},
-      {waves_kernel<8, 2, 0, 0>, waves_kernel<8, 2, 0, 1>}};
-  return table[cull - 1][scales];
+WaveKernelFn get_waves_r8(int cull, int lutv, int scales) {
+  static const WaveKernelFn unc[2] = {waves_kernel<8, 1, 0, 0>, waves_kernel<8, 1, 0, 1>};
+  static const WaveKernelFn comp[2][2] = {
+      {waves_kernel<8, 2, 0, 0>, waves_kernel<8, 2, 0, 1>},
+      {waves_kernel<8, 2, 2, 0>, waves_kernel<8, 2, 2, 1>}};
+  if (cull == 1) return unc[scales];
+  return comp[lutv == 2 ? 1 : 0][scales];
 }
 
 }  // namespace sct

@@ -105,6 +105,8 @@ void sc_build_opts_default(sc_build_opts* o) {
   o->chunk_bits = 8;
   o->eps_rel = 1.0 / 65536.0;
   o->threads = 0;
+  o->skip_bits = 0;
+  o->test_stride = 1;
 }
 
 sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
@@ -126,6 +128,8 @@ sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
   if (o.lut_size < 1 || o.lut_size > 256) fail(SC_ERR_ARG, "lut_size must be 1..256");
   if (o.chunk_bits < 1 || o.chunk_bits > 12) fail(SC_ERR_ARG, "chunk_bits must be 1..12");
   if (!(o.eps_rel >= 0.0)) fail(SC_ERR_ARG, "eps_rel must be >= 0");
+  if (o.skip_bits < 0) fail(SC_ERR_ARG, "skip_bits must be >= 0");
+  if (o.test_stride < 0) fail(SC_ERR_ARG, "test_stride must be >= 0");
   for (int64_t i = 0; i < 9 * n; ++i)
     if (!std::isfinite(tris[i])) fail(SC_ERR_ARG, "triangle %lld has a non-finite coordinate",
                                       (long long)(i / 9));

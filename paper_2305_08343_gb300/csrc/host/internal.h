@@ -98,7 +98,7 @@ struct ImageLayout {
   int scales = 0;          // per-child Alg. 1 scales stored at +64
   int mask_off = 64;       // first object mask inside a node record
   int node_bytes = 64;
-  size_t off_nodes = 0, off_tris = 0, off_lut = 0, off_pair = 0, off_clut = 0;
+  size_t off_nodes = 0, off_tris = 0, off_lut = 0, off_pair = 0, off_clut = 0, off_bits = 0;
   size_t total = 0;
 };
 ImageLayout image_layout(const Bvh& b, int layout);

@@ -19,11 +19,13 @@ namespace sc {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static bool full_mask(const uint32_t* m, int R) {
+// A child is kept without a test when its mask has >= skip bits set (an
+// all-ones mask can never be culled; denser masks rarely are).
+static bool skip_test(const uint32_t* m, int R, int skip_bits) {
   const int R3 = R * R * R;
-  for (int i = 0; i < R3; ++i)
-    if (!((m[i >> 5] >> (i & 31)) & 1u)) return false;
-  return true;
+  int pop = 0;
+  for (int w = 0; w < (R3 + 31) / 32; ++w) pop += __builtin_popcount(m[w]);
+  return pop >= (skip_bits > 0 ? skip_bits : R3);
 }
 
 uint32_t root_slot_word(const Bvh& b) {
@@ -67,6 +69,8 @@ ImageLayout image_layout(const Bvh& b, int layout) {
     if (L.compress) {
       L.off_clut = off;
       off = align256(off + (size_t)256 * L.mstride);
+      L.off_bits = off;
+      off = align256(off + R3 * R3 * 32);
     }
   }
   L.total = off;
@@ -102,7 +106,10 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
         const uint32_t* m = L.compress ? &b.clut[(size_t)b.cidx[2 * n + c] * L.W]
                                        : &b.masks[((size_t)n * 2 + c) * L.W];
         uint32_t meta = L.compress ? (uint32_t)b.cidx[2 * n + c] : 0u;
-        if (full_mask(m, L.R)) meta |= kMetaFull;
+        const int stride = b.opts.test_stride > 1 ? b.opts.test_stride : 1;
+        const bool inner = b.count[2 * n + c] == 0;
+        if (skip_test(m, L.R, b.opts.skip_bits) || (inner && (b.ndepth[n] + 1) % stride != 0))
+          meta |= kMetaFull;
         u[2 + c] = meta;
         if (!L.compress) std::memcpy(rec + L.mask_off + c * L.mstride, m, 4 * L.W);
       }
@@ -138,6 +145,19 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
     if (L.compress) {
       for (int j = 0; j < b.K; ++j)
         std::memcpy(base + L.off_clut + (size_t)j * L.mstride, &b.clut[(size_t)j * L.W], 4 * L.W);
+      // Sec. 3.2.2: bit (row, j) = the ray mask of row meets LUT entry j
+      uint32_t* bits = reinterpret_cast<uint32_t*>(base + L.off_bits);
+      const int W = L.W, K = b.K;
+      parallel_for((int64_t)(R3 * R3), resolve_threads(0), 1024, [&](int64_t row) {
+        const uint32_t* rm = &lut[(size_t)row * W];
+        uint32_t* out = bits + (size_t)row * 8;
+        for (int j = 0; j < K; ++j) {
+          const uint32_t* cm = &b.clut[(size_t)j * W];
+          uint32_t acc = 0;
+          for (int w = 0; w < W; ++w) acc |= rm[w] & cm[w];
+          if (acc) out[j >> 5] |= 1u << (j & 31);
+        }
+      });
     }
   }
 }

@@ -19,7 +19,7 @@ SC_SCENE_HAIR, SC_SCENE_SOUP = 0, 1
 SC_RAYS_PINHOLE, SC_RAYS_RANDOM = 0, 1
 SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED, SC_LAYOUT_MASKED_COMPACT = 0, 1, 2
 SC_CLOSEST, SC_ANY = 0, 1
-SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED = 0, 1, 2
+SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED, SC_LUT_BITTABLE = 0, 1, 2, 3
 STATUS_NAMES = {0: "SC_OK", -1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_NOMEM",
                 -4: "SC_ERR_TIMEOUT", -5: "SC_ERR_STACK", -6: "SC_ERR_UNSUPPORTED",
                 -7: "SC_ERR_STATE", -8: "SC_ERR_IO"}
@@ -43,7 +43,7 @@ class sc_ray_params(C.Structure):
 class sc_build_opts(C.Structure):
     _fields_ = [("max_leaf", C.c_int), ("bins", C.c_int), ("L", C.c_int),
                 ("lut_size", C.c_int), ("chunk_bits", C.c_int), ("eps_rel", C.c_double),
-                ("threads", C.c_int)]
+                ("threads", C.c_int), ("skip_bits", C.c_int), ("test_stride", C.c_int)]
 
 
 class sc_bvh_info(C.Structure):

@@ -41,13 +41,14 @@ def gpu_trace(bvh, rays, mode, cull, lut_mode=sc.SC_LUT_AUTO, layout=None, refil
                 counts=counts.cpu().numpy().view(np.uint32).copy())
 
 
-def oracle_trace(tris, rays, R, comp, mode, cull):
+def oracle_trace(tris, rays, R, comp, mode, cull, skip_bits=None, stride=1):
     ob = oracle.OracleBVH(tris)
     if R:
         ob.build_masks(R, 3)
         if comp:
             ob.compress(256, 8)
-    return ob.trace(rays, mode, (2 if comp else 1) if cull else 0)
+    return ob.trace(rays, mode, (2 if comp else 1) if cull else 0, skip_bits=skip_bits,
+                    stride=stride)
 
 
 def assert_parity(g, o, what=""):
@@ -87,8 +88,9 @@ def test_hair65k_parity_culled_and_plain(c1, comp):
 
 
 @pytest.mark.parametrize("R", [4, 6, 8])
-@pytest.mark.parametrize("comp", [0, 1])
-@pytest.mark.parametrize("lut", [sc.SC_LUT_GLOBAL, sc.SC_LUT_SHARED])
+@pytest.mark.parametrize("comp,lut", [(0, sc.SC_LUT_GLOBAL), (0, sc.SC_LUT_SHARED),
+                                      (1, sc.SC_LUT_GLOBAL), (1, sc.SC_LUT_SHARED),
+                                      (1, sc.SC_LUT_BITTABLE)])
 @pytest.mark.parametrize("layout", [sc.SC_LAYOUT_MASKED, sc.SC_LAYOUT_MASKED_COMPACT])
 def test_resolutions_lut_modes_layouts(hair_small, R, comp, lut, layout):
     tris, rays = hair_small
@@ -96,6 +98,25 @@ def test_resolutions_lut_modes_layouts(hair_small, R, comp, lut, layout):
     g = gpu_trace(b, rays, 0, 1, lut_mode=lut, layout=layout)
     o = oracle_trace(tris, rays, R, comp, 0, 1)
     assert_parity(g, o, f"R={R} comp={comp} lut={lut} layout={layout}")
+
+
+@pytest.mark.parametrize("skip", [150, 100, 40])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_dense_mask_skip_threshold(hair_small, skip, comp):
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, 6, comp, skip_bits=skip)
+    g = gpu_trace(b, rays, 0, 1)
+    assert_parity(g, oracle_trace(tris, rays, 6, comp, 0, 1, skip_bits=skip), f"skip={skip}")
+
+
+@pytest.mark.parametrize("stride,skip", [(2, 0), (3, 150)])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_test_stride(hair_small, stride, skip, comp):
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, 6, comp, skip_bits=skip, test_stride=stride)
+    g = gpu_trace(b, rays, 0, 1)
+    o = oracle_trace(tris, rays, 6, comp, 0, 1, skip_bits=skip or None, stride=stride)
+    assert_parity(g, o, f"stride={stride} skip={skip}")
 
 
 @pytest.mark.parametrize("refill", [1, 4, 16, 32])

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _oracle_waves(tris, rays, bounces, seed, R, comp, cull):
+def _oracle_waves(tris, rays, bounces, seed, R, comp, cull, skip_bits=None):
     ob = oracle.OracleBVH(tris)
     if R:
         ob.build_masks(R, 3)
@@ -24,18 +24,19 @@ def _oracle_waves(tris, rays, bounces, seed, R, comp, cull):
     waves = []
     cur, path = rays, np.arange(len(rays))
     for w in range(bounces + 1):
-        o = ob.trace(cur, 0, mode)
+        o = ob.trace(cur, 0, mode, skip_bits=skip_bits)
         waves.append(dict(path=path, **o))
         if w < bounces:
             cur, path = oracle.bounce_wave(cur, o["t"], o["id"], tris, seed, w + 1, path)
     return waves
 
 
-def _gpu_waves(tris, rays, bounces, seed, R, comp, cull):
+def _gpu_waves(tris, rays, bounces, seed, R, comp, cull, layout=None, lut=sc.SC_LUT_AUTO):
     b = sc.sc_bvh_build(tris, R, comp)
-    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED if cull else sc.SC_LAYOUT_PLAIN)
+    lay = layout if layout is not None else (sc.SC_LAYOUT_MASKED if cull else sc.SC_LAYOUT_PLAIN)
+    d = sc.DeviceBVH(b, lay)
     r = torch.from_numpy(rays).cuda()
-    bufs, sizes = sc.trace_waves(d, r, bounces, seed, cull)
+    bufs, sizes = sc.trace_waves(d, r, bounces, seed, cull, opts=sc._opts(lut_mode=lut))
     torch.cuda.synchronize()
     out = []
     for w in range(bounces + 1):
@@ -48,11 +49,13 @@ def _gpu_waves(tris, rays, bounces, seed, R, comp, cull):
     return out
 
 
-@pytest.mark.parametrize("cull,comp", [(0, 0), (1, 0), (1, 1)])
-def test_waves_match_oracle(cull, comp):
+@pytest.mark.parametrize("cull,comp,layout,lut", [
+    (0, 0, None, 0), (1, 0, 1, 0), (1, 0, 2, 0), (1, 1, 1, sc.SC_LUT_BITTABLE),
+    (1, 1, 2, sc.SC_LUT_BITTABLE), (1, 1, 1, sc.SC_LUT_GLOBAL)])
+def test_waves_match_oracle(cull, comp, layout, lut):
     tris = sg.hair(400, 16, True, seed=31)
     rays = sg.pinhole(64, 48)
-    g = _gpu_waves(tris, rays, 2, 1234, 6, comp, cull)
+    g = _gpu_waves(tris, rays, 2, 1234, 6, comp, cull, layout, lut)
     o = _oracle_waves(tris, rays, 2, 1234, 6, comp, cull)
     for w in range(3):
         op = o[w]["path"]
@@ -62,6 +65,20 @@ def test_waves_match_oracle(cull, comp):
         assert np.array_equal(g[w]["counts"], o[w]["counts"][order]), f"wave {w}: counts differ"
         assert np.array_equal(g[w]["t"], o[w]["t"][order])
     assert len(o[1]["path"]) > 100 and len(o[2]["path"]) > 10
+
+
+@pytest.mark.parametrize("comp,lut", [(0, sc.SC_LUT_SHARED), (1, sc.SC_LUT_SHARED),
+                                      (1, sc.SC_LUT_BITTABLE), (0, sc.SC_LUT_GLOBAL)])
+def test_waves_r4_lookup_variants(comp, lut):
+    tris = sg.hair(400, 16, True, seed=34)
+    rays = sg.pinhole(64, 48)
+    g = _gpu_waves(tris, rays, 2, 77, 4, comp, 1, None, lut)
+    o = _oracle_waves(tris, rays, 2, 77, 4, comp, 1)
+    for w in range(3):
+        order = np.argsort(o[w]["path"], kind="stable")
+        assert np.array_equal(g[w]["path"], np.sort(o[w]["path"]))
+        assert np.array_equal(g[w]["id"], o[w]["id"][order])
+        assert np.array_equal(g[w]["counts"], o[w]["counts"][order])
 
 
 def test_waves_culled_equals_plain_and_sizes():

@@ -101,6 +101,24 @@ def test_slab_closed_form():
     assert ok and tn == 0.0 and tf == 0.5
 
 
+def test_cell_in_ray_parameter_matches_alg1():
+    """or_cell_t (the traversal's form) evaluates Alg. 1 at p = o + t d; it
+    may differ from the literal form only where p is within rounding of a
+    cell border."""
+    rng = np.random.default_rng(3)
+    diff = 0
+    for _ in range(20000):
+        lo, hi = np.sort(rng.uniform(-2, 2, 2)).astype(np.float32)
+        o, d, t = np.float32(rng.uniform(-3, 3)), np.float32(rng.normal()), np.float32(rng.uniform(0, 4))
+        p = np.float32(o + t * d)
+        a, b = oracle.cell(p, lo, hi, 6), oracle.cell_t(t, o, d, lo, hi, 6)
+        if a != b:
+            q = (float(o) + float(t) * float(d) - float(lo)) * 6 / (float(hi) - float(lo))
+            assert abs(q - round(q)) < 1e-4
+            diff += 1
+    assert diff < 20
+
+
 def test_cell_index_alg1():
     # Alg. 1: floor(R/extent * (p - lower)), clamped to [0, R-1]
     assert oracle.cell(0.0, 0.0, 1.0, 4) == 0
@@ -222,11 +240,8 @@ def test_ray_mask_covers_sampled_segment():
         ok, tn, tf = oracle.slab(ray, np.concatenate([lo, hi]))
         if not ok:
             continue
-        r32 = ray.astype(np.float32)
-        p0 = r32[:3] + np.float32(tn) * r32[4:7]
-        p1 = r32[:3] + np.float32(tf) * r32[4:7]
-        cb = [oracle.cell(p0[k], lo[k], hi[k], R) for k in range(3)]
-        ce = [oracle.cell(p1[k], lo[k], hi[k], R) for k in range(3)]
+        cb = [oracle.cell_t(tn, ray[k], ray[4 + k], lo[k], hi[k], R) for k in range(3)]
+        ce = [oracle.cell_t(tf, ray[k], ray[4 + k], lo[k], hi[k], R) for k in range(3)]
         row = (cb[0] + R * cb[1] + R * R * cb[2]) * R ** 3 + (ce[0] + R * ce[1] + R * R * ce[2])
         m = bits[row].reshape(R, R, R)  # [z, y, x]
         od, dd = ray[:3].astype(np.float64), ray[4:7].astype(np.float64)
@@ -243,3 +258,26 @@ def test_ray_mask_covers_sampled_segment():
             assert any(m[z, y, x] for x in rngs[0] for y in rngs[1] for z in rngs[2])
         checked += 1
     assert checked > 1000
+
+
+def test_dense_mask_skip_keeps_hits_and_orders_counts(hair_small):
+    """Skipping the test for dense masks only keeps children: hits are the
+    same for every threshold, counts lie between the fully tested culled
+    traversal and the plain one, and fewer masks are tested."""
+    tris, rays = hair_small
+    b = oracle.OracleBVH(tris).build_masks(6, L=3).compress(256, 8)
+    plain = b.trace(rays, 0, 0)
+    for cull in (1, 2):
+        full = b.trace(rays, 0, cull)
+        prev = full
+        for skip in (180, 144, 100, 36, 0):
+            o = b.trace(rays, 0, cull, skip_bits=skip)
+            assert np.array_equal(o["id"], plain["id"]) and np.array_equal(o["t"], plain["t"])
+            assert (o["counts"] >= full["counts"]).all() and (o["counts"] <= plain["counts"]).all()
+            assert o["mask_tests"].sum() <= prev["mask_tests"].sum()
+            prev = o
+        assert prev["mask_tests"].sum() == 0 and np.array_equal(prev["counts"], plain["counts"])
+        for stride in (2, 3):
+            o = b.trace(rays, 0, cull, stride=stride)
+            assert np.array_equal(o["id"], plain["id"]) and np.array_equal(o["t"], plain["t"])
+            assert (o["counts"] >= full["counts"]).all() and (o["counts"] <= plain["counts"]).all()
