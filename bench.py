@@ -8,7 +8,9 @@ tests per ray.
 
 One step = one pass of the path over one batch of rays, the rays already in
 device memory: the primary wave (1920x1080 pinhole rays), then the diffuse
-bounce wave spawned from its hits, each traced with culling.
+bounce wave(s) spawned from its hits, all in one cooperative launch replayed
+from a CUDA graph, with block size, stack depth, refill batch and wave size
+picked by the library's autotuner beforehand.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores instead (a bounded sample of rays per step).
@@ -41,10 +43,15 @@ WORKLOADS = {
                 dict(strands=378125, ground=False, seed=4), (1920, 1080), 6, 1),
     "hair65k": ("65,536 hair triangles (2,048 strands), seed 1; 256x256 pinhole rays; R=6 "
                 "uncompressed", dict(strands=2048, ground=False, seed=1), (256, 256), 6, 0),
+    "soup4m": ("triangle soup stress: 4,194,304 triangles in the unit cube (50% slivers of "
+               "aspect 1:1000, 50% axis-aligned slabs, edges log-uniform 1e-4..1e-1), seed 3; "
+               "8,388,608 random rays (origins uniform in the cube, directions uniform on the "
+               "sphere), closest hit (any hit reported beside); R=6 uncompressed masks, L=3",
+               dict(soup=1 << 22, seed=3), (1 << 23, 0), 6, 0),
 }
 
 
-WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1}
+WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "soup4m": 0}
 
 
 def load_peaks():
@@ -150,8 +157,12 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, s
 def make_inputs(name):
     from paper_2305_08343_gb300 import scenegen as sg
     desc, sargs, (W, H), R, comp = WORKLOADS[name]
-    tris = sg.hair(sargs["strands"], 16, sargs["ground"], seed=sargs["seed"])
-    rays = sg.pinhole(W, H)
+    if "soup" in sargs:
+        tris = sg.soup(sargs["soup"], seed=sargs["seed"])
+        rays = sg.random_rays(W, seed=sargs["seed"])
+    else:
+        tris = sg.hair(sargs["strands"], 16, sargs["ground"], seed=sargs["seed"])
+        rays = sg.pinhole(W, H)
     return desc, tris, rays, R, comp
 
 
@@ -278,16 +289,31 @@ def run_gpu(args):
     bufs_c = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
     bufs_p = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
 
+    # autotuner: block size, stack depth, refill batch and wave chunk, per variant
+    tuned = {}
+    opts_c, opts_p = opts, opts
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        opts_c, rows_c = sc.sc_autotune_waves(d_masked, rays, bounces, seed, 1, bufs_c, opts, 3,
+                                              flush)
+        opts_p, rows_p = sc.sc_autotune_waves(d_plain, rays, bounces, seed, 0, bufs_p, opts, 3,
+                                              flush)
+        pick = lambda o: {"block": o.block, "stack": o.stack, "refill": o.refill,
+                          "wave_chunk": int(o.wave_chunk)}
+        tuned = {"culled": pick(opts_c), "plain": pick(opts_p), "candidates": len(rows_c),
+                 "seconds": time.perf_counter() - t0}
+
     def capture(dbvh, cull, bufs):
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream())
+        o = opts_c if cull else opts_p
         with torch.cuda.stream(side):
             for _ in range(2):
-                sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, opts)
+                sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, o)
         torch.cuda.current_stream().wait_stream(side)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, opts)
+            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, o)
         return g
 
     graphs = None
@@ -301,7 +327,8 @@ def run_gpu(args):
         if graphs is not None:
             graphs[i_graph].replay()
         else:
-            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws, opts)
+            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, bufs.outs(), bufs.ws,
+                              opts_c if cull else opts_p)
 
     def timed(i_graph, dbvh, cull, bufs):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -352,6 +379,17 @@ def run_gpu(args):
         ev[1].record(stream)
         torch.cuda.synchronize()
         prim[name] = 3 * n / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e6
+    anyhit = {}
+    if bounces == 0:
+        for name, dbvh, cull in (("culled", d_masked, 1), ("plain", d_plain, 0)):
+            sc.sc_trace(dbvh, rays, hits1, None, 1, cull, work, opts)
+            flush.zero_()
+            ev[2].record(stream)
+            for _ in range(3):
+                sc.sc_trace(dbvh, rays, hits1, None, 1, cull, work, opts)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            anyhit[name] = 3 * n / (ev[2].elapsed_time(ev[3]) * 1e-3) / 1e6
 
     # end to end through the public API: pinned host rays -> device, the wave
     # pipeline, every wave's hit buffer -> pinned host
@@ -361,7 +399,7 @@ def run_gpu(args):
 
     def e2e_step():
         d_rays.copy_(h_rays, non_blocking=True)
-        sc.sc_trace_waves(d_masked, d_rays, bounces, seed, 1, bufs_c.outs(), bufs_c.ws, opts)
+        sc.sc_trace_waves(d_masked, d_rays, bounces, seed, 1, bufs_c.outs(), bufs_c.ws, opts_c)
         for w in range(bounces + 1):
             h_hits[w].copy_(bufs_c.hits[w], non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -422,7 +460,8 @@ def run_gpu(args):
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "plain_mrays_s": plain_value, "speedup_vs_plain": value / world / plain_value,
-        "primary_only_mrays_s": prim,
+        "primary_only_mrays_s": prim, "any_hit_mrays_s": anyhit or None,
+        "autotuned": tuned or None,
         "identical_hits": same, "culled_counts_le_plain": le,
         "tests_per_ray": {"culled": {"node": cnt_c[0], "tri": cnt_c[1],
                                      "node_plus_tri": cnt_c[0] + cnt_c[1]},
@@ -451,7 +490,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hair1m", choices=sorted(WORKLOADS))
     ap.add_argument("--lut", type=int, default=0, help="0 auto, 1 global table, 2 shared")
-    ap.add_argument("--layout", type=int, default=1, help="1 masked (scales stored), 2 compact")
+    ap.add_argument("--layout", type=int, default=2, help="1 masked (scales stored), 2 compact")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--refill", type=int, default=0, help="idle lanes before a warp refills")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bounces", type=int, default=-1, help="bounce waves (-1: workload's)")

@@ -203,6 +203,10 @@ typedef struct {
                         compressed, else the full table                    */
   int refill;        /* a warp fetches new rays once this many of its lanes
                         are idle (1..32), 0 = default                     */
+  int stack;         /* waves: traversal stack entries, 32 or 64 (0 = 64)  */
+  int64_t wave_chunk;/* waves: primary rays per chunk (the wave size); each
+                        chunk runs through all its bounce waves before the
+                        next; 0 = all primary rays in one chunk           */
 } sc_trace_opts;
 
 /* Workspace bytes sc_trace needs (ray counter and device status word). */
@@ -276,9 +280,10 @@ typedef struct {
   uint32_t* counts; /* device uint32[n0][2] or NULL                        */
 } sc_wave_out;
 
-/* Workspace bytes sc_trace_waves needs for n0 primary rays (two ray queues,
-   their path ids and the control words). */
-size_t sc_trace_waves_workspace_bytes(int64_t n0);
+/* Workspace bytes sc_trace_waves needs for n0 primary rays with opts'
+   wave_chunk (NULL = one chunk): two ray queues of one chunk, their path
+   ids and the control words. */
+size_t sc_trace_waves_workspace_bytes(int64_t n0, const sc_trace_opts* opts);
 
 /* d_rays: device float[n0][8] primary rays; outs: host array of bounces+1
    sc_wave_out (each buffer sized for n0 entries); d_ws: device workspace,
@@ -294,6 +299,32 @@ sc_status sc_trace_waves(const sc_dbvh* d, const float* d_rays, int64_t n0,
    of rays of each bounce wave (sizes[0] = 0: wave 0 is the n0 primaries).
    Returns SC_ERR_TIMEOUT / SC_ERR_STACK / SC_ERR_STATE on device errors. */
 sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* stream);
+
+/* Autotuner of the wave pipeline: times sc_trace_waves (one warm-up, then
+   `reps` rounds over all candidates, CUDA events, median per candidate;
+   when d_flush is not NULL its flush_bytes -- make it larger than the L2
+   cache -- are overwritten before every timed run, so candidates are
+   compared from a cold cache) for block size {64, 128, 256},
+   stack depth {32, 64} (where the BVH fits), refill {4, 8, 16} and wave
+   chunk {n0, n0/2, n0/4} (chunks of at least 65,536 rays), writes the
+   fastest into *best (block, stack, refill and wave_chunk set; other fields
+   from `base`), and the tried configurations into results (host array of
+   `cap` entries, may be NULL) with their count in *n_results.  Block sizes
+   other than 128 and stack 32 exist for R = 6 and plain traversal only.
+   d_ws must be sized for the largest chunk (wave_chunk = 0).  Synchronous. */
+typedef struct {
+  int block, stack, refill;
+  int64_t wave_chunk;
+  float ms;
+} sc_tune_result;
+
+sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0,
+                            int bounces, uint32_t seed, int cull,
+                            const sc_wave_out* outs, const sc_trace_opts* base,
+                            void* d_ws, size_t ws_bytes, int reps,
+                            void* d_flush, size_t flush_bytes,
+                            sc_trace_opts* best, sc_tune_result* results,
+                            int cap, int* n_results, void* stream);
 
 /* Synchronizes `stream` and returns the device status word of d_work
    (SC_OK, or SC_ERR_STACK if a ray's stack overflowed). */

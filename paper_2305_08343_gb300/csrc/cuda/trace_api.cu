@@ -1,5 +1,6 @@
 // trace_api.cu — device entry points of the C-ABI: image upload, trace
 // launches, the end-to-end host-buffer form and the status poll.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -13,9 +14,9 @@ KernelFn get_kernel_plain(int mode);
 KernelFn get_kernel_r4(int cull, int mode, int lutv, int scales);
 KernelFn get_kernel_r6(int cull, int mode, int lutv, int scales);
 KernelFn get_kernel_r8(int cull, int mode, int lutv, int scales);
-WaveKernelFn get_waves_plain();
+WaveKernelFn get_waves_plain(int block, int stack);
 WaveKernelFn get_waves_r4(int cull, int lutv, int scales);
-WaveKernelFn get_waves_r6(int cull, int lutv, int scales);
+WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack);
 WaveKernelFn get_waves_r8(int cull, int lutv, int scales);
 }  // namespace sct
 
@@ -97,9 +98,10 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   if (d->stack_need > sct::kStack)
     fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
          sct::kStack);
-  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0};
+  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
   if (opts) o = *opts;
   if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
+  if (o.stack != 0 && o.stack != sct::kStack) fail(SC_ERR_UNSUPPORTED, "stack must be 0 or 64");
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   const int lutv = lut_variant(d, o.lut_mode);
   sct::KernelFn k = pick_kernel(d, mode, cull ? 1 : 0, lutv);
@@ -139,9 +141,21 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   CUDA_OK(cudaGetLastError());
 }
 
-size_t waves_ws_bytes(int64_t n0) {
-  const size_t q = (size_t)(n0 > 0 ? n0 : 1);
-  return 256 + 2 * (q * 32 + 255) / 256 * 256 + 2 * (q * 4 + 255) / 256 * 256;
+int64_t wave_chunk_of(int64_t n0, const sc_trace_opts* o) {
+  int64_t c = (o && o->wave_chunk > 0) ? o->wave_chunk : n0;
+  if (c > n0) c = n0;
+  return c > 0 ? c : 1;
+}
+
+size_t waves_ctrl_bytes(int64_t n0, int64_t chunk) {
+  const int64_t nch = n0 > 0 ? (n0 + chunk - 1) / chunk : 1;
+  return ((size_t)(sct::WW_HEAD + sct::WW_CHUNK_WORDS * nch) * 4 + 255) / 256 * 256;
+}
+
+size_t waves_ws_bytes(int64_t n0, int64_t chunk) {
+  const size_t q = (size_t)(chunk > 0 ? chunk : 1);
+  return waves_ctrl_bytes(n0, chunk) + 2 * ((q * 32 + 255) / 256 * 256) +
+         2 * ((q * 4 + 255) / 256 * 256);
 }
 
 void fill_params(const sc_dbvh* d, sct::Params& p) {
@@ -158,6 +172,21 @@ void fill_params(const sc_dbvh* d, sct::Params& p) {
   p.num_tris = d->ntri;
   p.root_slot = d->root_slot;
   p.has_root = d->has_root;
+}
+
+sct::WaveKernelFn pick_waves(const sc_dbvh* d, int cull, int lutv, int block, int stack) {
+  const bool tuned = block != kBlock || stack != sct::kStack;
+  if (!cull) return sct::get_waves_plain(block, stack);
+  const int c = d->lay.compress ? 2 : 1, sc = d->lay.scales;
+  if (d->lay.R == 6) return sct::get_waves_r6(c, lutv, sc, block, stack);
+  if (tuned)
+    fail(SC_ERR_UNSUPPORTED, "block %d / stack %d wave kernels exist for R = 6 and plain only",
+         block, stack);
+  switch (d->lay.R) {
+    case 4: return sct::get_waves_r4(c, lutv, sc);
+    case 8: return sct::get_waves_r8(c, lutv, sc);
+  }
+  fail(SC_ERR_UNSUPPORTED, "no wave kernel for R = %d", d->lay.R);
 }
 
 void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces, uint32_t seed,
@@ -177,32 +206,28 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   }
   if (n0 > 0 && !d_rays) fail(SC_ERR_ARG, "sc_trace_waves: NULL rays");
   if (reinterpret_cast<uintptr_t>(d_rays) & 15) fail(SC_ERR_ARG, "rays must be 16-byte aligned");
-  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255) || ws_bytes < waves_ws_bytes(n0))
-    fail(SC_ERR_ARG, "sc_trace_waves: workspace must be 256-byte aligned and >= %zu bytes",
-         waves_ws_bytes(n0));
-  if (cull && d->lay.R == 0) fail(SC_ERR_STATE, "sc_trace_waves: culling needs a masked image");
-  if (d->stack_need > sct::kStack)
-    fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
-         sct::kStack);
-  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0};
+  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
   if (opts) o = *opts;
-  if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
+  const int64_t chunk = wave_chunk_of(n0, &o);
+  if (o.wave_chunk < 0) fail(SC_ERR_ARG, "wave_chunk must be >= 0");
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255) || ws_bytes < waves_ws_bytes(n0, chunk))
+    fail(SC_ERR_ARG, "sc_trace_waves: workspace must be 256-byte aligned and >= %zu bytes",
+         waves_ws_bytes(n0, chunk));
+  if (cull && d->lay.R == 0) fail(SC_ERR_STATE, "sc_trace_waves: culling needs a masked image");
+  const int block = o.block ? o.block : kBlock;
+  const int stack = o.stack ? o.stack : sct::kStack;
+  if (block != 64 && block != 128 && block != 256) fail(SC_ERR_ARG, "block must be 64, 128 or 256");
+  if (stack != 32 && stack != 64) fail(SC_ERR_ARG, "stack must be 32 or 64");
+  if (d->stack_need > stack)
+    fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
+         stack);
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   int lutv = lut_variant(d, o.lut_mode);
   if (lutv == 1 && d->lay.R != 4) lutv = 0;  // factored tables: single-batch kernel only
-  sct::WaveKernelFn k = nullptr;
-  if (!cull) {
-    k = sct::get_waves_plain();
-  } else {
-    const int c = d->lay.compress ? 2 : 1, sc = d->lay.scales;
-    switch (d->lay.R) {
-      case 4: k = sct::get_waves_r4(c, lutv, sc); break;
-      case 6: k = sct::get_waves_r6(c, lutv, sc); break;
-      case 8: k = sct::get_waves_r8(c, lutv, sc); break;
-      default: fail(SC_ERR_UNSUPPORTED, "no wave kernel for R = %d", d->lay.R);
-    }
-  }
-  CUDA_OK(cudaMemsetAsync(d_ws, 0, 256, st));
+  sct::WaveKernelFn k = pick_waves(d, cull, lutv, block, stack);
+  if (!k) fail(SC_ERR_UNSUPPORTED, "no wave kernel for this block / stack / lookup combination");
+  const size_t ctrl = waves_ctrl_bytes(n0, chunk);
+  CUDA_OK(cudaMemsetAsync(d_ws, 0, ctrl, st));
   if (n0 == 0) return;
   sct::WaveParams wp;
   std::memset(&wp, 0, sizeof(wp));
@@ -212,8 +237,8 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   wp.p.refill = o.refill ? o.refill : kDefaultRefill;
   wp.p.n = n0;
   uint8_t* ws = reinterpret_cast<uint8_t*>(d_ws);
-  const size_t q = (size_t)n0;
-  size_t off = 256;
+  const size_t q = (size_t)chunk;
+  size_t off = ctrl;
   for (int i = 0; i < 2; ++i) {
     wp.qrays[i] = reinterpret_cast<float4*>(ws + off);
     off += (q * 32 + 255) / 256 * 256;
@@ -224,6 +249,7 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   }
   wp.rays0 = reinterpret_cast<const float4*>(d_rays);
   wp.n0 = n0;
+  wp.chunk = chunk;
   for (int w = 0; w <= bounces; ++w) {
     wp.hits[w] = reinterpret_cast<float4*>(outs[w].hits);
     wp.path[w] = outs[w].path;
@@ -234,13 +260,13 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   wp.timeout_ns = 2000000000ULL;
   DevInfo di = device_info();
   int per_sm = 0;
-  CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, kBlock, 0));
+  CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, block, 0));
   if (per_sm < 1) fail(SC_ERR_CUDA, "wave kernel cannot be resident");
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3((unsigned)(di.sms * per_sm));
-  cfg.blockDim = dim3(kBlock);
+  cfg.blockDim = dim3((unsigned)block);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -391,7 +417,9 @@ sc_status sc_trace_noalloc(const sc_dbvh* d, const float* d_rays, int64_t n, sc_
   SC_CATCH
 }
 
-size_t sc_trace_waves_workspace_bytes(int64_t n0) { return waves_ws_bytes(n0); }
+size_t sc_trace_waves_workspace_bytes(int64_t n0, const sc_trace_opts* opts) {
+  return waves_ws_bytes(n0, wave_chunk_of(n0, opts));
+}
 
 sc_status sc_trace_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces,
                          uint32_t seed, int cull, const sc_wave_out* outs,
@@ -408,15 +436,99 @@ sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* st
   if (!d_ws || !sizes || bounces < 0 || bounces + 1 > sct::kMaxWaves)
     fail(SC_ERR_ARG, "sc_waves_poll: bad argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  unsigned w[sct::WW_WORDS];
-  CUDA_OK(cudaMemcpyAsync(w, d_ws, sizeof(w), cudaMemcpyDeviceToHost, st));
+  unsigned head[sct::WW_HEAD];
+  CUDA_OK(cudaMemcpyAsync(head, d_ws, sizeof(head), cudaMemcpyDeviceToHost, st));
   CUDA_OK(cudaStreamSynchronize(st));
-  for (int i = 0; i <= bounces; ++i) sizes[i] = i == 0 ? 0u : w[sct::WW_SIZE + i];
-  const unsigned status = w[sct::WW_STATUS];
+  const unsigned nch = head[sct::WW_NCHUNKS];
+  std::vector<unsigned> cw((size_t)nch * sct::WW_CHUNK_WORDS);
+  if (nch) {
+    CUDA_OK(cudaMemcpyAsync(cw.data(), reinterpret_cast<const unsigned*>(d_ws) + sct::WW_HEAD,
+                            cw.size() * 4, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+  }
+  for (int i = 0; i <= bounces; ++i) {
+    uint64_t tot = 0;
+    if (i > 0)
+      for (unsigned c = 0; c < nch; ++c) tot += cw[(size_t)c * sct::WW_CHUNK_WORDS + sct::WW_SIZE + i];
+    sizes[i] = (uint32_t)tot;
+  }
+  const unsigned status = head[sct::WW_STATUS];
   if (status & sct::ST_TIMEOUT) fail(SC_ERR_TIMEOUT, "device: a wave barrier timed out");
   if (status & sct::ST_STACK) fail(SC_ERR_STACK, "device: a traversal stack overflowed");
   if (status & sct::ST_BAD_NODE)
     fail(SC_ERR_STATE, "device: the BVH image holds an invalid child reference");
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces,
+                            uint32_t seed, int cull, const sc_wave_out* outs,
+                            const sc_trace_opts* base, void* d_ws, size_t ws_bytes, int reps,
+                            void* d_flush, size_t flush_bytes, sc_trace_opts* best,
+                            sc_tune_result* results, int cap, int* n_results, void* stream) {
+  SC_TRY
+  if (!d || !best || n0 <= 0 || reps < 1) fail(SC_ERR_ARG, "sc_autotune_waves: bad argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
+  if (base) o = *base;
+  const bool all_blocks = (!cull) || d->lay.R == 6;
+  std::vector<int> blocks = all_blocks ? std::vector<int>{64, 128, 256} : std::vector<int>{128};
+  std::vector<int> stacks;
+  if (all_blocks && d->stack_need <= 32) stacks.push_back(32);
+  stacks.push_back(64);
+  const int refills[3] = {4, 8, 16};
+  std::vector<int64_t> chunks = {n0};
+  for (int64_t c = n0 / 2; c >= 65536 && chunks.size() < 3; c /= 2) chunks.push_back(c);
+  std::vector<sc_trace_opts> cands;
+  for (int blk : blocks)
+    for (int stk : stacks)
+      for (int rf : refills)
+        for (int64_t ch : chunks) {
+          sc_trace_opts t = o;
+          t.block = blk;
+          t.stack = stk;
+          t.refill = rf;
+          t.wave_chunk = ch;
+          cands.push_back(t);
+        }
+  cudaEvent_t e0, e1;
+  CUDA_OK(cudaEventCreate(&e0));
+  CUDA_OK(cudaEventCreate(&e1));
+  std::vector<std::vector<float>> ms(cands.size());
+  try {
+    for (auto& t : cands)  // warm-up: code, first touches
+      launch_waves(d, d_rays, n0, bounces, seed, cull, outs, &t, d_ws, ws_bytes, st);
+    for (int r = 0; r < reps; ++r)
+      for (size_t i = 0; i < cands.size(); ++i) {
+        if (d_flush && flush_bytes) CUDA_OK(cudaMemsetAsync(d_flush, r & 0xFF, flush_bytes, st));
+        CUDA_OK(cudaEventRecord(e0, st));
+        launch_waves(d, d_rays, n0, bounces, seed, cull, outs, &cands[i], d_ws, ws_bytes, st);
+        CUDA_OK(cudaEventRecord(e1, st));
+        CUDA_OK(cudaEventSynchronize(e1));
+        float x = 0;
+        CUDA_OK(cudaEventElapsedTime(&x, e0, e1));
+        ms[i].push_back(x);
+      }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  float best_ms = 1e30f;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    std::sort(ms[i].begin(), ms[i].end());
+    const float med = ms[i][ms[i].size() / 2];
+    if (results && (int)i < cap)
+      results[i] = sc_tune_result{cands[i].block, cands[i].stack, cands[i].refill,
+                                  cands[i].wave_chunk, med};
+    if (med < best_ms) {
+      best_ms = med;
+      *best = cands[i];
+    }
+  }
+  if (n_results) *n_results = (int)cands.size();
   return SC_OK;
   SC_CATCH
 }

@@ -294,7 +294,7 @@ __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const flo
 // One traversal step of one ray: either the triangles of one leaf or one
 // inner node, then a pop if nothing is left to visit.  Returns true when the
 // ray has finished (or was stopped by a recorded device error).
-template <int R, int CULL, int MODE, int LUTV, int SCALES>
+template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack>
 __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* stack,
                                            const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
   constexpr int RR = (R > 0 ? R : 4);
@@ -421,7 +421,7 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
         done = true;
       } else if (hit[0] && hit[1]) {
         const int nr = tn[1] < tn[0] ? 1 : 0;
-        if (s.sp < kStack) {
+        if (s.sp < STACK) {
           stack[s.sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
           ++s.sp;
           s.cur = nr ? s1 : s0;
@@ -514,14 +514,17 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
 constexpr int kMaxWaves = 5;  // primary + up to 4 bounces
 constexpr int kWaveMinBlocks = 8;  // register bound of the wave kernel (<= 72 / thread)
 
-// Control words at the head of the wave workspace (uint32 indices).
+// Control words of the wave workspace (uint32 indices): a head, then 16
+// words per chunk of primary rays.
 enum {
-  WW_FETCH = 0,        // [0, kMaxWaves): ray counters of each wave
-  WW_SIZE = 8,         // [8, 8 + kMaxWaves): rays appended to each wave
   WW_STATUS = 16,
   WW_BAR_COUNT = 24,
   WW_BAR_GEN = 25,
-  WW_WORDS = 64
+  WW_NCHUNKS = 32,     // written by the kernel: chunks of this launch
+  WW_HEAD = 64,        // chunk c's words start at WW_HEAD + 16 c:
+  WW_FETCH = 0,        //   [0, kMaxWaves): ray counters of each wave
+  WW_SIZE = 8,         //   [8, 8 + kMaxWaves): rays appended to each wave
+  WW_CHUNK_WORDS = 16
 };
 enum { ST_TIMEOUT = 4 };
 
@@ -529,7 +532,8 @@ struct WaveParams {
   Params p;                    // image, status word (p.work = control words), refill
   const float4* rays0;         // primary rays
   long long n0;
-  float4* qrays[2];            // bounce-ray queues (scratch), n0 rays each
+  long long chunk;             // primary rays per chunk (the wave size)
+  float4* qrays[2];            // bounce-ray queues (scratch), `chunk` rays each
   int* qpath[2];               // path id of each queued ray
   float4* hits[kMaxWaves];     // per wave: {t, id, u, v}
   int* path[kMaxWaves];        // per wave: path id (primary ray index)
@@ -640,12 +644,15 @@ static __device__ __noinline__ bool make_bounce(float ox, float oy, float oz, fl
   return true;
 }
 
-// All waves in one cooperative persistent launch: wave 0 traces the primary
-// rays; every hit of wave w < bounces appends its bounce ray to the queue of
-// wave w + 1 (warp-aggregated atomicAdd, so the queue holds only spawned
-// rays: compacted); a bounded grid barrier separates the waves.
-template <int R, int CULL, int LUTV, int SCALES>
-__global__ void __launch_bounds__(kBlock, kWaveMinBlocks) waves_kernel(WaveParams wp) {
+// All waves in one cooperative persistent launch.  The primary rays are
+// taken in chunks of `chunk` rays (the wave size); for each chunk, wave 0
+// traces its primary rays and every hit of wave w < bounces appends its
+// bounce ray to the queue of wave w + 1 (warp-aggregated atomicAdd, so a
+// queue holds only spawned rays: compacted).  A bounded grid barrier
+// separates the waves.  Outputs: wave 0 by primary index; wave w >= 1 after
+// the entries of the previous chunks.
+template <int R, int CULL, int LUTV, int SCALES, int BLOCK = kBlock, int STACK = kStack>
+__global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_kernel(WaveParams wp) {
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
   const Params& p = wp.p;
@@ -654,66 +661,97 @@ __global__ void __launch_bounds__(kBlock, kWaveMinBlocks) waves_kernel(WaveParam
     __syncthreads();
   }
   const unsigned lane = threadIdx.x & 31u;
-  uint2 stack[kStack];
-  for (int w = 0; w <= wp.bounces; ++w) {
-    const long long n =
-        (w == 0) ? wp.n0 : (long long)(*(volatile unsigned*)&p.work[WW_SIZE + w]);
-    const float4* rays = (w == 0) ? wp.rays0 : wp.qrays[w & 1];
-    const int* qpath = (w == 0) ? nullptr : wp.qpath[w & 1];
-    RayState s;
-    s.have = false;
-    long long rid = -1;
-    bool active = false, exhausted = false;
-    for (;;) {
-      const long long r = warp_fetch(active, &p.work[WW_FETCH + w], n, p.refill, exhausted);
-      if (r >= 0) {
-        rid = r;
-        active = true;
-        // queued rays were written by other SMs in this launch: read them
-        // through L2 (ld.global.cg), never through the read-only / L1 path
-        ray_init(s, __ldcg(&rays[2 * r]), __ldcg(&rays[2 * r + 1]), p);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    p.work[WW_NCHUNKS] = (unsigned)((wp.n0 + wp.chunk - 1) / wp.chunk);
+  uint2 stack[STACK];
+  long long ci = 0;
+  for (long long c0 = 0; c0 < wp.n0; c0 += wp.chunk, ++ci) {
+    unsigned* cw = p.work + WW_HEAD + WW_CHUNK_WORDS * ci;
+    const long long nc = (wp.n0 - c0 < wp.chunk) ? wp.n0 - c0 : wp.chunk;
+    for (int w = 0; w <= wp.bounces; ++w) {
+      const long long n = (w == 0) ? nc : (long long)(*(volatile unsigned*)&cw[WW_SIZE + w]);
+      long long out_base = c0;
+      if (w > 0) {
+        out_base = 0;
+        for (long long c = 0; c < ci; ++c)
+          out_base += *(volatile unsigned*)&p.work[WW_HEAD + WW_CHUNK_WORDS * c + WW_SIZE + w];
       }
-      if (!__any_sync(0xffffffffu, active)) break;
-      const bool done = active && trace_step<R, CULL, 0, LUTV, SCALES>(p, s, stack, sh);
-      if (!__any_sync(0xffffffffu, done)) continue;
-      bool spawn = false;
-      float4 b0, b1;
-      unsigned pid = 0;
-      if (done) {
-        pid = qpath ? (unsigned)__ldcg(&qpath[rid]) : (unsigned)rid;
-        wp.hits[w][rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
-        if (wp.path[w]) wp.path[w][rid] = (int)pid;
-        if (wp.counts[w]) wp.counts[w][rid] = make_uint2(s.ntest, s.ttest);
-        if (w < wp.bounces && s.hid >= 0) {
-          const float4* tp = p.tris + 3 * (long long)s.hpos;
-          spawn = make_bounce(s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.ht, __ldg(tp + 1),
-                              __ldg(tp + 2), wp.seed, pid, (unsigned)(w + 1), b0, b1);
+      const float4* rays = (w == 0) ? wp.rays0 + 2 * c0 : wp.qrays[w & 1];
+      const int* qpath = (w == 0) ? nullptr : wp.qpath[w & 1];
+      RayState s;
+      s.have = false;
+      long long rid = -1;
+      bool active = false, exhausted = false;
+      for (;;) {
+        const long long r = warp_fetch(active, &cw[WW_FETCH + w], n, p.refill, exhausted);
+        if (r >= 0) {
+          rid = r;
+          active = true;
+          // queued rays were written by other SMs in this launch: read them
+          // through L2 (ld.global.cg), never through the read-only / L1 path
+          ray_init(s, __ldcg(&rays[2 * r]), __ldcg(&rays[2 * r + 1]), p);
         }
-        active = false;
-      }
-      const unsigned sm = __ballot_sync(0xffffffffu, spawn);
-      if (sm) {
-        const int leader = __ffs(sm) - 1;
-        unsigned base = 0;
-        if ((int)lane == leader) base = atomicAdd(&p.work[WW_SIZE + w + 1], (unsigned)__popc(sm));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (spawn) {
-          const unsigned pos = base + __popc(sm & ((1u << lane) - 1u));
-          float4* q = wp.qrays[(w + 1) & 1];
-          q[2 * pos] = b0;
-          q[2 * pos + 1] = b1;
-          wp.qpath[(w + 1) & 1][pos] = (int)pid;
+        if (!__any_sync(0xffffffffu, active)) break;
+        const bool done =
+            active && trace_step<R, CULL, 0, LUTV, SCALES, STACK>(p, s, stack, sh);
+        if (!__any_sync(0xffffffffu, done)) continue;
+        bool spawn = false;
+        float4 b0, b1;
+        unsigned pid = 0;
+        if (done) {
+          pid = qpath ? (unsigned)__ldcg(&qpath[rid]) : (unsigned)(c0 + rid);
+          const long long o = out_base + rid;
+          wp.hits[w][o] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+          if (wp.path[w]) wp.path[w][o] = (int)pid;
+          if (wp.counts[w]) wp.counts[w][o] = make_uint2(s.ntest, s.ttest);
+          if (w < wp.bounces && s.hid >= 0) {
+            const float4* tp = p.tris + 3 * (long long)s.hpos;
+            spawn = make_bounce(s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.ht, __ldg(tp + 1),
+                                __ldg(tp + 2), wp.seed, pid, (unsigned)(w + 1), b0, b1);
+          }
+          active = false;
+        }
+        const unsigned sm = __ballot_sync(0xffffffffu, spawn);
+        if (sm) {
+          const int leader = __ffs(sm) - 1;
+          unsigned base = 0;
+          if ((int)lane == leader) base = atomicAdd(&cw[WW_SIZE + w + 1], (unsigned)__popc(sm));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (spawn) {
+            const unsigned pos = base + __popc(sm & ((1u << lane) - 1u));
+            float4* q = wp.qrays[(w + 1) & 1];
+            q[2 * pos] = b0;
+            q[2 * pos + 1] = b1;
+            wp.qpath[(w + 1) & 1][pos] = (int)pid;
+          }
         }
       }
-    }
-    if (w < wp.bounces) {
-      __threadfence();
-      if (!grid_barrier(p.work, wp.timeout_ns)) return;
+      const bool last = (w == wp.bounces) && (c0 + wp.chunk >= wp.n0);
+      if (!last) {
+        __threadfence();
+        if (!grid_barrier(p.work, wp.timeout_ns)) return;
+      }
     }
   }
 }
 
 typedef void (*KernelFn)(Params);
 typedef void (*WaveKernelFn)(WaveParams);
+
+// Block size x stack depth variants of one wave kernel (for the autotuner):
+// index [block 64/128/256][stack 32/64].
+template <int R, int CULL, int LUTV, int SCALES>
+struct WaveVariants {
+  static WaveKernelFn get(int block, int stack) {
+    static const WaveKernelFn t[3][2] = {
+        {waves_kernel<R, CULL, LUTV, SCALES, 64, 32>, waves_kernel<R, CULL, LUTV, SCALES, 64, 64>},
+        {waves_kernel<R, CULL, LUTV, SCALES, 128, 32>,
+         waves_kernel<R, CULL, LUTV, SCALES, 128, 64>},
+        {waves_kernel<R, CULL, LUTV, SCALES, 256, 32>,
+         waves_kernel<R, CULL, LUTV, SCALES, 256, 64>}};
+    const int bi = block == 64 ? 0 : (block == 256 ? 2 : 1);
+    return t[bi][stack == 32 ? 0 : 1];
+  }
+};
 
 }  // namespace sct

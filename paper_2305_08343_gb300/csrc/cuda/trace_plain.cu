@@ -8,6 +8,8 @@ KernelFn get_kernel_plain(int mode) {
   return mode ? trace_kernel<0, 0, 1, 0, 0> : trace_kernel<0, 0, 0, 0, 0>;
 }
 
-WaveKernelFn get_waves_plain() { return waves_kernel<0, 0, 0, 0>; }
+WaveKernelFn get_waves_plain(int block, int stack) {
+  return WaveVariants<0, 0, 0, 0>::get(block, stack);
+}
 
 }  // namespace sct

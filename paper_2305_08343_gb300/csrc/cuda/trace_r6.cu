@@ -18,13 +18,15 @@ KernelFn get_kernel_r6(int cull, int mode, int lutv, int scales) {
 }
 #undef SCT_V
 
-WaveKernelFn get_waves_r6(int cull, int lutv, int scales) {
-  static const WaveKernelFn unc[2] = {waves_kernel<6, 1, 0, 0>, waves_kernel<6, 1, 0, 1>};
-  static const WaveKernelFn comp[2][2] = {
-      {waves_kernel<6, 2, 0, 0>, waves_kernel<6, 2, 0, 1>},
-      {waves_kernel<6, 2, 2, 0>, waves_kernel<6, 2, 2, 1>}};
-  if (cull == 1) return unc[scales];
-  return comp[lutv == 2 ? 1 : 0][scales];
+WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack) {
+  if (cull == 1)
+    return scales ? WaveVariants<6, 1, 0, 1>::get(block, stack)
+                  : WaveVariants<6, 1, 0, 0>::get(block, stack);
+  if (lutv == 2)
+    return scales ? WaveVariants<6, 2, 2, 1>::get(block, stack)
+                  : WaveVariants<6, 2, 2, 0>::get(block, stack);
+  if (block != kBlock || stack != kStack) return nullptr;
+  return scales ? waves_kernel<6, 2, 0, 1> : waves_kernel<6, 2, 0, 0>;
 }
 
 }  // namespace sct

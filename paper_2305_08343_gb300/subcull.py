@@ -62,7 +62,12 @@ SC_MAX_BOUNCES = 4
 
 class sc_trace_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int),
-                ("refill", C.c_int)]
+                ("refill", C.c_int), ("stack", C.c_int), ("wave_chunk", C.c_int64)]
+
+
+class sc_tune_result(C.Structure):
+    _fields_ = [("block", C.c_int), ("stack", C.c_int), ("refill", C.c_int),
+                ("wave_chunk", C.c_int64), ("ms", C.c_float)]
 
 
 _lock = threading.Lock()
@@ -102,7 +107,11 @@ def lib():
             "sc_status_poll": (C.c_int, [vp, vp]),
             "sc_trace_noalloc": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, C.c_int,
                                            P(sc_trace_opts), vp]),
-            "sc_trace_waves_workspace_bytes": (C.c_size_t, [i64]),
+            "sc_trace_waves_workspace_bytes": (C.c_size_t, [i64, P(sc_trace_opts)]),
+            "sc_autotune_waves": (C.c_int, [vp, vp, i64, C.c_int, C.c_uint32, C.c_int,
+                                            P(sc_wave_out), P(sc_trace_opts), vp, C.c_size_t,
+                                            C.c_int, vp, C.c_size_t, P(sc_trace_opts),
+                                            P(sc_tune_result), C.c_int, P(C.c_int), vp]),
             "sc_trace_waves": (C.c_int, [vp, vp, i64, C.c_int, C.c_uint32, C.c_int,
                                          P(sc_wave_out), P(sc_trace_opts), vp, C.c_size_t, vp]),
             "sc_waves_poll": (C.c_int, [vp, C.c_int, u32p, vp]),
@@ -274,8 +283,8 @@ def sc_bvh_upload(bvh: Bvh, layout: int, stream=None) -> DeviceBVH:
     return DeviceBVH(bvh, layout, stream=stream)
 
 
-def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO, refill=0):
-    return sc_trace_opts(block, blocks_per_sm, lut_mode, refill)
+def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO, refill=0, stack=0, wave_chunk=0):
+    return sc_trace_opts(block, blocks_per_sm, lut_mode, refill, stack, wave_chunk)
 
 
 def sc_trace(dbvh: DeviceBVH, rays, hits, counts, mode: int, cull: int, work,
@@ -347,8 +356,8 @@ def split_hits(hits):
 
 # ------------------------------------------------------------------ waves --
 
-def sc_trace_waves_workspace_bytes(n0: int) -> int:
-    return int(lib().sc_trace_waves_workspace_bytes(n0))
+def sc_trace_waves_workspace_bytes(n0: int, opts: sc_trace_opts | None = None) -> int:
+    return int(lib().sc_trace_waves_workspace_bytes(n0, C.byref(opts) if opts else None))
 
 
 def sc_trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, outs, ws,
@@ -385,7 +394,7 @@ class WaveBuffers:
         self.path = [torch.empty(n0, dtype=torch.int32, device=device) for _ in range(bounces + 1)]
         self.counts = [torch.empty((n0, 2), dtype=torch.int32, device=device) if with_counts
                        else None for _ in range(bounces + 1)]
-        nb = sc_trace_waves_workspace_bytes(n0)
+        nb = sc_trace_waves_workspace_bytes(n0)  # largest chunk: fits every wave_chunk
         # 256-byte aligned view into a slightly larger buffer
         self._raw = torch.empty(nb + 256, dtype=torch.uint8, device=device)
         off = (-self._raw.data_ptr()) % 256
@@ -403,3 +412,29 @@ def trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, buffe
     sizes = sc_waves_poll(b.ws, bounces, stream)
     sizes[0] = rays.shape[0]
     return b, sizes
+
+
+def sc_autotune_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, buffers,
+                      base: sc_trace_opts | None = None, reps: int = 3, flush=None, stream=None):
+    """Times the wave pipeline over block / stack / refill / wave-chunk
+    candidates; returns (best opts, list of (block, stack, refill, chunk, ms))."""
+    n0 = rays.shape[0]
+    outs = buffers.outs()
+    arr = (sc_wave_out * (bounces + 1))()
+    for w, (h, pth, cnt) in enumerate(outs):
+        arr[w].hits = h.data_ptr()
+        arr[w].path = pth.data_ptr() if pth is not None else None
+        arr[w].counts = cnt.data_ptr() if cnt is not None else None
+    best = sc_trace_opts()
+    cap = 256
+    res = (sc_tune_result * cap)()
+    nres = C.c_int()
+    b = base or _opts()
+    _check(lib().sc_autotune_waves(dbvh.handle, C.c_void_p(rays.data_ptr()), n0, bounces,
+                                   seed & 0xFFFFFFFF, cull, arr, C.byref(b),
+                                   C.c_void_p(buffers.ws.data_ptr()), buffers.ws.numel(), reps,
+                                   C.c_void_p(flush.data_ptr()) if flush is not None else None,
+                                   flush.numel() if flush is not None else 0,
+                                   C.byref(best), res, cap, C.byref(nres), _stream_ptr(stream)))
+    rows = [(r.block, r.stack, r.refill, r.wave_chunk, r.ms) for r in res[: min(nres.value, cap)]]
+    return best, rows

@@ -31,12 +31,13 @@ def _oracle_waves(tris, rays, bounces, seed, R, comp, cull, skip_bits=None):
     return waves
 
 
-def _gpu_waves(tris, rays, bounces, seed, R, comp, cull, layout=None, lut=sc.SC_LUT_AUTO):
+def _gpu_waves(tris, rays, bounces, seed, R, comp, cull, layout=None, lut=sc.SC_LUT_AUTO,
+               **opts):
     b = sc.sc_bvh_build(tris, R, comp)
     lay = layout if layout is not None else (sc.SC_LAYOUT_MASKED if cull else sc.SC_LAYOUT_PLAIN)
     d = sc.DeviceBVH(b, lay)
     r = torch.from_numpy(rays).cuda()
-    bufs, sizes = sc.trace_waves(d, r, bounces, seed, cull, opts=sc._opts(lut_mode=lut))
+    bufs, sizes = sc.trace_waves(d, r, bounces, seed, cull, opts=sc._opts(lut_mode=lut, **opts))
     torch.cuda.synchronize()
     out = []
     for w in range(bounces + 1):
@@ -79,6 +80,40 @@ def test_waves_r4_lookup_variants(comp, lut):
         assert np.array_equal(g[w]["path"], np.sort(o[w]["path"]))
         assert np.array_equal(g[w]["id"], o[w]["id"][order])
         assert np.array_equal(g[w]["counts"], o[w]["counts"][order])
+
+
+@pytest.mark.parametrize("cfg", [dict(wave_chunk=1000), dict(wave_chunk=777, block=64, stack=32),
+                                 dict(block=256, stack=32, refill=16), dict(block=64, refill=1)])
+@pytest.mark.parametrize("cull,comp", [(1, 1), (1, 0), (0, 0)])
+def test_waves_chunks_blocks_stacks(cfg, cull, comp):
+    """Chunked waves (the wave size), block sizes and stack depths: per-path
+    results must not depend on the configuration."""
+    tris = sg.hair(300, 16, True, seed=35)
+    rays = sg.pinhole(80, 40)
+    g = _gpu_waves(tris, rays, 2, 5, 6, comp, cull, None, sc.SC_LUT_AUTO, **cfg)
+    o = _oracle_waves(tris, rays, 2, 5, 6, comp, cull)
+    for w in range(3):
+        order = np.argsort(o[w]["path"], kind="stable")
+        assert np.array_equal(g[w]["path"], np.sort(o[w]["path"])), f"wave {w} {cfg}"
+        assert np.array_equal(g[w]["id"], o[w]["id"][order])
+        assert np.array_equal(g[w]["counts"], o[w]["counts"][order])
+
+
+def test_autotuner_returns_a_valid_config():
+    tris = sg.hair(300, 16, True, seed=36)
+    rays = sg.pinhole(256, 256)
+    b = sc.sc_bvh_build(tris, 6, 1)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED_COMPACT)
+    r = torch.from_numpy(rays).cuda()
+    bufs = sc.WaveBuffers(r.shape[0], 2, with_counts=False)
+    best, rows = sc.sc_autotune_waves(d, r, 2, 9, 1, bufs, reps=1)
+    assert len(rows) >= 9 and best.block in (64, 128, 256) and best.stack in (32, 64)
+    assert min(x[-1] for x in rows) > 0
+    # the tuned configuration gives the same results as the default one
+    b1, s1 = sc.trace_waves(d, r, 2, 9, 1, opts=best)
+    b2, s2 = sc.trace_waves(d, r, 2, 9, 1)
+    assert list(s1) == list(s2)
+    assert torch.equal(b1.hits[0].view(torch.int32), b2.hits[0].view(torch.int32))
 
 
 def test_waves_culled_equals_plain_and_sizes():
