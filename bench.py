@@ -225,6 +225,93 @@ def _sorted_waves(bufs, sizes):
     return out
 
 
+def run_learned(args, bvh, d_masked, dev, flush, W, H):
+    """Learned proposal against plain culled traversal on held-out rays:
+    train on the GPU (training pairs from the plain traversal of jittered
+    primary rays and their bounce waves), then time [network top-1 + seeded
+    traversal] and [culled traversal] on 2^22 held-out jittered primary
+    rays (other jitter seeds), identical hits asserted."""
+    import torch
+
+    from paper_2305_08343_gb300 import learned
+    from paper_2305_08343_gb300 import subcull as sc
+
+    t0 = time.perf_counter()
+    lp = learned.LearnedProposal(bvh, depth=8, seed=0, device=dev)
+    target = args.learned_pairs
+    pairs_r, pairs_l, total, s = [], [], 0, 1
+    while total < target and s <= 64:
+        rays = learned.primary_rays(W, H, 1000 + s, device=dev)
+        r, l = lp.collect(d_masked, [rays], bounces=2, seed=77 + s)
+        pairs_r.append(r.clone())
+        pairs_l.append(l.clone())
+        total += r.shape[0]
+        s += 1
+    tr_r = torch.cat(pairs_r)[:target]
+    tr_l = torch.cat(pairs_l)[:target]
+    del pairs_r, pairs_l
+    collect_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = lp.fit(tr_r, tr_l, steps=args.learned_steps, batch=4096, lr=3e-3, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    n_held = 1 << 22
+    held = torch.cat([learned.primary_rays(W, H, 5 + k, device=dev)
+                      for k in range((n_held + W * H - 1) // (W * H))])[:n_held].contiguous()
+    n = held.shape[0]
+    cls = torch.empty(n, dtype=torch.int32, device=dev)
+    hits_s = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    hits_p = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    cnt_s = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    cnt_p = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
+    out = {"training_pairs": int(tr_r.shape[0]), "train_steps": args.learned_steps,
+           "batch": 4096, "final_loss": loss, "collect_s": collect_s, "train_s": train_s,
+           "held_out_rays": n, "frontier": lp.n_frontier}
+    stream = torch.cuda.current_stream()
+    for min_prob in (0.0, 0.8):
+        key = "top1" if min_prob == 0.0 else f"top1_p{min_prob}"
+        lp.predict(held, cls, min_prob=min_prob)
+        lp.trace(d_masked, held, cls, hits_s, cnt_s, 1, work)
+        sc.sc_trace(d_masked, held, hits_p, cnt_p, 0, 1, work)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(hits_s.view(torch.int32), hits_p.view(torch.int32)))
+        ts = cnt_s.double().mean(0).tolist()
+        tp = cnt_p.double().mean(0).tolist()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ms_l, ms_p, ms_net = [], [], []
+        for _ in range(args.warmup):
+            lp.predict(held, cls, min_prob=min_prob)
+            lp.trace(d_masked, held, cls, hits_s, None, 1, work)
+            sc.sc_trace(d_masked, held, hits_p, None, 0, 1, work)
+        for _ in range(args.steps):
+            flush.zero_()
+            ev[0].record(stream)
+            lp.predict(held, cls, min_prob=min_prob)
+            ev[1].record(stream)
+            lp.trace(d_masked, held, cls, hits_s, None, 1, work)
+            ev[2].record(stream)
+            flush.zero_()
+            ev[3].record(stream)
+            sc.sc_trace(d_masked, held, hits_p, None, 0, 1, work)
+            e4 = torch.cuda.Event(enable_timing=True)
+            e4.record(stream)
+            torch.cuda.synchronize()
+            ms_net.append(ev[0].elapsed_time(ev[1]))
+            ms_l.append(ev[0].elapsed_time(ev[2]))
+            ms_p.append(ev[3].elapsed_time(e4))
+        sc.sc_status_poll(work)
+        out[key] = {
+            "identical_hits": same,
+            "seeded_fraction": float((cls >= 0).double().mean().item()),
+            "learned_mrays_s": n / (np.mean(ms_l) * 1e-3) / 1e6,
+            "network_ms": float(np.mean(ms_net)),
+            "plain_culled_mrays_s": n / (np.mean(ms_p) * 1e-3) / 1e6,
+            "tests_per_ray": {"learned": {"node": ts[0], "tri": ts[1]},
+                              "plain_culled": {"node": tp[0], "tri": tp[1]}}}
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -430,6 +517,14 @@ def run_gpu(args):
                 "peak_source": "measured" if peaks else "fallback",
                 "bytes_per_ray": b_ray, "kernel": "waves_kernel (culled)"}
 
+    learned_out = None
+    if args.learned:
+        W, H = WORKLOADS[args.workload][2]
+        if H == 0:
+            learned_out = {"skipped": "the learned proposal is trained on camera rays"}
+        else:
+            learned_out = run_learned(args, bvh, d_masked, dev, flush, W, H)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -468,6 +563,7 @@ def run_gpu(args):
                           "plain": {"node": cnt_p[0], "tri": cnt_p[1],
                                     "node_plus_tri": cnt_p[0] + cnt_p[1]}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "learned_proposal": learned_out,
         "gpu_launches": args.steps,
         "build_s": build_s, "bvh": {"nodes": info.num_nodes, "max_depth": info.max_depth,
                                     "ms_bvh": info.ms_bvh, "ms_masks": info.ms_masks,
@@ -503,6 +599,11 @@ def main():
                     help="only a few single-batch traces (for ncu captures)")
     ap.add_argument("--skip-bits", type=int, default=0,
                     help="keep children with >= this many mask bits untested (0: R^3)")
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the learned proposal and time it against plain culled "
+                         "traversal on held-out rays")
+    ap.add_argument("--learned-pairs", type=int, default=1 << 24)
+    ap.add_argument("--learned-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

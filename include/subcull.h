@@ -278,6 +278,7 @@ typedef struct {
   sc_hit* hits;     /* device sc_hit[n0]: wave entries in queue order      */
   int32_t* path;    /* device int32[n0] or NULL: primary ray of each entry */
   uint32_t* counts; /* device uint32[n0][2] or NULL                        */
+  float* rays;      /* device float[n0][8] or NULL: the traced rays         */
 } sc_wave_out;
 
 /* Workspace bytes sc_trace_waves needs for n0 primary rays with opts'
@@ -325,6 +326,85 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0,
                             void* d_flush, size_t flush_bytes,
                             sc_trace_opts* best, sc_tune_result* results,
                             int cap, int* n_results, void* stream);
+
+/* --------------------------------------------------- learned proposal --- */
+/* Not in the paper.  A small network proposes, per ray, the depth-`depth`
+   subtree of the BVH most likely to hold the closest hit; that subtree is
+   traced first, and its hit t (if any) tightens t_max of the full culled
+   traversal that follows, so results are exactly those of the traversal
+   without the proposal.
+
+   Frontier: the slots at depth `depth` below the root (the root slot has
+   depth 0), plus leaf slots reached before that depth, in pre-order (left
+   child first); at most 2^depth entries, 32 bytes each: the slot's box as
+   its parent stores it (the scene box for the root slot) and its slot word
+   (an inner node index, or 0x80000000 | (count-1) << 28 | first triangle
+   position). */
+typedef struct {
+  float lo[3], hi[3];
+  uint32_t slot;
+  uint32_t reserved; /* 0 */
+} sc_frontier_entry;
+
+/* out: host sc_frontier_entry[cap]; *n_slots <- the number written;
+   class_of_tri: host uint8[num_tris] or NULL, the frontier index of each
+   triangle id.  depth 0..8.  SC_ERR_NOMEM if cap is too small. */
+sc_status sc_bvh_frontier(const sc_bvh* b, int depth, sc_frontier_entry* out, int cap,
+                          int* n_slots, uint8_t* class_of_tri);
+
+/* Seeded traversal (closest hit).  d_cls: device int32[n], the proposed
+   frontier index of each ray; an index outside [0, n_frontier) traces that
+   ray without a seed.  d_frontier: device sc_frontier_entry[n_frontier]
+   (16-byte aligned), n_frontier 1..256.  For a seeded ray the seed box is
+   slab-tested with the ray's t_max (one node test); if the ray enters it,
+   phase 1 traverses the seed subtree with that t_max.  Phase 2 traverses
+   from the root, skipping the seed slot: a phase-1 hit at t_s is held
+   provisionally with t_max = nextafter(t_s, +inf), and t_max drops to t_s
+   when phase 2 reaches the seed slot in its traversal order, so hits are
+   bit-identical to sc_trace's closest hits; counts (node tests, triangle
+   tests) sum both phases.  Other arguments as sc_trace (block and stack
+   must be default). */
+sc_status sc_trace_seeded(const sc_dbvh* d, const float* d_rays, int64_t n,
+                          const int32_t* d_cls, const sc_frontier_entry* d_frontier,
+                          int n_frontier, sc_hit* d_hits, uint32_t* d_counts,
+                          int cull, const sc_trace_opts* opts, void* d_work,
+                          size_t work_bytes, void* stream);
+
+/* The network: MLP 6 -> 64 -> 64 -> 256, GELU, BF16 weights, FP32
+   accumulation.  Input of a ray: (origin - box centre) / box half-extent
+   and the direction; d_box: device float[6] = centre.xyz, half.xyz.
+   Parameters: sc_mlp_num_params() floats, layout W1[64][6], b1[64],
+   W2[64][64], b2[64], W3[256][64], b3[256]; d_wb: the BF16 copy (2 bytes
+   per parameter) that the kernels read. */
+int sc_mlp_num_params(void);
+/* d_wb <- BF16(d_w) (round to nearest even). */
+sc_status sc_mlp_to_bf16(const float* d_w, void* d_wb, void* stream);
+/* Top-1 class of each ray (d_cls: device int32[n]) and optionally all
+   logits (d_logits: device float[n][256] or NULL).  With min_prob > 0 a
+   ray whose top-1 softmax probability is below min_prob gets class -1
+   (no seed: sc_trace_seeded then traces it plainly). */
+sc_status sc_mlp_forward(const void* d_wb, const float* d_rays, int64_t n,
+                         const float* d_box, int32_t* d_cls, float* d_logits,
+                         float min_prob, void* stream);
+/* Workspace bytes of one training batch. */
+size_t sc_mlp_train_workspace_bytes(int64_t batch);
+/* Gradient of the mean cross-entropy of a batch (d_labels: int32 classes)
+   w.r.t. the parameters, ADDED to d_grad (float[P]); *d_loss (device) <-
+   the mean loss.  Forward with the BF16 weights, FP32 accumulation. */
+sc_status sc_mlp_grad(const void* d_wb, const float* d_rays, const int32_t* d_labels,
+                      int64_t batch, const float* d_box, float* d_grad, float* d_loss,
+                      void* d_ws, size_t ws_bytes, void* stream);
+/* Adam step `step` (1-based) on the FP32 master d_w with d_grad (then
+   zeroed), moments d_m, d_v; refreshes d_wb. */
+sc_status sc_mlp_adam(float* d_w, void* d_wb, float* d_grad, float* d_m, float* d_v,
+                      int step, float lr, float beta1, float beta2, float eps,
+                      void* stream);
+/* Training pairs: appends (ray, class_of_tri[hit id]) of every ray that hit
+   to d_out_rays / d_out_labels at position atomicAdd(d_count); at most cap. */
+sc_status sc_mlp_labels(const float* d_rays, const void* d_hits, int64_t n,
+                        const uint8_t* d_class_of_tri, float* d_out_rays,
+                        int32_t* d_out_labels, uint32_t* d_count, int64_t cap,
+                        void* stream);
 
 /* Synchronizes `stream` and returns the device status word of d_work
    (SC_OK, or SC_ERR_STACK if a ray's stack overflowed). */

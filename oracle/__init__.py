@@ -89,6 +89,10 @@ def lib():
             "or_slab": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f)]),
             "or_cell": (C.c_int, [f, f, f, C.c_int]),
             "or_cell_t": (C.c_int, [f, f, f, f, f, C.c_int]),
+            "or_bvh_frontier": (C.c_int, [vp, C.c_int, _P(i32), _P(i32), _P(f), _P(u8)]),
+            "or_trace_seeded": (C.c_int, [vp, _P(f), _P(f), i64, C.c_int, C.c_int, C.c_int,
+                                          _P(i32), _P(i32), _P(i32), _P(f), C.c_int, _P(f),
+                                          _P(i32), _P(f), _P(u32)]),
             "or_pcg_hash": (u32, [u32]),
             "or_bounce_hash": (u32, [u32, u32, u32, u32]),
             "or_bounce": (C.c_int, [_P(f), f, _P(f), u32, u32, u32, _P(f)]),
@@ -292,6 +296,46 @@ class OracleBVH:
         if rc != 0:
             raise ValueError(f"or_trace failed ({rc})")
         return out
+
+
+def _frontier(self, depth: int = 8):
+    """(child, count, box[k][6], class_of_tri) of the depth-`depth` frontier."""
+    cap = 1 << depth
+    fc = np.zeros(cap, np.int32)
+    fn = np.zeros(cap, np.int32)
+    fb = np.zeros((cap, 6), np.float32)
+    cls = np.zeros(max(self.ntri, 1), np.uint8)
+    k = lib().or_bvh_frontier(self._h, depth, _ptr(fc, C.c_int32), _ptr(fn, C.c_int32),
+                              _ptr(fb, C.c_float), _ptr(cls, C.c_uint8))
+    return fc[:k], fn[:k], fb[:k], cls[: self.ntri]
+
+
+def _trace_seeded(self, rays, cls, depth: int = 8, cull: int = 0, skip_bits=None, stride=1):
+    """Seeded closest-hit traversal over the depth-`depth` frontier; cls[i]
+    outside [0, frontier size) traces ray i without a seed."""
+    rays = _f32(rays).reshape(-1, 8)
+    n = rays.shape[0]
+    fc, fn, fb, _ = self.frontier(depth)
+    fb = np.ascontiguousarray(fb)
+    c = np.ascontiguousarray(cls, dtype=np.int32)
+    if skip_bits is None:
+        skip_bits = max(self.R, 1) ** 3
+    t = np.zeros(n, np.float32)
+    hid = np.zeros(n, np.int32)
+    uv = np.zeros((n, 2), np.float32)
+    cnt = np.zeros((n, 2), np.uint32)
+    rc = lib().or_trace_seeded(self._h, _ptr(self.tris, C.c_float), _ptr(rays, C.c_float), n,
+                               cull, skip_bits, stride, _ptr(c, C.c_int32),
+                               _ptr(fc, C.c_int32), _ptr(fn, C.c_int32), _ptr(fb, C.c_float),
+                               len(fc), _ptr(t, C.c_float), _ptr(hid, C.c_int32),
+                               _ptr(uv, C.c_float), _ptr(cnt, C.c_uint32))
+    if rc != 0:
+        raise ValueError(f"or_trace_seeded failed ({rc})")
+    return dict(t=t, id=hid, uv=uv, counts=cnt)
+
+
+OracleBVH.frontier = _frontier
+OracleBVH.trace_seeded = _trace_seeded
 
 
 def scene_eps(tris, eps_rel: float = 2.0 ** -16) -> float:

@@ -917,6 +917,15 @@ typedef struct {
   float tn;
 } StackEntry;
 
+/* Seed of the second phase of a seeded traversal: the slot (child, count)
+   whose subtree the first phase traced in full, and that phase's hit
+   (id < 0: none). */
+typedef struct {
+  int32_t child, count;
+  float t, u, v;
+  int32_t id;
+} Seed;
+
 /*
  * Alg. 4 for one ray.  Readings where the paper is silent (it gives neither
  * child order nor pop rule): the root box is not tested; visiting an inner
@@ -940,7 +949,7 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
                       int mode, int cull, int skip_bits, int stride, StackEntry* stack,
                       float* hit_t,
                       int32_t* hit_id, float* hit_uv, uint32_t* counts,
-                      uint32_t* mtests) {
+                      uint32_t* mtests, const Seed* seed) {
   ORay r;
   load_ray(ray8, &r);
   float tcur = r.tmax, bu = 0.0f, bv = 0.0f, bt = INFINITY;
@@ -948,15 +957,28 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
   uint32_t ntest = 0, ttest = 0, mtest = 0;
   int sp = 0, have = b->ntri > 0, done = 0;
   int32_t cur_child = b->root_child, cur_count = b->root_count;
+  /* seeded second phase: the seed hit is provisional, with t_max just
+     above it, until the traversal reaches the seed slot in its own order */
+  int prov = 0;
+  if (seed && seed->id >= 0) {
+    bt = seed->t; bid = seed->id; bu = seed->u; bv = seed->v;
+    tcur = nextafterf(seed->t, INFINITY);
+    prov = 1;
+  }
   while (!done) {
     if (have) {
-      if (cur_count > 0) {
+      if (seed && cur_child == seed->child && cur_count == seed->count) {
+        if (prov) tcur = bt; /* the seed now counts as found here */
+        have = 0;
+        continue;
+      } else if (cur_count > 0) {
         for (int32_t i = 0; i < cur_count; ++i) {
           int32_t tid = b->perm[cur_child + i];
           float t, u, v;
           ++ttest;
           if (mt_test(&r, tris + 9 * (size_t)tid, tcur, &t, &u, &v)) {
             bt = t; bid = tid; bu = u; bv = v;
+            prov = 0;
             if (mode == 1) { done = 1; break; }
             tcur = t;
           }
@@ -1037,7 +1059,7 @@ int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
   for (int64_t i = r_begin; i < r_end; ++i)
     trace_one(b, tris, rays + 8 * i, mode, cull, skip_bits, stride, stack, hit_t + i,
               hit_id + i,
-              hit_uv + 2 * i, counts + 2 * i, mask_tests ? mask_tests + i : NULL);
+              hit_uv + 2 * i, counts + 2 * i, mask_tests ? mask_tests + i : NULL, NULL);
   free(stack);
   return 0;
 }
@@ -1148,4 +1170,113 @@ int or_bounce(const float* ray8, float t, const float* tri9, uint32_t seed,
   out8[3] = 1e-4f;
   out8[7] = INFINITY;
   return 1;
+}
+
+/* ------------------------------------------------ learned-proposal seeds --- */
+/* Not in the paper.  Frontier of depth D: the slots at depth D below the
+   root (root slot depth 0) and leaf slots reached earlier, in pre-order
+   (left child first), with the box each slot's parent stores for it (the
+   root box for the root slot).  Returns their number; class_of_tri (or
+   NULL) gets the frontier index of every triangle id. */
+static void frontier_rec(const OrBvh* b, int32_t child, int32_t count, const float* box,
+                         int depth, int D, int32_t* fc, int32_t* fn, float* fbox, int* n,
+                         uint8_t* cls) {
+  if (count > 0 || depth == D) {
+    fc[*n] = child;
+    fn[*n] = count;
+    if (fbox) memcpy(fbox + 6 * *n, box, 6 * sizeof(float));
+    if (cls) {
+      /* every triangle below this slot */
+      int32_t stack_c[128], stack_n[128];
+      int sp = 0;
+      stack_c[sp] = child; stack_n[sp] = count; ++sp;
+      while (sp > 0) {
+        --sp;
+        int32_t c = stack_c[sp], k = stack_n[sp];
+        if (k > 0) {
+          for (int32_t i = 0; i < k; ++i) cls[b->perm[c + i]] = (uint8_t)*n;
+        } else {
+          stack_c[sp] = b->child[2 * c]; stack_n[sp] = b->count[2 * c]; ++sp;
+          stack_c[sp] = b->child[2 * c + 1]; stack_n[sp] = b->count[2 * c + 1]; ++sp;
+        }
+      }
+    }
+    ++*n;
+    return;
+  }
+  for (int c = 0; c < 2; ++c)
+    frontier_rec(b, b->child[2 * child + c], b->count[2 * child + c],
+                 b->box + 12 * (size_t)child + 6 * c, depth + 1, D, fc, fn, fbox, n, cls);
+}
+
+int or_bvh_frontier(const OrBvh* b, int D, int32_t* fchild, int32_t* fcount, float* fbox,
+                    uint8_t* cls) {
+  int n = 0;
+  if (b->ntri == 0) return 0;
+  frontier_rec(b, b->root_child, b->root_count, b->root_box, 0, D, fchild, fcount, fbox, &n,
+               cls);
+  return n;
+}
+
+/* Seeded closest-hit traversal.  A class outside [0, nf) means no seed:
+   the plain traversal.  Otherwise the seed slot's box is slab-tested with
+   the ray's tmax (one node test); if the ray enters it, phase 1 traverses
+   that subtree with the ray's tmax.  Phase 2 traverses from the root,
+   skipping the seed slot (phase 1 covered it, or the ray misses its box):
+   if phase 1 hit at t_s, phase 2 starts with that hit, held provisionally
+   with tmax = nextafterf(t_s, +inf) so that an equally distant triangle
+   met earlier in traversal order replaces it, and lowers tmax to t_s when
+   it reaches the seed slot; else it starts with the ray's tmax.  The
+   result is the plain traversal's closest hit; counts sum both phases. */
+int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_t n,
+                    int cull, int skip_bits, int stride, const int32_t* cls,
+                    const int32_t* fchild, const int32_t* fcount, const float* fbox, int nf,
+                    float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts) {
+  if (stride < 1) return -3;
+  if (cull && !b->masks) return -1;
+  if (cull == 2 && !b->clut) return -2;
+  if (cull && !b->raylut) {
+    int R3 = b->R * b->R * b->R;
+    uint32_t* lut = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)R3 * R3 * b->W);
+    or_raylut(b->R, lut);
+    ((OrBvh*)b)->raylut = lut;
+  }
+  StackEntry* stack = (StackEntry*)malloc(sizeof(StackEntry) * (size_t)(b->max_depth + 4));
+  OrBvh sub = *b; /* a view whose root is the seed slot */
+  for (int64_t i = 0; i < n; ++i) {
+    const float* r8 = rays + 8 * i;
+    float t1 = INFINITY, uv1[2] = {0.0f, 0.0f}, t2, uv2[2];
+    int32_t id1 = -1, id2;
+    uint32_t c1[2] = {0, 0}, c2[2], mt;
+    int k = cls[i];
+    if (k < 0 || k >= nf) {
+      trace_one(b, tris, r8, 0, cull, skip_bits, stride, stack, &t2, &id2, uv2, c2, &mt, NULL);
+    } else {
+      ORay r;
+      float tn, tf;
+      load_ray(r8, &r);
+      c1[0] = 1;
+      if (slab_test(&r, fbox + 6 * (size_t)k, r.tmax, &tn, &tf)) {
+        uint32_t cs[2];
+        sub.root_child = fchild[k];
+        sub.root_count = fcount[k];
+        trace_one(&sub, tris, r8, 0, cull, skip_bits, stride, stack, &t1, &id1, uv1, cs, &mt,
+                  NULL);
+        c1[0] += cs[0];
+        c1[1] += cs[1];
+      }
+      Seed sd;
+      sd.child = fchild[k];
+      sd.count = fcount[k];
+      sd.t = t1; sd.u = uv1[0]; sd.v = uv1[1]; sd.id = id1;
+      trace_one(b, tris, r8, 0, cull, skip_bits, stride, stack, &t2, &id2, uv2, c2, &mt, &sd);
+    }
+    hit_t[i] = t2;
+    hit_id[i] = id2;
+    if (hit_uv) { hit_uv[2 * i] = uv2[0]; hit_uv[2 * i + 1] = uv2[1]; }
+    counts[2 * i] = c1[0] + c2[0];
+    counts[2 * i + 1] = c1[1] + c2[1];
+  }
+  free(stack);
+  return 0;
 }

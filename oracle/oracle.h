@@ -99,6 +99,16 @@ uint32_t or_bounce_hash(uint32_t seed, uint32_t rid, uint32_t bounce, uint32_t k
 int or_bounce(const float* ray8, float t, const float* tri9, uint32_t seed,
               uint32_t rid, uint32_t bounce, float* out8);
 
+/* Learned-proposal seeds (not in the paper): the frontier of depth D in
+   pre-order (slot child/count and box), and the seeded closest-hit
+   traversal (see oracle.c). */
+int or_bvh_frontier(const OrBvh* b, int D, int32_t* fchild, int32_t* fcount, float* fbox,
+                    uint8_t* cls);
+int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_t n,
+                    int cull, int skip_bits, int stride, const int32_t* cls,
+                    const int32_t* fchild, const int32_t* fcount, const float* fbox, int nf,
+                    float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts);
+
 /* Single ray-triangle test and slab test, exposed for pins. */
 int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
                float* u, float* v);

@@ -1,0 +1,495 @@
+// mlp.cu — the learned proposal network: MLP 6 -> 64 -> 64 -> 256 (GELU),
+// BF16 weights, FP32 accumulation, trained on the GPU with these kernels.
+//
+// Input of a ray: its origin mapped to the scene box ([-1, 1]^3, with box
+// centre c and half extents h: (o - c) / h) and its direction.  Output: 256
+// logits, one per depth-8 subtree of the BVH (the "frontier").
+//
+// Parameter layout (floats, the same for the FP32 master copy, the BF16
+// copy, the gradient and both Adam moments):
+//   W1[64][6] @0, b1[64] @384, W2[64][64] @448, b2[64] @4544,
+//   W3[256][64] @4608, b3[256] @20992;  P = 21248.
+//
+// Training step (sc_mlp_grad, then sc_mlp_adam): forward over the batch
+// storing the pre-activations A1, A2 and dZ = (softmax(z) - onehot(y)) / B
+// (the gradient of the mean cross-entropy); weight gradients as split-K
+// reductions over the batch; the hidden backward dA = (dZ W) * gelu'(A);
+// Adam on the FP32 master copy, then re-rounding to BF16.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "host/internal.h"
+
+using namespace sc;
+
+namespace mlpk {
+
+constexpr int IN = 6, H = 64, OUT = 256;
+constexpr int OFF_W1 = 0, OFF_B1 = 384, OFF_W2 = 448, OFF_B2 = 4544, OFF_W3 = 4608,
+              OFF_B3 = 20992, P = 21248;
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ float gelu(float x) {
+  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
+         x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// Input features of one ray.
+__device__ __forceinline__ void features(const float4 ra, const float4 rb, const float* box,
+                                         float* x) {
+  x[0] = (ra.x - box[0]) / box[3];
+  x[1] = (ra.y - box[1]) / box[4];
+  x[2] = (ra.z - box[2]) / box[5];
+  x[3] = rb.x;
+  x[4] = rb.y;
+  x[5] = rb.z;
+}
+
+// Weights staged in shared memory as floats (from the BF16 copy).
+struct SmemW {
+  float w[P];
+};
+
+__device__ __forceinline__ void stage(SmemW& s, const __nv_bfloat16* wb) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s.w[i] = __bfloat162float(wb[i]);
+}
+
+// h1 = gelu(W1 x + b1), h2 = gelu(W2 h1 + b2); the pre-activations are
+// written to the rows a1 / a2 when those are not null (training).
+__device__ __forceinline__ void hidden(const SmemW& s, const float* x, float* a1, float* h1,
+                                       float* a2, float* h2) {
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    float acc = s.w[OFF_B1 + o];
+#pragma unroll
+    for (int i = 0; i < IN; ++i) acc += s.w[OFF_W1 + o * IN + i] * x[i];
+    if (a1) a1[o] = acc;
+    h1[o] = gelu(acc);
+  }
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    const float4* row = reinterpret_cast<const float4*>(&s.w[OFF_W2 + o * H]);
+    float acc0 = s.w[OFF_B2 + o], acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < H / 4; ++i) {
+      const float4 w = row[i];
+      acc0 += w.x * h1[4 * i];
+      acc1 += w.y * h1[4 * i + 1];
+      acc2 += w.z * h1[4 * i + 2];
+      acc3 += w.w * h1[4 * i + 3];
+    }
+    const float acc = (acc0 + acc1) + (acc2 + acc3);
+    if (a2) a2[o] = acc;
+    h2[o] = gelu(acc);
+  }
+}
+
+__device__ __forceinline__ float logit(const SmemW& s, const float* h2, int o) {
+  const float4* row = reinterpret_cast<const float4*>(&s.w[OFF_W3 + o * H]);
+  float acc0 = s.w[OFF_B3 + o], acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll
+  for (int i = 0; i < H / 4; ++i) {
+    const float4 w = row[i];
+    acc0 += w.x * h2[4 * i];
+    acc1 += w.y * h2[4 * i + 1];
+    acc2 += w.z * h2[4 * i + 2];
+    acc3 += w.w * h2[4 * i + 3];
+  }
+  return (acc0 + acc1) + (acc2 + acc3);
+}
+
+// Inference: top-1 class (and optionally all logits) of each ray; -1 when
+// the top-1 softmax probability is below min_prob (min_prob <= 0: never).
+__global__ void __launch_bounds__(kThreads) infer_kernel(const __nv_bfloat16* wb,
+                                                         const float4* rays, long long n,
+                                                         const float* box, int* cls,
+                                                         float* logits, float min_prob) {
+  extern __shared__ float4 smem_raw[];
+  SmemW& s = *reinterpret_cast<SmemW*>(smem_raw);
+  stage(s, wb);
+  __syncthreads();
+  float bx[6];
+  for (int k = 0; k < 6; ++k) bx[k] = box[k];
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    float x[IN], h1[H], h2[H];
+    features(__ldg(&rays[2 * r]), __ldg(&rays[2 * r + 1]), bx, x);
+    hidden(s, x, nullptr, h1, nullptr, h2);
+    float best = -INFINITY, se = 0.0f;  // running max and sum of exp(z - max)
+    int bi = 0;
+    for (int o = 0; o < OUT; ++o) {
+      const float z = logit(s, h2, o);
+      if (logits) logits[r * OUT + o] = z;
+      if (z > best) {
+        if (min_prob > 0.0f) se = se * expf(best - z) + 1.0f;
+        best = z;
+        bi = o;
+      } else if (min_prob > 0.0f) {
+        se += expf(z - best);
+      }
+    }
+    // top-1 probability = 1 / se
+    cls[r] = (min_prob > 0.0f && se * min_prob > 1.0f) ? -1 : bi;
+  }
+}
+
+// Training forward: A1, A2 and dZ = (softmax - onehot) / B; loss sum.
+__global__ void __launch_bounds__(kThreads) train_fwd_kernel(
+    const __nv_bfloat16* wb, const float4* rays, const int* labels, long long B,
+    const float* box, float* A1, float* A2, float* dZ, float* loss) {
+  extern __shared__ float4 smem_raw[];
+  SmemW& s = *reinterpret_cast<SmemW*>(smem_raw);
+  stage(s, wb);
+  __syncthreads();
+  float bx[6];
+  for (int k = 0; k < 6; ++k) bx[k] = box[k];
+  float lsum = 0.0f;
+  const float invB = 1.0f / (float)B;
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+       b += (long long)gridDim.x * blockDim.x) {
+    float x[IN], h1[H], h2[H];
+    features(__ldg(&rays[2 * b]), __ldg(&rays[2 * b + 1]), bx, x);
+    hidden(s, x, A1 + b * H, h1, A2 + b * H, h2);
+    float* z = dZ + b * OUT;
+    float m = -INFINITY;
+    for (int o = 0; o < OUT; ++o) {
+      const float v = logit(s, h2, o);
+      z[o] = v;
+      m = fmaxf(m, v);
+    }
+    float se = 0.0f;
+    for (int o = 0; o < OUT; ++o) se += expf(z[o] - m);
+    const int y = labels[b];
+    lsum += (logf(se) + m) - z[y];
+    const float inv = 1.0f / se;
+    for (int o = 0; o < OUT; ++o) z[o] = (expf(z[o] - m) * inv - (o == y ? 1.0f : 0.0f)) * invB;
+  }
+  // block reduction of the loss
+  __shared__ float red[kThreads];
+  red[threadIdx.x] = lsum;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] * invB);
+}
+
+// dW[o][i] += sum_b dA[b][o] * Hin[b][i] and db[o] += sum_b dA[b][o], where
+// Hin = gelu(Asrc) (act = 1), Asrc itself (act = 0) or the ray features
+// (act = 2, Asrc = rays).  Split-K over the batch: each block reduces a
+// batch slice for a 32 x 32 output tile and adds it atomically.
+constexpr int TG = 32, KB = 32;
+__global__ void __launch_bounds__(256) grad_w_kernel(const float* dA, int O, const float* Asrc,
+                                                     int I, int act, const float* box,
+                                                     long long B, long long slice, float* dW,
+                                                     float* db) {
+  __shared__ float sa[KB][TG + 1];
+  __shared__ float sh[KB][TG + 1];
+  const int o0 = blockIdx.y * TG, i0 = blockIdx.z * TG;
+  const long long b_begin = (long long)blockIdx.x * slice;
+  const long long b_end = b_begin + slice < B ? b_begin + slice : B;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float accb[4] = {0.f, 0.f, 0.f, 0.f};
+  for (long long b0 = b_begin; b0 < b_end; b0 += KB) {
+    for (int r = ty; r < KB; r += 8) {
+      const long long b = b0 + r;
+      const bool ok = b < b_end;
+      sa[r][tx] = (ok && o0 + tx < O) ? dA[b * O + o0 + tx] : 0.0f;
+      float hv = 0.0f;
+      if (ok && i0 + tx < I) {
+        if (act == 2) {
+          const float4* rr = reinterpret_cast<const float4*>(Asrc) + 2 * b;
+          float x[IN];
+          features(rr[0], rr[1], box, x);
+          hv = x[i0 + tx];
+        } else {
+          const float a = Asrc[b * I + i0 + tx];
+          hv = act ? gelu(a) : a;
+        }
+      }
+      sh[r][tx] = hv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < KB; ++r) {
+      const float hv = sh[r][tx];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float av = sa[r][ty + 8 * j];
+        acc[j] += av * hv;
+        if (blockIdx.z == 0 && tx == 0) accb[j] += av;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = o0 + ty + 8 * j, i = i0 + tx;
+    if (o < O && i < I) atomicAdd(&dW[o * I + i], acc[j]);
+    if (blockIdx.z == 0 && tx == 0 && o < O) atomicAdd(&db[o], accb[j]);
+  }
+}
+
+// dAprev[b][i] = (sum_o dA[b][o] * W[o][i]) * gelu'(Aprev[b][i]), W from
+// the BF16 copy (as used by the forward pass).
+template <int O>
+__global__ void __launch_bounds__(kThreads) back_hidden_kernel(const float* dA,
+                                                              const __nv_bfloat16* wb, int off_w,
+                                                              const float* Aprev, long long B,
+                                                              float* dAprev) {
+  extern __shared__ float4 smem_w4[];
+  float* w = reinterpret_cast<float*>(smem_w4);
+  for (int k = threadIdx.x; k < O * H; k += blockDim.x) w[k] = __bfloat162float(wb[off_w + k]);
+  __syncthreads();
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+       b += (long long)gridDim.x * blockDim.x) {
+    float acc[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) acc[i] = 0.0f;
+    for (int o = 0; o < O; ++o) {
+      const float g = dA[b * O + o];
+      const float4* row = reinterpret_cast<const float4*>(&w[o * H]);
+#pragma unroll
+      for (int i = 0; i < H / 4; ++i) {
+        const float4 v = row[i];
+        acc[4 * i] += g * v.x;
+        acc[4 * i + 1] += g * v.y;
+        acc[4 * i + 2] += g * v.z;
+        acc[4 * i + 3] += g * v.w;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) dAprev[b * H + i] = acc[i] * gelu_grad(Aprev[b * H + i]);
+  }
+}
+
+// Adam on the FP32 master copy; refreshes the BF16 copy; zeroes the
+// gradient.  bc1 = 1 / (1 - beta1^t), bc2 = 1 / (1 - beta2^t).
+__global__ void adam_kernel(float* w, __nv_bfloat16* wb, float* g, float* m, float* v, float lr,
+                            float beta1, float beta2, float eps, float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const float gi = g[i];
+  const float mi = beta1 * m[i] + (1.0f - beta1) * gi;
+  const float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi * bc1) / (sqrtf(vi * bc2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16_rn(wi);
+  g[i] = 0.0f;
+}
+
+__global__ void to_bf16_kernel(const float* w, __nv_bfloat16* wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// Training pairs from a traced wave: rays with a hit and their subtree
+// class (class_of_tri[hit id]), appended with a warp-aggregated atomic.
+__global__ void labels_kernel(const float4* rays, const float4* hits, long long n,
+                              const unsigned char* class_of_tri, float4* out_rays, int* out_lbl,
+                              unsigned* count, long long cap) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int cls = -1;
+  if (i < n) {
+    const int id = __float_as_int(hits[i].y);
+    if (id >= 0) cls = class_of_tri[id];
+  }
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned m = __ballot_sync(0xffffffffu, cls >= 0);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if ((int)lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (cls >= 0) {
+    const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
+    if (pos < cap) {
+      out_rays[2 * pos] = rays[2 * i];
+      out_rays[2 * pos + 1] = rays[2 * i + 1];
+      out_lbl[pos] = cls;
+    }
+  }
+}
+
+int num_sms() {
+  static std::once_flag f;
+  static int sms = 0;
+  std::call_once(f, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace mlpk
+
+#define CUDA_OK(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      fail(SC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+#define SC_TRY \
+  try {        \
+    clear_error();
+#define SC_CATCH                            \
+  }                                         \
+  catch (const Error& e) {                  \
+    set_error("%s", e.msg.c_str());         \
+    return e.code;                          \
+  }                                         \
+  catch (...) {                             \
+    set_error("unexpected internal error"); \
+    return SC_ERR_STATE;                    \
+  }
+
+namespace {
+
+constexpr size_t kSmemW = sizeof(mlpk::SmemW);
+
+void set_smem(const void* k) {
+  CUDA_OK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemW));
+}
+
+int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  const long long cap = (long long)mlpk::num_sms() * 2;
+  if (g > cap) g = cap;
+  return (int)(g > 0 ? g : 1);
+}
+
+void check_box(const float* box) {
+  if (!box) fail(SC_ERR_ARG, "mlp: NULL scene box");
+}
+
+}  // namespace
+
+extern "C" {
+
+int sc_mlp_num_params(void) { return mlpk::P; }
+
+size_t sc_mlp_train_workspace_bytes(int64_t batch) {
+  return (size_t)batch * (3 * mlpk::H + mlpk::OUT) * 4 + 256;
+}
+
+sc_status sc_mlp_to_bf16(const float* d_w, void* d_wb, void* stream) {
+  SC_TRY
+  if (!d_w || !d_wb) fail(SC_ERR_ARG, "sc_mlp_to_bf16: NULL argument");
+  mlpk::to_bf16_kernel<<<(mlpk::P + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      d_w, reinterpret_cast<__nv_bfloat16*>(d_wb));
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_forward(const void* d_wb, const float* d_rays, int64_t n, const float* d_box,
+                         int32_t* d_cls, float* d_logits, float min_prob, void* stream) {
+  SC_TRY
+  check_box(d_box);
+  if (n < 0 || (n > 0 && (!d_wb || !d_rays || !d_cls))) fail(SC_ERR_ARG, "sc_mlp_forward: bad args");
+  if (n == 0) return SC_OK;
+  set_smem((const void*)mlpk::infer_kernel);
+  mlpk::infer_kernel<<<grid_for(n, mlpk::kThreads), mlpk::kThreads, kSmemW,
+                       reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const __nv_bfloat16*>(d_wb), reinterpret_cast<const float4*>(d_rays), n,
+      d_box, d_cls, d_logits, min_prob);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_grad(const void* d_wb, const float* d_rays, const int32_t* d_labels,
+                      int64_t batch, const float* d_box, float* d_grad, float* d_loss,
+                      void* d_ws, size_t ws_bytes, void* stream) {
+  SC_TRY
+  check_box(d_box);
+  if (batch <= 0 || !d_wb || !d_rays || !d_labels || !d_grad || !d_loss || !d_ws)
+    fail(SC_ERR_ARG, "sc_mlp_grad: bad arguments");
+  if (ws_bytes < sc_mlp_train_workspace_bytes(batch)) fail(SC_ERR_ARG, "sc_mlp_grad: workspace too small");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  using namespace mlpk;
+  float* A1 = reinterpret_cast<float*>(d_ws);
+  float* A2 = A1 + batch * H;
+  float* dZ = A2 + batch * H;
+  const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(d_wb);
+  CUDA_OK(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
+  set_smem((const void*)train_fwd_kernel);
+  train_fwd_kernel<<<grid_for(batch, kThreads), kThreads, kSmemW, st>>>(
+      wb, reinterpret_cast<const float4*>(d_rays), d_labels, batch, d_box, A1, A2, dZ, d_loss);
+  CUDA_OK(cudaGetLastError());
+  // layer 3: dW3 = dZ^T h2, db3
+  const long long slice = 512;  // batch rows per split-K block
+  const unsigned nsl = (unsigned)((batch + slice - 1) / slice);
+  grad_w_kernel<<<dim3(nsl, OUT / TG, H / TG), 256, 0, st>>>(dZ, OUT, A2, H, 1, d_box, batch,
+                                                              slice, d_grad + OFF_W3,
+                                                              d_grad + OFF_B3);
+  CUDA_OK(cudaGetLastError());
+  // dA2 = (dZ W3) * gelu'(A2), after dZ in the workspace
+  float* dAh = dZ + batch * OUT;
+  CUDA_OK(cudaFuncSetAttribute((const void*)back_hidden_kernel<OUT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, OUT * H * 4));
+  back_hidden_kernel<OUT><<<grid_for(batch, kThreads), kThreads, OUT * H * 4, st>>>(
+      dZ, wb, OFF_W3, A2, batch, dAh);
+  CUDA_OK(cudaGetLastError());
+  // layer 2: dW2 = dA2^T h1, db2
+  grad_w_kernel<<<dim3(nsl, H / TG, H / TG), 256, 0, st>>>(dAh, H, A1, H, 1, d_box, batch, slice,
+                                                            d_grad + OFF_W2, d_grad + OFF_B2);
+  CUDA_OK(cudaGetLastError());
+  // dA1 = (dA2 W2) * gelu'(A1) -> into A2 (no longer needed)
+  back_hidden_kernel<H><<<grid_for(batch, kThreads), kThreads, H * H * 4, st>>>(
+      dAh, wb, OFF_W2, A1, batch, A2);
+  CUDA_OK(cudaGetLastError());
+  // layer 1: dW1 = dA1^T x, db1
+  grad_w_kernel<<<dim3(nsl, H / TG, 1), 256, 0, st>>>(A2, H, d_rays, IN, 2, d_box, batch, slice,
+                                                       d_grad + OFF_W1, d_grad + OFF_B1);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_adam(float* d_w, void* d_wb, float* d_grad, float* d_m, float* d_v, int step,
+                      float lr, float beta1, float beta2, float eps, void* stream) {
+  SC_TRY
+  if (!d_w || !d_wb || !d_grad || !d_m || !d_v || step < 1) fail(SC_ERR_ARG, "sc_mlp_adam: bad args");
+  const float bc1 = 1.0f / (1.0f - std::pow(beta1, (float)step));
+  const float bc2 = 1.0f / (1.0f - std::pow(beta2, (float)step));
+  mlpk::adam_kernel<<<(mlpk::P + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      d_w, reinterpret_cast<__nv_bfloat16*>(d_wb), d_grad, d_m, d_v, lr, beta1, beta2, eps, bc1,
+      bc2);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_labels(const float* d_rays, const void* d_hits, int64_t n,
+                        const uint8_t* d_class_of_tri, float* d_out_rays, int32_t* d_out_labels,
+                        uint32_t* d_count, int64_t cap, void* stream) {
+  SC_TRY
+  if (n < 0 || (n > 0 && (!d_rays || !d_hits || !d_class_of_tri || !d_out_rays || !d_out_labels ||
+                          !d_count)))
+    fail(SC_ERR_ARG, "sc_mlp_labels: bad arguments");
+  if (n == 0) return SC_OK;
+  mlpk::labels_kernel<<<(unsigned)((n + 255) / 256), 256, 0,
+                        reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float4*>(d_rays), reinterpret_cast<const float4*>(d_hits), n,
+      d_class_of_tri, reinterpret_cast<float4*>(d_out_rays), d_out_labels, d_count, cap);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+}  // extern "C"

@@ -18,6 +18,10 @@ WaveKernelFn get_waves_plain(int block, int stack);
 WaveKernelFn get_waves_r4(int cull, int lutv, int scales);
 WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack);
 WaveKernelFn get_waves_r8(int cull, int lutv, int scales);
+SeededKernelFn get_seeded_plain();
+SeededKernelFn get_seeded_r4(int cull, int lutv, int scales);
+SeededKernelFn get_seeded_r6(int cull, int lutv, int scales);
+SeededKernelFn get_seeded_r8(int cull, int lutv, int scales);
 }  // namespace sct
 
 using namespace sc;
@@ -254,6 +258,9 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
     wp.hits[w] = reinterpret_cast<float4*>(outs[w].hits);
     wp.path[w] = outs[w].path;
     wp.counts[w] = reinterpret_cast<uint2*>(outs[w].counts);
+    wp.orays[w] = reinterpret_cast<float4*>(outs[w].rays);
+    if (reinterpret_cast<uintptr_t>(outs[w].rays) & 15)
+      fail(SC_ERR_ARG, "sc_trace_waves: misaligned ray output of wave %d", w);
   }
   wp.bounces = bounces;
   wp.seed = seed;
@@ -367,6 +374,71 @@ sc_status sc_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_h
   SC_TRY
   launch_trace(d, d_rays, n, d_hits, d_counts, mode, cull, opts, d_work, work_bytes,
                reinterpret_cast<cudaStream_t>(stream));
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_trace_seeded(const sc_dbvh* d, const float* d_rays, int64_t n, const int32_t* d_cls,
+                          const sc_frontier_entry* d_frontier, int n_frontier, sc_hit* d_hits,
+                          uint32_t* d_counts, int cull, const sc_trace_opts* opts, void* d_work,
+                          size_t work_bytes, void* stream) {
+  SC_TRY
+  if (!d) fail(SC_ERR_ARG, "sc_trace_seeded: NULL device BVH");
+  if (n < 0 || n > (int64_t)0x7FFFFF00) fail(SC_ERR_ARG, "sc_trace_seeded: n out of range");
+  if (n > 0 && (!d_rays || !d_hits || !d_cls || !d_frontier))
+    fail(SC_ERR_ARG, "sc_trace_seeded: NULL buffer");
+  if (n_frontier < 1 || n_frontier > 256) fail(SC_ERR_ARG, "sc_trace_seeded: n_frontier 1..256");
+  if (!d_work || work_bytes < kWorkBytes) fail(SC_ERR_ARG, "sc_trace_seeded: workspace too small");
+  if ((reinterpret_cast<uintptr_t>(d_rays) & 15) || (reinterpret_cast<uintptr_t>(d_hits) & 15) ||
+      (reinterpret_cast<uintptr_t>(d_counts) & 7) || (reinterpret_cast<uintptr_t>(d_frontier) & 15))
+    fail(SC_ERR_ARG, "sc_trace_seeded: misaligned buffer");
+  if (cull && d->lay.R == 0) fail(SC_ERR_STATE, "sc_trace_seeded: culling needs a masked image");
+  if (d->stack_need > sct::kStack)
+    fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
+         sct::kStack);
+  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
+  if (opts) o = *opts;
+  if ((o.block && o.block != kBlock) || (o.stack && o.stack != sct::kStack))
+    fail(SC_ERR_UNSUPPORTED, "sc_trace_seeded: default block and stack only");
+  if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
+  int lutv = lut_variant(d, o.lut_mode);
+  if (lutv == 1 || lutv == 3) lutv = 0;
+  sct::SeededKernelFn k = nullptr;
+  if (!cull) {
+    k = sct::get_seeded_plain();
+  } else {
+    const int c = d->lay.compress ? 2 : 1, sc = d->lay.scales;
+    switch (d->lay.R) {
+      case 4: k = sct::get_seeded_r4(c, lutv, sc); break;
+      case 6: k = sct::get_seeded_r6(c, lutv, sc); break;
+      case 8: k = sct::get_seeded_r8(c, lutv, sc); break;
+      default: fail(SC_ERR_UNSUPPORTED, "no seeded kernel for R = %d", d->lay.R);
+    }
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_OK(cudaMemsetAsync(d_work, 0, kWorkBytes, st));
+  if (n == 0) return SC_OK;
+  DevInfo di = device_info();
+  int per_sm = o.blocks_per_sm;
+  if (per_sm <= 0) {
+    CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, kBlock, 0));
+    if (per_sm < 1) per_sm = 1;
+  }
+  int64_t grid = (int64_t)di.sms * per_sm, need = (n + kBlock - 1) / kBlock;
+  if (grid > need) grid = need;
+  sct::Params p;
+  std::memset(&p, 0, sizeof(p));
+  fill_params(d, p);
+  p.rays = reinterpret_cast<const float4*>(d_rays);
+  p.hits = reinterpret_cast<float4*>(d_hits);
+  p.counts = reinterpret_cast<uint2*>(d_counts);
+  p.work = reinterpret_cast<unsigned*>(d_work);
+  p.status = p.work + 1;
+  p.n = n;
+  p.refill = o.refill ? o.refill : kDefaultRefill;
+  k<<<(unsigned)grid, kBlock, 0, st>>>(p, d_cls, reinterpret_cast<const float4*>(d_frontier),
+                                       n_frontier);
+  CUDA_OK(cudaGetLastError());
   return SC_OK;
   SC_CATCH
 }

@@ -538,6 +538,7 @@ struct WaveParams {
   float4* hits[kMaxWaves];     // per wave: {t, id, u, v}
   int* path[kMaxWaves];        // per wave: path id (primary ray index)
   uint2* counts[kMaxWaves];    // per wave, optional
+  float4* orays[kMaxWaves];    // per wave, optional: the traced rays
   int bounces;
   unsigned seed;
   unsigned long long timeout_ns;
@@ -704,6 +705,10 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
           wp.hits[w][o] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
           if (wp.path[w]) wp.path[w][o] = (int)pid;
           if (wp.counts[w]) wp.counts[w][o] = make_uint2(s.ntest, s.ttest);
+          if (wp.orays[w]) {
+            wp.orays[w][2 * o] = __ldcg(&rays[2 * rid]);
+            wp.orays[w][2 * o + 1] = __ldcg(&rays[2 * rid + 1]);
+          }
           if (w < wp.bounces && s.hid >= 0) {
             const float4* tp = p.tris + 3 * (long long)s.hpos;
             spawn = make_bounce(s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.ht, __ldg(tp + 1),
@@ -735,7 +740,111 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
   }
 }
 
+// Slab test of one box (lo = b0.xyz, hi = (b0.w, b1.x, b1.y)) on [tmin,
+// tmax], in the same arithmetic as the child tests of trace_step.
+__device__ __forceinline__ bool box_hit(const RayState& s, const float4 b0, const float4 b1,
+                                        float tmax) {
+  const float lo[3] = {b0.x, b0.y, b0.z}, hi[3] = {b0.w, b1.x, b1.y};
+  const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+  float a0[3], a1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
+    a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
+  }
+  const float tn = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
+                         fmaxf(fminf(a0[2], a1[2]), s.tmin));
+  const float tf = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
+                         fminf(fmaxf(a0[2], a1[2]), tmax));
+  return tn <= __fmul_rn(tf, kRobust);
+}
+
+// Seeded closest-hit traversal (learned proposal; not in the paper).
+// frontier: entries of 2 float4 = box lo.xyz, hi.x | hi.yz, slot word, 0.
+// A class outside [0, nfront) traces the ray without a seed.  Otherwise
+// the seed box is slab-tested with the ray's t_max (one node test); if the
+// ray enters it, phase 1 traverses the seed subtree with that t_max.
+// Phase 2 traverses from the root and skips the seed slot (phase 1 covered
+// it, or the ray misses its box).  A phase-1 hit at t_s is held
+// provisionally with t_max = nextafter(t_s, +inf), so that an equally
+// distant triangle met earlier in traversal order replaces it, and t_max
+// drops to t_s when phase 2 reaches the seed slot: the result is the
+// plain traversal's closest hit.  Counts sum both phases.
+template <int R, int CULL, int LUTV, int SCALES>
+__global__ void __launch_bounds__(kBlock) seeded_kernel(Params p, const int* cls,
+                                                        const float4* frontier, int nfront) {
+  constexpr int RR = (R > 0 ? R : 4);
+  __shared__ SharedTables<RR, LUTV> sh;
+  if constexpr (CULL != 0) {
+    stage_tables(sh, p);
+    __syncthreads();
+  }
+  uint2 stack[kStack];
+  RayState s;
+  s.have = false;
+  long long rid = -1;
+  float tmax0 = 0.0f;
+  int phase = 0, seed_pos = -1;
+  uint32_t seed = 0u;
+  bool has_seed = false, active = false, exhausted = false;
+  for (;;) {
+    const long long r = warp_fetch(active, &p.work[0], p.n, p.refill, exhausted);
+    if (r >= 0) {
+      rid = r;
+      active = true;
+      const float4 rb = __ldg(&p.rays[2 * r + 1]);
+      ray_init(s, __ldg(&p.rays[2 * r]), rb, p);
+      tmax0 = rb.w;
+      seed_pos = -1;
+      has_seed = false;
+      phase = 2;
+      s.cur = p.root_slot;
+      s.have = p.has_root != 0;
+      const int c = cls[r];
+      if (p.has_root && c >= 0 && c < nfront) {
+        const float4 e0 = __ldg(&frontier[2 * c]), e1 = __ldg(&frontier[2 * c + 1]);
+        seed = __float_as_uint(e1.z);
+        if (!slot_ok(seed, -1, p)) {
+          atomicOr(p.status, (unsigned)ST_BAD_NODE);
+        } else {
+          has_seed = true;
+          ++s.ntest;
+          if (box_hit(s, e0, e1, tmax0)) {
+            phase = 1;
+            s.cur = seed;
+          }
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (!active) continue;
+    if (phase == 2 && has_seed && s.have && s.cur == seed) {
+      if (s.hid >= 0 && s.hpos == seed_pos) s.tcur = s.ht;  // the seed counts as found here
+      s.have = false;
+    }
+    if (trace_step<R, CULL, 0, LUTV, SCALES>(p, s, stack, sh)) {
+      if (phase == 1) {
+        phase = 2;
+        s.sp = 0;
+        s.cur = p.root_slot;
+        s.have = p.has_root != 0;
+        if (s.hid >= 0) {
+          seed_pos = s.hpos;
+          s.tcur = nextafterf(s.ht, __int_as_float(0x7f800000));
+        } else {
+          s.tcur = tmax0;
+        }
+        continue;
+      }
+      p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+      if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
+      active = false;
+    }
+  }
+}
+
 typedef void (*KernelFn)(Params);
+typedef void (*SeededKernelFn)(Params, const int*, const float4*, int);
 typedef void (*WaveKernelFn)(WaveParams);
 
 // Block size x stack depth variants of one wave kernel (for the autotuner):

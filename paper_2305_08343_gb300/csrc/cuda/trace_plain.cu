@@ -12,4 +12,6 @@ WaveKernelFn get_waves_plain(int block, int stack) {
   return WaveVariants<0, 0, 0, 0>::get(block, stack);
 }
 
+SeededKernelFn get_seeded_plain() { return seeded_kernel<0, 0, 0, 0>; }
+
 }  // namespace sct

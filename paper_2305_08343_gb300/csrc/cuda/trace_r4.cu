@@ -31,4 +31,10 @@ WaveKernelFn get_waves_r4(int cull, int lutv, int scales) {
   return comp[lutv][scales];
 }
 
+SeededKernelFn get_seeded_r4(int cull, int lutv, int scales) {
+  if (cull == 1) return scales ? seeded_kernel<4, 1, 0, 1> : seeded_kernel<4, 1, 0, 0>;
+  if (lutv == 2) return scales ? seeded_kernel<4, 2, 2, 1> : seeded_kernel<4, 2, 2, 0>;
+  return scales ? seeded_kernel<4, 2, 0, 1> : seeded_kernel<4, 2, 0, 0>;
+}
+
 }  // namespace sct

@@ -29,4 +29,10 @@ WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack) 
   return scales ? waves_kernel<6, 2, 0, 1> : waves_kernel<6, 2, 0, 0>;
 }
 
+SeededKernelFn get_seeded_r6(int cull, int lutv, int scales) {
+  if (cull == 1) return scales ? seeded_kernel<6, 1, 0, 1> : seeded_kernel<6, 1, 0, 0>;
+  if (lutv == 2) return scales ? seeded_kernel<6, 2, 2, 1> : seeded_kernel<6, 2, 2, 0>;
+  return scales ? seeded_kernel<6, 2, 0, 1> : seeded_kernel<6, 2, 0, 0>;
+}
+
 }  // namespace sct

@@ -27,4 +27,10 @@ WaveKernelFn get_waves_r8(int cull, int lutv, int scales) {
   return comp[lutv == 2 ? 1 : 0][scales];
 }
 
+SeededKernelFn get_seeded_r8(int cull, int lutv, int scales) {
+  if (cull == 1) return scales ? seeded_kernel<8, 1, 0, 1> : seeded_kernel<8, 1, 0, 0>;
+  if (lutv == 2) return scales ? seeded_kernel<8, 2, 2, 1> : seeded_kernel<8, 2, 2, 0>;
+  return scales ? seeded_kernel<8, 2, 0, 1> : seeded_kernel<8, 2, 0, 0>;
+}
+
 }  // namespace sct

@@ -1,6 +1,8 @@
 // api.cpp — host entry points of the C-ABI (include/subcull.h): inputs,
 // build, export and image packing.  Device entry points live in
 // cuda/trace.cu.  No exception leaves these functions.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -197,6 +199,63 @@ sc_status sc_bvh_export(const sc_bvh* h, int32_t* root2, int32_t* child, int32_t
     if (clut) std::memcpy(clut, b.clut.data(), 4 * b.clut.size());
     if (cidx) std::memcpy(cidx, b.cidx.data(), b.cidx.size());
   }
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_bvh_frontier(const sc_bvh* h, int depth, sc_frontier_entry* out, int cap,
+                          int* n_slots, uint8_t* class_of_tri) {
+  SC_TRY
+  if (!h || !out || !n_slots || depth < 0 || depth > 8 || cap < 1)
+    fail(SC_ERR_ARG, "sc_bvh_frontier: bad argument (depth 0..8)");
+  const Bvh& b = h->b;
+  int n = 0;
+  *n_slots = 0;
+  if (b.ntri == 0) return SC_OK;
+  struct It {
+    int32_t child, count;
+    int depth;
+    const float* box;
+  };
+  std::vector<It> st;
+  st.push_back(It{b.root_child, b.root_count, 0, b.root_box});
+  while (!st.empty()) {
+    It it = st.back();
+    st.pop_back();
+    if (it.count > 0 || it.depth == depth) {
+      if (n >= cap) fail(SC_ERR_NOMEM, "sc_bvh_frontier: more than %d slots", cap);
+      sc_frontier_entry& e = out[n];
+      std::memcpy(e.lo, it.box, 3 * sizeof(float));
+      std::memcpy(e.hi, it.box + 3, 3 * sizeof(float));
+      e.slot = it.count > 0 ? (kLeafBit | ((uint32_t)(it.count - 1) << 28) | (uint32_t)it.child)
+                            : (uint32_t)it.child;
+      e.reserved = 0;
+      if (class_of_tri) {
+        // the triangle positions of a subtree form one contiguous range
+        int64_t lo = INT64_MAX, hi = -1;
+        std::vector<It> sub{it};
+        while (!sub.empty()) {
+          It x = sub.back();
+          sub.pop_back();
+          if (x.count > 0) {
+            lo = std::min<int64_t>(lo, x.child);
+            hi = std::max<int64_t>(hi, (int64_t)x.child + x.count);
+          } else {
+            for (int c = 0; c < 2; ++c)
+              sub.push_back(It{b.child[2 * x.child + c], b.count[2 * x.child + c], 0, nullptr});
+          }
+        }
+        for (int64_t pos = lo; pos < hi; ++pos) class_of_tri[b.perm[pos]] = (uint8_t)n;
+      }
+      ++n;
+      continue;
+    }
+    // push the right child first: pre-order visits the left subtree first
+    for (int c = 1; c >= 0; --c)
+      st.push_back(It{b.child[2 * it.child + c], b.count[2 * it.child + c], it.depth + 1,
+                      &b.box[12 * (size_t)it.child + 6 * c]});
+  }
+  *n_slots = n;
   return SC_OK;
   SC_CATCH
 }

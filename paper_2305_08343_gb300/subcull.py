@@ -54,7 +54,8 @@ class sc_bvh_info(C.Structure):
 
 
 class sc_wave_out(C.Structure):
-    _fields_ = [("hits", C.c_void_p), ("path", C.c_void_p), ("counts", C.c_void_p)]
+    _fields_ = [("hits", C.c_void_p), ("path", C.c_void_p), ("counts", C.c_void_p),
+                ("rays", C.c_void_p)]
 
 
 SC_MAX_BOUNCES = 4
@@ -115,6 +116,17 @@ def lib():
             "sc_trace_waves": (C.c_int, [vp, vp, i64, C.c_int, C.c_uint32, C.c_int,
                                          P(sc_wave_out), P(sc_trace_opts), vp, C.c_size_t, vp]),
             "sc_waves_poll": (C.c_int, [vp, C.c_int, u32p, vp]),
+            "sc_bvh_frontier": (C.c_int, [vp, C.c_int, vp, C.c_int, P(C.c_int), u8p]),
+            "sc_trace_seeded": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, vp, vp, C.c_int,
+                                          P(sc_trace_opts), vp, C.c_size_t, vp]),
+            "sc_mlp_num_params": (C.c_int, []),
+            "sc_mlp_to_bf16": (C.c_int, [vp, vp, vp]),
+            "sc_mlp_forward": (C.c_int, [vp, vp, i64, vp, vp, vp, C.c_float, vp]),
+            "sc_mlp_train_workspace_bytes": (C.c_size_t, [i64]),
+            "sc_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_size_t, vp]),
+            "sc_mlp_adam": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float,
+                                      C.c_float, C.c_float, vp]),
+            "sc_mlp_labels": (C.c_int, [vp, vp, i64, vp, vp, vp, vp, i64, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -360,16 +372,25 @@ def sc_trace_waves_workspace_bytes(n0: int, opts: sc_trace_opts | None = None) -
     return int(lib().sc_trace_waves_workspace_bytes(n0, C.byref(opts) if opts else None))
 
 
-def sc_trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, outs, ws,
-                   opts: sc_trace_opts | None = None, stream=None):
-    """outs: list of bounces+1 (hits float32[n0,4], path int32[n0] | None,
-    counts int32[n0,2] | None) device tensors; ws: uint8 device tensor."""
-    n0 = rays.shape[0]
+def _wave_arr(outs, bounces: int):
     arr = (sc_wave_out * (bounces + 1))()
-    for w, (h, pth, cnt) in enumerate(outs):
+    for w, o in enumerate(outs):
+        h, pth, cnt = o[0], o[1], o[2]
+        ry = o[3] if len(o) > 3 else None
         arr[w].hits = h.data_ptr()
         arr[w].path = pth.data_ptr() if pth is not None else None
         arr[w].counts = cnt.data_ptr() if cnt is not None else None
+        arr[w].rays = ry.data_ptr() if ry is not None else None
+    return arr
+
+
+def sc_trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, outs, ws,
+                   opts: sc_trace_opts | None = None, stream=None):
+    """outs: list of bounces+1 (hits float32[n0,4], path int32[n0] | None,
+    counts int32[n0,2] | None[, rays float32[n0,8] | None]) device tensors;
+    ws: uint8 device tensor."""
+    n0 = rays.shape[0]
+    arr = _wave_arr(outs, bounces)
     o = opts or _opts()
     _check(lib().sc_trace_waves(dbvh.handle, C.c_void_p(rays.data_ptr()), n0, bounces,
                                 seed & 0xFFFFFFFF, cull, arr, C.byref(o),
@@ -386,7 +407,8 @@ def sc_waves_poll(ws, bounces: int, stream=None):
 class WaveBuffers:
     """Device outputs and workspace for sc_trace_waves (torch-owned)."""
 
-    def __init__(self, n0: int, bounces: int, with_counts: bool = True, device="cuda"):
+    def __init__(self, n0: int, bounces: int, with_counts: bool = True, device="cuda",
+                 with_rays: bool = False):
         import torch
         self.n0, self.bounces = n0, bounces
         self.hits = [torch.empty((n0, 4), dtype=torch.float32, device=device)
@@ -394,6 +416,8 @@ class WaveBuffers:
         self.path = [torch.empty(n0, dtype=torch.int32, device=device) for _ in range(bounces + 1)]
         self.counts = [torch.empty((n0, 2), dtype=torch.int32, device=device) if with_counts
                        else None for _ in range(bounces + 1)]
+        self.rays = [torch.empty((n0, 8), dtype=torch.float32, device=device) if with_rays
+                     else None for _ in range(bounces + 1)]
         nb = sc_trace_waves_workspace_bytes(n0)  # largest chunk: fits every wave_chunk
         # 256-byte aligned view into a slightly larger buffer
         self._raw = torch.empty(nb + 256, dtype=torch.uint8, device=device)
@@ -401,7 +425,7 @@ class WaveBuffers:
         self.ws = self._raw[off:off + nb]
 
     def outs(self):
-        return list(zip(self.hits, self.path, self.counts))
+        return list(zip(self.hits, self.path, self.counts, self.rays))
 
 
 def trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, buffers=None,
@@ -419,12 +443,7 @@ def sc_autotune_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int,
     """Times the wave pipeline over block / stack / refill / wave-chunk
     candidates; returns (best opts, list of (block, stack, refill, chunk, ms))."""
     n0 = rays.shape[0]
-    outs = buffers.outs()
-    arr = (sc_wave_out * (bounces + 1))()
-    for w, (h, pth, cnt) in enumerate(outs):
-        arr[w].hits = h.data_ptr()
-        arr[w].path = pth.data_ptr() if pth is not None else None
-        arr[w].counts = cnt.data_ptr() if cnt is not None else None
+    arr = _wave_arr(buffers.outs(), bounces)
     best = sc_trace_opts()
     cap = 256
     res = (sc_tune_result * cap)()
@@ -438,3 +457,81 @@ def sc_autotune_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int,
                                    C.byref(best), res, cap, C.byref(nres), _stream_ptr(stream)))
     rows = [(r.block, r.stack, r.refill, r.wave_chunk, r.ms) for r in res[: min(nres.value, cap)]]
     return best, rows
+
+
+# --------------------------------------------------------- learned proposal --
+
+class sc_frontier_entry(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("slot", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+def sc_bvh_frontier(bvh: Bvh, depth: int = 8):
+    """Frontier entries as float32[k][8] (lo.xyz, hi.xyz, slot word bits, 0)
+    and the class of each triangle id (uint8[num_tris])."""
+    cap = 1 << depth
+    ent = np.zeros((cap, 8), np.float32)
+    ntri = bvh.info().num_tris
+    cls = np.zeros(max(ntri, 1), np.uint8)
+    n = C.c_int()
+    _check(lib().sc_bvh_frontier(bvh.handle, depth, ent.ctypes.data_as(C.c_void_p), cap,
+                                 C.byref(n), _ptr(cls, C.c_uint8)))
+    return ent[: n.value].copy(), cls[:ntri].copy()
+
+
+def sc_trace_seeded(dbvh: DeviceBVH, rays, cls, frontier, hits, counts, cull: int, work,
+                    opts: sc_trace_opts | None = None, stream=None):
+    """rays float32[n,8], cls int32[n], frontier float32[k,8] entries
+    (device); hits float32[n,4]; counts int32[n,2] or None; work: uint8."""
+    o = opts or _opts()
+    _check(lib().sc_trace_seeded(dbvh.handle, C.c_void_p(rays.data_ptr()), rays.shape[0],
+                                 C.c_void_p(cls.data_ptr()), C.c_void_p(frontier.data_ptr()),
+                                 frontier.shape[0], C.c_void_p(hits.data_ptr()),
+                                 C.c_void_p(counts.data_ptr()) if counts is not None else None,
+                                 cull, C.byref(o), C.c_void_p(work.data_ptr()), work.numel(),
+                                 _stream_ptr(stream)))
+
+
+def sc_mlp_num_params() -> int:
+    return int(lib().sc_mlp_num_params())
+
+
+def sc_mlp_to_bf16(w, wb, stream=None):
+    _check(lib().sc_mlp_to_bf16(C.c_void_p(w.data_ptr()), C.c_void_p(wb.data_ptr()),
+                                _stream_ptr(stream)))
+
+
+def sc_mlp_forward(wb, rays, box, cls, logits=None, min_prob: float = 0.0, stream=None):
+    _check(lib().sc_mlp_forward(C.c_void_p(wb.data_ptr()), C.c_void_p(rays.data_ptr()),
+                                rays.shape[0], C.c_void_p(box.data_ptr()),
+                                C.c_void_p(cls.data_ptr()),
+                                C.c_void_p(logits.data_ptr()) if logits is not None else None,
+                                min_prob, _stream_ptr(stream)))
+
+
+def sc_mlp_train_workspace_bytes(batch: int) -> int:
+    return int(lib().sc_mlp_train_workspace_bytes(batch))
+
+
+def sc_mlp_grad(wb, rays, labels, box, grad, loss, ws, stream=None):
+    _check(lib().sc_mlp_grad(C.c_void_p(wb.data_ptr()), C.c_void_p(rays.data_ptr()),
+                             C.c_void_p(labels.data_ptr()), rays.shape[0],
+                             C.c_void_p(box.data_ptr()), C.c_void_p(grad.data_ptr()),
+                             C.c_void_p(loss.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
+                             _stream_ptr(stream)))
+
+
+def sc_mlp_adam(w, wb, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8,
+                stream=None):
+    _check(lib().sc_mlp_adam(C.c_void_p(w.data_ptr()), C.c_void_p(wb.data_ptr()),
+                             C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
+                             C.c_void_p(v.data_ptr()), step, lr, beta1, beta2, eps,
+                             _stream_ptr(stream)))
+
+
+def sc_mlp_labels(rays, hits, class_of_tri, out_rays, out_labels, count, stream=None):
+    _check(lib().sc_mlp_labels(C.c_void_p(rays.data_ptr()), C.c_void_p(hits.data_ptr()),
+                               rays.shape[0], C.c_void_p(class_of_tri.data_ptr()),
+                               C.c_void_p(out_rays.data_ptr()),
+                               C.c_void_p(out_labels.data_ptr()), C.c_void_p(count.data_ptr()),
+                               out_labels.shape[0], _stream_ptr(stream)))

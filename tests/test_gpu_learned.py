@@ -1,0 +1,303 @@
+"""Learned proposal on the GPU (not in the paper), through the C-ABI.
+
+* Seeded traversal: hits (all four words) and per-ray counts bit-identical
+  to the oracle's seeded traversal for seeded-random classes (including
+  out-of-range ones, which mean "no seed"); hits identical to sc_trace.
+* Network kernels against the fp64 reference (oracle/mlp.py, pinned by
+  finite differences): BF16 rounding exact; logits within 1e-4; top-1
+  agreement >= 99.9% away from ties; every gradient tensor within 1e-3
+  relative L2 (FP32 accumulation order differs); Adam within 1e-5.
+* Training: the trained network beats the untrained and most-frequent-label
+  controls on held-out rays, and the seeded traversal keeps exact hits.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2305_08343_gb300 import learned
+from paper_2305_08343_gb300 import scenegen as sg
+from paper_2305_08343_gb300 import subcull as sc
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+def _bits(a):
+    return np.ascontiguousarray(a).view(np.int32)
+
+
+@pytest.fixture(scope="module")
+def scene():
+    """1,024 strands x 16 segments x 2 + ground = 32,770 triangles, 96x64 rays."""
+    return sg.hair(1024, 16, True, seed=21), sg.pinhole(96, 64)
+
+
+def _gpu_seeded(b, layout, rays, cls, depth, cull):
+    d = sc.DeviceBVH(b, layout)
+    ent, _ = sc.sc_bvh_frontier(b, depth)
+    r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
+    c = torch.from_numpy(np.ascontiguousarray(cls, dtype=np.int32)).cuda()
+    f = torch.from_numpy(ent).cuda()
+    n = rays.shape[0]
+    hits = torch.full((n, 4), -7.0, dtype=torch.float32, device="cuda")
+    counts = torch.zeros((n, 2), dtype=torch.int32, device="cuda")
+    work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    sc.sc_trace_seeded(d, r, c, f, hits, counts, cull, work)
+    sc.sc_status_poll(work)
+    ref_h, ref_c = sc.trace(d, r, 0, cull)
+    torch.cuda.synchronize()
+    return (hits.cpu().numpy(), counts.cpu().numpy().view(np.uint32), ref_h.cpu().numpy(),
+            ent.shape[0])
+
+
+@pytest.mark.parametrize("R,comp,layout,depth", [
+    (0, 0, sc.SC_LAYOUT_PLAIN, 8), (6, 0, sc.SC_LAYOUT_MASKED, 8),
+    (6, 1, sc.SC_LAYOUT_MASKED, 8), (6, 1, sc.SC_LAYOUT_MASKED_COMPACT, 8),
+    (4, 0, sc.SC_LAYOUT_MASKED, 3), (8, 1, sc.SC_LAYOUT_MASKED, 8), (6, 0, sc.SC_LAYOUT_MASKED, 0)])
+def test_seeded_matches_oracle(scene, R, comp, layout, depth):
+    _need_gpu()
+    tris, rays = scene
+    rays = rays[:4000]  # ragged: not a multiple of the warp or block
+    b = sc.sc_bvh_build(tris, R, comp)
+    nf = sc.sc_bvh_frontier(b, depth)[0].shape[0]
+    rng = np.random.default_rng(17)
+    cls = rng.integers(-2, nf + 2, rays.shape[0]).astype(np.int32)
+    cull = 1 if R else 0
+    g, gc, plain, _ = _gpu_seeded(b, layout, rays, cls, depth, cull)
+    ob = oracle.OracleBVH(tris)
+    if R:
+        ob.build_masks(R, 3)
+        if comp:
+            ob.compress(256, 8)
+    o = ob.trace_seeded(rays, cls, depth, cull=(2 if comp else 1) if cull else 0)
+    assert np.array_equal(_bits(g[:, 1]), o["id"])
+    assert np.array_equal(_bits(g[:, 0]), _bits(o["t"]))
+    assert np.array_equal(_bits(g[:, 2:]), _bits(o["uv"]))
+    bad = np.nonzero((gc != o["counts"]).any(1))[0]
+    assert bad.size == 0, f"counts differ on {bad.size} rays, e.g. {bad[:4]}"
+    # the seed never changes a hit
+    assert np.array_equal(_bits(g), _bits(plain))
+
+
+def test_seeded_edge_cases(scene):
+    _need_gpu()
+    tris, rays = scene
+    b = sc.sc_bvh_build(tris, 6, 0)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    ent, _ = sc.sc_bvh_frontier(b, 8)
+    f = torch.from_numpy(ent).cuda()
+    work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device="cuda")
+    empty = torch.empty((0, 8), dtype=torch.float32, device="cuda")
+    e_cls = torch.empty(0, dtype=torch.int32, device="cuda")
+    e_hits = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+    sc.sc_trace_seeded(d, empty, e_cls, f, e_hits, None, 1, work)  # n = 0 is fine
+    r = torch.from_numpy(rays[:64]).cuda()
+    c = torch.zeros(64, dtype=torch.int32, device="cuda")
+    h = torch.empty((64, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(sc.SubcullError):
+        sc.sc_trace_seeded(d, r, c, f[:0], h, None, 1, work)  # no frontier
+    dp = sc.DeviceBVH(b, sc.SC_LAYOUT_PLAIN)
+    with pytest.raises(sc.SubcullError):
+        sc.sc_trace_seeded(dp, r, c, f, h, None, 1, work)  # culling needs masks
+    # all rays on one class, and no counts buffer
+    sc.sc_trace_seeded(d, r, c, f, h, None, 1, work)
+    ref, _ = sc.trace(d, r, 0, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(h.cpu().numpy()), _bits(ref.cpu().numpy()))
+
+
+# ------------------------------------------------------------------ MLP --
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    w = omlp.init_params(seed)
+    return (w + 0.05 * rng.standard_normal(w.size)).astype(np.float32)
+
+
+def _upload_weights(w):
+    dw = torch.from_numpy(w).cuda()
+    wb = torch.empty(w.size, dtype=torch.bfloat16, device="cuda")
+    sc.sc_mlp_to_bf16(dw, wb)
+    return dw, wb
+
+
+BOX = np.array([0.5, 0.5, 0.5, 0.5, 0.5, 0.5], np.float32)
+
+
+def test_mlp_bf16_and_forward():
+    _need_gpu()
+    assert sc.sc_mlp_num_params() == omlp.P
+    w = _params(1)
+    dw, wb = _upload_weights(w)
+    wr = omlp.bf16_round(w)
+    got = wb.view(torch.int16).cpu().numpy().astype(np.uint16)
+    assert np.array_equal(got, (wr.view(np.uint32) >> 16).astype(np.uint16))
+    rays = sg.random_rays(3001, seed=4)
+    r = torch.from_numpy(rays).cuda()
+    box = torch.from_numpy(BOX).cuda()
+    cls = torch.empty(3001, dtype=torch.int32, device="cuda")
+    logits = torch.empty((3001, 256), dtype=torch.float32, device="cuda")
+    sc.sc_mlp_forward(wb, r, box, cls, logits)
+    cls2 = torch.empty(3001, dtype=torch.int32, device="cuda")
+    sc.sc_mlp_forward(wb, r, box, cls2, None)
+    torch.cuda.synchronize()
+    z = omlp.forward(omlp.unpack(wr.astype(np.float64)), omlp.features(rays, BOX))[-1]
+    zg = logits.cpu().numpy()
+    assert np.all(np.abs(zg - z) <= 1e-4 + 1e-4 * np.abs(z))
+    top = np.sort(z, 1)
+    clear = (top[:, -1] - top[:, -2]) > 1e-3
+    agree = (cls.cpu().numpy() == z.argmax(1))[clear].mean()
+    assert agree >= 0.999
+    assert np.array_equal(cls.cpu().numpy(), cls2.cpu().numpy())
+    # abstention: class -1 where the top-1 softmax probability < min_prob
+    p1 = 1.0 / np.exp(z - z.max(1, keepdims=True)).sum(1)
+    thr = float(np.median(p1))
+    cls3 = torch.empty(3001, dtype=torch.int32, device="cuda")
+    sc.sc_mlp_forward(wb, r, box, cls3, None, min_prob=thr)
+    torch.cuda.synchronize()
+    c3 = cls3.cpu().numpy()
+    away = np.abs(p1 - thr) > 1e-4 * thr
+    assert np.array_equal((c3 < 0)[away], (p1 < thr)[away])
+    kept = (c3 >= 0) & away
+    assert np.array_equal(c3[kept], cls.cpu().numpy()[kept])
+
+
+@pytest.mark.parametrize("batch", [37, 5000])
+def test_mlp_gradient_vs_oracle(batch):
+    _need_gpu()
+    w = _params(2)
+    dw, wb = _upload_weights(w)
+    rng = np.random.default_rng(batch)
+    rays = sg.random_rays(batch, seed=batch)
+    labels = rng.integers(0, 256, batch).astype(np.int32)
+    r = torch.from_numpy(rays).cuda()
+    lab = torch.from_numpy(labels).cuda()
+    box = torch.from_numpy(BOX).cuda()
+    grad = torch.zeros(omlp.P, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ws = torch.empty(sc.sc_mlp_train_workspace_bytes(batch), dtype=torch.uint8, device="cuda")
+    sc.sc_mlp_grad(wb, r, lab, box, grad, loss, ws)
+    torch.cuda.synchronize()
+    ref_loss, ref_g = omlp.loss_and_grad(omlp.bf16_round(w).astype(np.float64),
+                                         omlp.features(rays, BOX), labels)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * abs(ref_loss)
+    g = grad.cpu().numpy().astype(np.float64)
+    gd, rd = omlp.unpack(g), omlp.unpack(ref_g)
+    for name, _ in omlp.SHAPES:
+        err = np.linalg.norm(gd[name] - rd[name]) / np.linalg.norm(rd[name])
+        assert err <= 1e-3, (name, err)
+    # gradients accumulate
+    sc.sc_mlp_grad(wb, r, lab, box, grad, loss, ws)
+    torch.cuda.synchronize()
+    g2 = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g2 - 2 * g) <= 1e-5 * np.linalg.norm(g2)
+
+
+def test_mlp_adam_step():
+    _need_gpu()
+    w = _params(3)
+    rng = np.random.default_rng(3)
+    g = (1e-2 * rng.standard_normal(w.size)).astype(np.float32)
+    m = (1e-3 * rng.standard_normal(w.size)).astype(np.float32)
+    v = (1e-5 * rng.random(w.size)).astype(np.float32)
+    dw, wb = _upload_weights(w)
+    dg, dm, dv = (torch.from_numpy(a.copy()).cuda() for a in (g, m, v))
+    step, lr, b1, b2, eps = 7, 1e-3, 0.9, 0.999, 1e-8
+    sc.sc_mlp_adam(dw, wb, dg, dm, dv, step, lr, b1, b2, eps)
+    torch.cuda.synchronize()
+    # the hyper-parameters cross the C-ABI as float32: use those values
+    f1, f2 = np.float64(np.float32(b1)), np.float64(np.float32(b2))
+    c1, c2 = np.float64(np.float32(1) - np.float32(b1)), np.float64(np.float32(1) - np.float32(b2))
+    m64 = f1 * m.astype(np.float64) + c1 * g
+    v64 = f2 * v.astype(np.float64) + c2 * g.astype(np.float64) ** 2
+    w64 = w - np.float32(lr) * (m64 / (1 - f1 ** step)) / (np.sqrt(v64 / (1 - f2 ** step)) + eps)
+    wn = dw.cpu().numpy()
+    assert np.allclose(dm.cpu().numpy(), m64, rtol=1e-5, atol=1e-9)
+    assert np.allclose(dv.cpu().numpy(), v64, rtol=1e-5, atol=1e-14)
+    assert np.allclose(wn, w64, rtol=1e-6, atol=1e-7)
+    assert np.all(dg.cpu().numpy() == 0)
+    got = wb.view(torch.int16).cpu().numpy().astype(np.uint16)
+    assert np.array_equal(got, (omlp.bf16_round(wn).view(np.uint32) >> 16).astype(np.uint16))
+
+
+def test_mlp_labels():
+    _need_gpu()
+    n = 5000
+    rng = np.random.default_rng(8)
+    rays = sg.random_rays(n, seed=8)
+    ids = np.where(rng.random(n) < 0.6, rng.integers(0, 900, n), -1).astype(np.int32)
+    hits = np.zeros((n, 4), np.float32)
+    hits[:, 1] = ids.view(np.float32)
+    cot = rng.integers(0, 256, 900).astype(np.uint8)
+    out_r = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    out_l = torch.empty(n, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sc.sc_mlp_labels(torch.from_numpy(rays).cuda(), torch.from_numpy(hits).cuda(),
+                     torch.from_numpy(cot).cuda(), out_r, out_l, count)
+    torch.cuda.synchronize()
+    k = int(count.item())
+    hit = ids >= 0
+    assert k == hit.sum()
+    got_r, got_l = out_r[:k].cpu().numpy(), out_l[:k].cpu().numpy()
+    order = np.lexsort(got_r.T[::-1])
+    exp_r, exp_l = rays[hit], cot[ids[hit]].astype(np.int32)
+    eorder = np.lexsort(exp_r.T[::-1])
+    assert np.array_equal(got_r[order], exp_r[eorder])
+    assert np.array_equal(got_l[order], exp_l[eorder])
+
+
+# ------------------------------------------------------------- training --
+
+def test_trained_proposal_gain():
+    """Train on jittered primary + bounce rays of a 131,074-triangle hair
+    scene; evaluate on held-out rays (another jitter seed and its bounces).
+    The trained network must beat the untrained and most-frequent-label
+    controls in top-1 accuracy, every seeding must leave the hits exact, and
+    the node + triangle tests per ray of each seeding are reported beside
+    the plain culled traversal and the true-label upper bound."""
+    _need_gpu()
+    tris = sg.hair(4096, 16, True, seed=4)
+    b = sc.sc_bvh_build(tris, 6, 1)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    lp = learned.LearnedProposal(b, depth=8, seed=0)
+    train = [learned.primary_rays(256, 256, s) for s in range(1, 9)]
+    tr_r, tr_l = lp.collect(d, train, bounces=1, seed=100)
+    held_r, held_l = lp.collect(d, [learned.primary_rays(256, 256, 99)], bounces=1, seed=900)
+    assert tr_r.shape[0] > 100000 and held_r.shape[0] > 10000
+    held_lab = held_l.cpu().numpy()
+    majority = int(np.bincount(tr_l.cpu().numpy(), minlength=256).argmax())
+    plain_h, plain_c = sc.trace(d, held_r, 0, 1)
+    torch.cuda.synchronize()
+    plain_h = plain_h.cpu().numpy()
+    plain_tests = plain_c.cpu().numpy().astype(np.float64).sum(1).mean()
+
+    def tests_per_ray(cls):
+        n = held_r.shape[0]
+        counts = torch.zeros((n, 2), dtype=torch.int32, device="cuda")
+        hits = lp.trace(d, held_r, cls, counts=counts)
+        torch.cuda.synchronize()
+        assert np.array_equal(_bits(hits.cpu().numpy()), _bits(plain_h))
+        return float(counts.cpu().numpy().astype(np.float64).sum(1).mean())
+
+    untrained = lp.predict(held_r).clone()
+    loss = lp.fit(tr_r, tr_l, steps=1500, batch=4096, lr=3e-3, seed=1)
+    trained = lp.predict(held_r)
+    confident = lp.predict(held_r, min_prob=0.8).clone()
+    maj = torch.full_like(trained, majority)
+    acc = {k: float((c.cpu().numpy() == held_lab).mean())
+           for k, c in (("trained", trained), ("untrained", untrained), ("majority", maj))}
+    tests = {k: tests_per_ray(c) for k, c in (
+        ("trained", trained), ("trained_p0.8", confident), ("untrained", untrained),
+        ("majority", maj), ("true_label", held_l))}
+    tests["plain"] = plain_tests
+    seeded = float((confident.cpu().numpy() >= 0).mean())
+    print(f"\nlearned proposal: final loss {loss:.3f}; top-1 {acc}; p>=0.8 seeds {seeded:.3f} "
+          f"of rays; node+tri tests/ray {tests}")
+    assert acc["trained"] >= acc["majority"] + 0.08
+    assert acc["trained"] >= acc["untrained"] + 0.5
