@@ -125,7 +125,8 @@ def cpu_count():
         return os.cpu_count() or 1
 
 
-def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, stride=1):
+def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, stride=1,
+                      leaf_min=0):
     """Times the oracle's traversal (threads split the rays statically) on a
     sample of rays sized to roughly budget_s seconds of CPU time."""
     import oracle  # noqa: F401  (the oracle package; CPU baseline only)
@@ -133,7 +134,7 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, s
     # calibrate on a small sample
     m = min(n, 512)
     t0 = time.perf_counter()
-    ob.trace(rays[:m], 0, cull, skip_bits=skip_bits, stride=stride)
+    ob.trace(rays[:m], 0, cull, skip_bits=skip_bits, stride=stride, leaf_min=leaf_min)
     per_ray = (time.perf_counter() - t0) / m
     sample = int(min(n, max(threads * 256, budget_s * threads / max(per_ray, 1e-9))))
     idx = np.linspace(0, n - 1, sample).astype(np.int64)
@@ -143,7 +144,8 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, s
                mask_tests=np.zeros(sample, np.uint32))
     bounds = np.linspace(0, sample, threads + 1).astype(np.int64)
     ts = [threading.Thread(target=ob.trace, args=(sub, 0, cull, int(bounds[i]),
-                                                   int(bounds[i + 1]), out, skip_bits, stride))
+                                                   int(bounds[i + 1]), out, skip_bits, stride,
+                                                   leaf_min))
           for i in range(threads)]
     t0 = time.perf_counter()
     for t in ts:
@@ -334,7 +336,7 @@ def run_gpu(args):
     bounces = args.bounces if args.bounces >= 0 else WORKLOAD_BOUNCES.get(args.workload, 1)
     t0 = time.perf_counter()
     bvh = sc.sc_bvh_build(tris, R, comp, skip_bits=args.skip_bits, L=args.L,
-                          test_stride=args.stride)
+                          test_stride=args.stride, leaf_min_tris=args.leaf_min)
     build_s = time.perf_counter() - t0
     info = bvh.info()
     d_masked = sc.DeviceBVH(bvh, args.layout)
@@ -535,7 +537,8 @@ def run_gpu(args):
             cull_mode = 2
         thr = cpu_count()
         v, sample, dt, _ = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0,
-                                             args.skip_bits or R ** 3, args.stride)
+                                             args.skip_bits or R ** 3, args.stride,
+                                             args.leaf_min)
         cpu = {"value": v / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{sample} primary rays evenly spaced over the {n}, culled closest hit, "
                          f"{dt:.1f} s on {thr} threads (oracle's own BVH and masks)"}
@@ -551,6 +554,7 @@ def run_gpu(args):
                    "compressed": bool(comp), "L": args.L, "lut_mode": args.lut,
                    "layout": args.layout, "refill": args.refill,
                    "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
+                   "leaf_min_tris": args.leaf_min,
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -586,7 +590,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hair1m", choices=sorted(WORKLOADS))
     ap.add_argument("--lut", type=int, default=0, help="0 auto, 1 global table, 2 shared")
-    ap.add_argument("--layout", type=int, default=2, help="1 masked (scales stored), 2 compact")
+    ap.add_argument("--layout", type=int, default=1,
+                    help="1 masked (Alg. 1 scales stored per child), 2 compact (scales divided)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--refill", type=int, default=0, help="idle lanes before a warp refills")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -597,6 +602,8 @@ def main():
                     help="test inner children only at depths that are multiples of this")
     ap.add_argument("--primary-only", action="store_true",
                     help="only a few single-batch traces (for ncu captures)")
+    ap.add_argument("--leaf-min", type=int, default=0,
+                    help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,
                     help="keep children with >= this many mask bits untested (0: R^3)")
     ap.add_argument("--learned", action="store_true",

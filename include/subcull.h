@@ -109,6 +109,9 @@ typedef struct {
   int test_stride; /* device images: inner children are tested only at
                       depths that are multiples of this (0 or 1 = every
                       level, the paper's method); leaves are always tested */
+  int leaf_min_tris; /* device images: leaf children holding fewer than this
+                        many triangles are kept without a mask test (0 or 1:
+                        every leaf is tested, the paper's method) */
 } sc_build_opts;
 
 void sc_build_opts_default(sc_build_opts* o);

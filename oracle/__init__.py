@@ -82,8 +82,8 @@ def lib():
             "or_bvh_compress": (C.c_int, [vp, C.c_int, C.c_int]),
             "or_bvh_get_clut": (None, [vp, _P(u32), _P(u8)]),
             "or_trace_range": (C.c_int, [vp, _P(f), _P(f), i64, i64, C.c_int, C.c_int,
-                                         C.c_int, C.c_int, _P(f), _P(i32), _P(f), _P(u32),
-                                         _P(u32)]),
+                                         C.c_int, C.c_int, C.c_int, _P(f), _P(i32), _P(f),
+                                         _P(u32), _P(u32)]),
             "or_brute": (None, [_P(f), i64, _P(f), i64, C.c_int, _P(f), _P(i32), _P(f)]),
             "or_ray_tri": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f), _P(f)]),
             "or_slab": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f)]),
@@ -91,7 +91,8 @@ def lib():
             "or_cell_t": (C.c_int, [f, f, f, f, f, C.c_int]),
             "or_bvh_frontier": (C.c_int, [vp, C.c_int, _P(i32), _P(i32), _P(f), _P(u8)]),
             "or_trace_seeded": (C.c_int, [vp, _P(f), _P(f), i64, C.c_int, C.c_int, C.c_int,
-                                          _P(i32), _P(i32), _P(i32), _P(f), C.c_int, _P(f),
+                                          C.c_int, _P(i32), _P(i32), _P(i32), _P(f), C.c_int,
+                                          _P(f),
                                           _P(i32), _P(f), _P(u32)]),
             "or_pcg_hash": (u32, [u32]),
             "or_bounce_hash": (u32, [u32, u32, u32, u32]),
@@ -271,11 +272,12 @@ class OracleBVH:
 
     def trace(self, rays: np.ndarray, mode: int = 0, cull: int = 0,
               r_begin: int = 0, r_end: int | None = None, out=None, skip_bits: int | None = None,
-              stride: int = 1):
+              stride: int = 1, leaf_min: int = 0):
         """Alg. 4.  cull: 0 plain, 1 uncompressed masks, 2 compressed masks.
         skip_bits: children whose mask has at least this many bits set are
         kept untested (default R^3: only all-ones masks); stride: inner
-        children are tested only at depths that are multiples of it.
+        children are tested only at depths that are multiples of it;
+        leaf_min: leaf children with fewer triangles are kept untested.
         Returns dict(t, id, uv, counts[n,2], mask_tests)."""
         if skip_bits is None:
             skip_bits = max(self.R, 1) ** 3
@@ -288,7 +290,7 @@ class OracleBVH:
                        counts=np.zeros((n, 2), np.uint32),
                        mask_tests=np.zeros(n, np.uint32))
         rc = lib().or_trace_range(self._h, _ptr(self.tris, C.c_float), _ptr(rays, C.c_float),
-                                  r_begin, r_end, mode, cull, skip_bits, stride,
+                                  r_begin, r_end, mode, cull, skip_bits, stride, leaf_min,
                                   _ptr(out["t"], C.c_float),
                                   _ptr(out["id"], C.c_int32), _ptr(out["uv"], C.c_float),
                                   _ptr(out["counts"], C.c_uint32),
@@ -310,7 +312,8 @@ def _frontier(self, depth: int = 8):
     return fc[:k], fn[:k], fb[:k], cls[: self.ntri]
 
 
-def _trace_seeded(self, rays, cls, depth: int = 8, cull: int = 0, skip_bits=None, stride=1):
+def _trace_seeded(self, rays, cls, depth: int = 8, cull: int = 0, skip_bits=None, stride=1,
+                  leaf_min=0):
     """Seeded closest-hit traversal over the depth-`depth` frontier; cls[i]
     outside [0, frontier size) traces ray i without a seed."""
     rays = _f32(rays).reshape(-1, 8)
@@ -325,7 +328,7 @@ def _trace_seeded(self, rays, cls, depth: int = 8, cull: int = 0, skip_bits=None
     uv = np.zeros((n, 2), np.float32)
     cnt = np.zeros((n, 2), np.uint32)
     rc = lib().or_trace_seeded(self._h, _ptr(self.tris, C.c_float), _ptr(rays, C.c_float), n,
-                               cull, skip_bits, stride, _ptr(c, C.c_int32),
+                               cull, skip_bits, stride, leaf_min, _ptr(c, C.c_int32),
                                _ptr(fc, C.c_int32), _ptr(fn, C.c_int32), _ptr(fb, C.c_float),
                                len(fc), _ptr(t, C.c_float), _ptr(hid, C.c_int32),
                                _ptr(uv, C.c_float), _ptr(cnt, C.c_uint32))

@@ -942,11 +942,13 @@ typedef struct {
  * whose test cannot fail -- the paper's method exactly; smaller values skip
  * dense masks, which rarely cull), and an inner child at depth d is tested
  * only when d is a multiple of `stride` (1: every level, the paper's
- * method).  Skipping a test only keeps a child, so hits are the same for
- * every setting.
+ * method); a leaf child holding fewer than leaf_min triangles is kept
+ * untested (0 or 1: every leaf is tested, the paper's method).  Skipping a
+ * test only keeps a child, so hits are the same for every setting.
  */
 static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
-                      int mode, int cull, int skip_bits, int stride, StackEntry* stack,
+                      int mode, int cull, int skip_bits, int stride, int leaf_min,
+                      StackEntry* stack,
                       float* hit_t,
                       int32_t* hit_id, float* hit_uv, uint32_t* counts,
                       uint32_t* mtests, const Seed* seed) {
@@ -1000,6 +1002,7 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
                         : b->masks + ((size_t)m * 2 + c) * b->W;
           if (popcount_mask(om, b->W) >= skip_bits) continue; /* kept untested */
           if (b->count[2 * m + c] == 0 && (b->ndepth[m] + 1) % stride != 0) continue;
+          if (b->count[2 * m + c] > 0 && b->count[2 * m + c] < leaf_min) continue;
           ++mtest;
           hit[c] = cull_pass(b, &r, b->box + 12 * m + 6 * c, tn[c], tf[c], om);
         }
@@ -1042,7 +1045,8 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
 
 int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
                    int64_t r_begin, int64_t r_end, int mode, int cull,
-                   int skip_bits, int stride, float* hit_t, int32_t* hit_id, float* hit_uv,
+                   int skip_bits, int stride, int leaf_min, float* hit_t, int32_t* hit_id,
+                   float* hit_uv,
                    uint32_t* counts, uint32_t* mask_tests) {
   if (stride < 1) return -3;
   if (cull && !b->masks) return -1;
@@ -1057,7 +1061,7 @@ int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
   StackEntry* stack =
       (StackEntry*)malloc(sizeof(StackEntry) * (size_t)(b->max_depth + 4));
   for (int64_t i = r_begin; i < r_end; ++i)
-    trace_one(b, tris, rays + 8 * i, mode, cull, skip_bits, stride, stack, hit_t + i,
+    trace_one(b, tris, rays + 8 * i, mode, cull, skip_bits, stride, leaf_min, stack, hit_t + i,
               hit_id + i,
               hit_uv + 2 * i, counts + 2 * i, mask_tests ? mask_tests + i : NULL, NULL);
   free(stack);
@@ -1068,7 +1072,7 @@ int or_trace(const OrBvh* b, const float* tris, const float* rays, int64_t n,
              int mode, int cull, float* hit_t, int32_t* hit_id, float* hit_uv,
              uint32_t* counts, uint32_t* mask_tests) {
   int R3 = b->R * b->R * b->R;
-  return or_trace_range(b, tris, rays, 0, n, mode, cull, R3, 1, hit_t, hit_id, hit_uv,
+  return or_trace_range(b, tris, rays, 0, n, mode, cull, R3, 1, 0, hit_t, hit_id, hit_uv,
                         counts, mask_tests);
 }
 
@@ -1229,7 +1233,7 @@ int or_bvh_frontier(const OrBvh* b, int D, int32_t* fchild, int32_t* fcount, flo
    it reaches the seed slot; else it starts with the ray's tmax.  The
    result is the plain traversal's closest hit; counts sum both phases. */
 int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_t n,
-                    int cull, int skip_bits, int stride, const int32_t* cls,
+                    int cull, int skip_bits, int stride, int leaf_min, const int32_t* cls,
                     const int32_t* fchild, const int32_t* fcount, const float* fbox, int nf,
                     float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts) {
   if (stride < 1) return -3;
@@ -1250,7 +1254,8 @@ int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_
     uint32_t c1[2] = {0, 0}, c2[2], mt;
     int k = cls[i];
     if (k < 0 || k >= nf) {
-      trace_one(b, tris, r8, 0, cull, skip_bits, stride, stack, &t2, &id2, uv2, c2, &mt, NULL);
+      trace_one(b, tris, r8, 0, cull, skip_bits, stride, leaf_min, stack, &t2, &id2, uv2, c2,
+                &mt, NULL);
     } else {
       ORay r;
       float tn, tf;
@@ -1260,7 +1265,8 @@ int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_
         uint32_t cs[2];
         sub.root_child = fchild[k];
         sub.root_count = fcount[k];
-        trace_one(&sub, tris, r8, 0, cull, skip_bits, stride, stack, &t1, &id1, uv1, cs, &mt,
+        trace_one(&sub, tris, r8, 0, cull, skip_bits, stride, leaf_min, stack, &t1, &id1, uv1,
+                  cs, &mt,
                   NULL);
         c1[0] += cs[0];
         c1[1] += cs[1];
@@ -1269,7 +1275,8 @@ int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_
       sd.child = fchild[k];
       sd.count = fcount[k];
       sd.t = t1; sd.u = uv1[0]; sd.v = uv1[1]; sd.id = id1;
-      trace_one(b, tris, r8, 0, cull, skip_bits, stride, stack, &t2, &id2, uv2, c2, &mt, &sd);
+      trace_one(b, tris, r8, 0, cull, skip_bits, stride, leaf_min, stack, &t2, &id2, uv2, c2,
+                &mt, &sd);
     }
     hit_t[i] = t2;
     hit_id[i] = id2;

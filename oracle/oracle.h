@@ -79,11 +79,12 @@ int or_trace(const OrBvh* b, const float* tris, const float* rays, int64_t n,
 /* The same, for rays [r_begin, r_end) only (threads may split the rays).
    Test selection: children whose mask has >= skip_bits bits set are kept
    untested (R^3: only all-ones masks), and inner children are tested only
-   at depths that are multiples of `stride` (1: every level).  skip_bits =
-   R^3 and stride = 1 is the paper's method. */
+   at depths that are multiples of `stride` (1: every level), and leaf
+   children with fewer than leaf_min triangles are kept untested.  skip_bits
+   = R^3, stride = 1 and leaf_min <= 1 is the paper's method. */
 int or_trace_range(const OrBvh* b, const float* tris, const float* rays,
                    int64_t r_begin, int64_t r_end, int mode, int cull,
-                   int skip_bits, int stride, float* hit_t, int32_t* hit_id,
+                   int skip_bits, int stride, int leaf_min, float* hit_t, int32_t* hit_id,
                    float* hit_uv, uint32_t* counts, uint32_t* mask_tests);
 
 /* Brute force over all ray x triangle pairs, same ray-triangle test.
@@ -105,7 +106,7 @@ int or_bounce(const float* ray8, float t, const float* tri9, uint32_t seed,
 int or_bvh_frontier(const OrBvh* b, int D, int32_t* fchild, int32_t* fcount, float* fbox,
                     uint8_t* cls);
 int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_t n,
-                    int cull, int skip_bits, int stride, const int32_t* cls,
+                    int cull, int skip_bits, int stride, int leaf_min, const int32_t* cls,
                     const int32_t* fchild, const int32_t* fcount, const float* fbox, int nf,
                     float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts);
 

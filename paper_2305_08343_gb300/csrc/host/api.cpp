@@ -109,6 +109,7 @@ void sc_build_opts_default(sc_build_opts* o) {
   o->threads = 0;
   o->skip_bits = 0;
   o->test_stride = 1;
+  o->leaf_min_tris = 0;
 }
 
 sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
@@ -132,6 +133,7 @@ sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
   if (!(o.eps_rel >= 0.0)) fail(SC_ERR_ARG, "eps_rel must be >= 0");
   if (o.skip_bits < 0) fail(SC_ERR_ARG, "skip_bits must be >= 0");
   if (o.test_stride < 0) fail(SC_ERR_ARG, "test_stride must be >= 0");
+  if (o.leaf_min_tris < 0) fail(SC_ERR_ARG, "leaf_min_tris must be >= 0");
   for (int64_t i = 0; i < 9 * n; ++i)
     if (!std::isfinite(tris[i])) fail(SC_ERR_ARG, "triangle %lld has a non-finite coordinate",
                                       (long long)(i / 9));

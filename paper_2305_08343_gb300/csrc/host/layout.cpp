@@ -107,8 +107,10 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
                                        : &b.masks[((size_t)n * 2 + c) * L.W];
         uint32_t meta = L.compress ? (uint32_t)b.cidx[2 * n + c] : 0u;
         const int stride = b.opts.test_stride > 1 ? b.opts.test_stride : 1;
-        const bool inner = b.count[2 * n + c] == 0;
-        if (skip_test(m, L.R, b.opts.skip_bits) || (inner && (b.ndepth[n] + 1) % stride != 0))
+        const int32_t cnt = b.count[2 * n + c];
+        const bool inner = cnt == 0;
+        if (skip_test(m, L.R, b.opts.skip_bits) || (inner && (b.ndepth[n] + 1) % stride != 0) ||
+            (!inner && cnt < b.opts.leaf_min_tris))
           meta |= kMetaFull;
         u[2 + c] = meta;
         if (!L.compress) std::memcpy(rec + L.mask_off + c * L.mstride, m, 4 * L.W);

@@ -41,14 +41,14 @@ def gpu_trace(bvh, rays, mode, cull, lut_mode=sc.SC_LUT_AUTO, layout=None, refil
                 counts=counts.cpu().numpy().view(np.uint32).copy())
 
 
-def oracle_trace(tris, rays, R, comp, mode, cull, skip_bits=None, stride=1):
+def oracle_trace(tris, rays, R, comp, mode, cull, skip_bits=None, stride=1, leaf_min=0):
     ob = oracle.OracleBVH(tris)
     if R:
         ob.build_masks(R, 3)
         if comp:
             ob.compress(256, 8)
     return ob.trace(rays, mode, (2 if comp else 1) if cull else 0, skip_bits=skip_bits,
-                    stride=stride)
+                    stride=stride, leaf_min=leaf_min)
 
 
 def assert_parity(g, o, what=""):
@@ -117,6 +117,16 @@ def test_test_stride(hair_small, stride, skip, comp):
     g = gpu_trace(b, rays, 0, 1)
     o = oracle_trace(tris, rays, 6, comp, 0, 1, skip_bits=skip or None, stride=stride)
     assert_parity(g, o, f"stride={stride} skip={skip}")
+
+
+@pytest.mark.parametrize("leaf_min,stride", [(2, 1), (3, 1), (4, 2)])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_leaf_min(hair_small, leaf_min, stride, comp):
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, 6, comp, leaf_min_tris=leaf_min, test_stride=stride)
+    g = gpu_trace(b, rays, 0, 1)
+    o = oracle_trace(tris, rays, 6, comp, 0, 1, stride=stride, leaf_min=leaf_min)
+    assert_parity(g, o, f"leaf_min={leaf_min} stride={stride}")
 
 
 @pytest.mark.parametrize("refill", [1, 4, 16, 32])

@@ -281,3 +281,12 @@ def test_dense_mask_skip_keeps_hits_and_orders_counts(hair_small):
             o = b.trace(rays, 0, cull, stride=stride)
             assert np.array_equal(o["id"], plain["id"]) and np.array_equal(o["t"], plain["t"])
             assert (o["counts"] >= full["counts"]).all() and (o["counts"] <= plain["counts"]).all()
+        prev = full
+        for leaf_min in (2, 3, 4, 5):
+            o = b.trace(rays, 0, cull, leaf_min=leaf_min)
+            assert np.array_equal(o["id"], plain["id"]) and np.array_equal(o["t"], plain["t"])
+            assert (o["counts"] >= full["counts"]).all() and (o["counts"] <= plain["counts"]).all()
+            assert o["mask_tests"].sum() <= prev["mask_tests"].sum()
+            # nodes are culled the same way; only leaf triangles can be added
+            assert np.array_equal(o["counts"][:, 0], full["counts"][:, 0])
+            prev = o
