@@ -149,6 +149,15 @@ sc_status sc_bvh_export(const sc_bvh* b, int32_t* root2, int32_t* child,
                         int32_t* count, float* box, int32_t* perm,
                         uint32_t* masks, uint32_t* clut, uint8_t* cidx);
 
+/* Checkpoint of a built BVH (everything sc_bvh_build computed, so that a
+   large build is paid once; not in the paper).  sc_bvh_save writes `path`
+   (through a temporary file renamed into place); sc_bvh_load returns a new
+   handle owned by the caller (free with sc_bvh_destroy).  The file carries
+   a format version, a byte-order mark and a hash; a file that fails any
+   check, or whose tree indices are out of range, gives SC_ERR_IO. */
+sc_status sc_bvh_save(const sc_bvh* b, const char* path);
+sc_status sc_bvh_load(const char* path, sc_bvh** out);
+
 /* The ray-mask table (Sec. 3.1.1): uint32[R^3 * R^3][W], row
    beg*R^3 + end, cell index x + R*y + R*R*z.  Built here from the 2-D
    sweep tables of each pair of axes (Helly's theorem on intervals of t). */

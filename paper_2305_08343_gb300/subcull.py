@@ -8,6 +8,7 @@ loaded this module raises; there is no fallback.
 from __future__ import annotations
 
 import ctypes as C
+import os
 import threading
 
 import numpy as np
@@ -15,6 +16,8 @@ import numpy as np
 from . import _build
 
 SC_OK = 0
+SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_NOMEM, SC_ERR_TIMEOUT = -1, -2, -3, -4
+SC_ERR_STACK, SC_ERR_UNSUPPORTED, SC_ERR_STATE, SC_ERR_IO = -5, -6, -7, -8
 SC_SCENE_HAIR, SC_SCENE_SOUP = 0, 1
 SC_RAYS_PINHOLE, SC_RAYS_RANDOM = 0, 1
 SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED, SC_LAYOUT_MASKED_COMPACT = 0, 1, 2
@@ -98,6 +101,8 @@ def lib():
             "sc_bvh_get_info": (C.c_int, [vp, P(sc_bvh_info)]),
             "sc_bvh_export": (C.c_int, [vp, i32p, i32p, i32p, f32p, i32p, u32p, u32p, u8p]),
             "sc_raylut": (C.c_int, [C.c_int, u32p]),
+            "sc_bvh_save": (C.c_int, [vp, C.c_char_p]),
+            "sc_bvh_load": (C.c_int, [C.c_char_p, P(vp)]),
             "sc_bvh_device_bytes": (C.c_int, [vp, C.c_int, P(C.c_size_t)]),
             "sc_bvh_upload": (C.c_int, [vp, C.c_int, vp, C.c_size_t, vp, P(vp)]),
             "sc_dbvh_destroy": (None, [vp]),
@@ -241,6 +246,18 @@ def sc_bvh_build(tris: np.ndarray, grid_res: int = 6, compress: int = 0,
     _check(lib().sc_bvh_build(_ptr(t, C.c_float) if len(t) else None, t.shape[0], grid_res,
                               compress, C.byref(o), C.byref(h)))
     return Bvh(h, t.shape[0])
+
+
+def sc_bvh_save(bvh: Bvh, path: str):
+    _check(lib().sc_bvh_save(bvh.handle, os.fsencode(path)))
+
+
+def sc_bvh_load(path: str) -> Bvh:
+    h = C.c_void_p()
+    _check(lib().sc_bvh_load(os.fsencode(path), C.byref(h)))
+    b = Bvh(h, 0)
+    b.ntri = b.info().num_tris
+    return b
 
 
 def sc_raylut(R: int) -> np.ndarray:
