@@ -54,6 +54,28 @@ WORKLOADS = {
 WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "soup4m": 0}
 
 
+# DRAM traffic per launch of the timed kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture, summarised in profiles/), valid
+# only while the kernel source is the one that was measured: keyed by the
+# SHA-256 of the traversal kernel header.
+MEASURED_TRAFFIC = {
+    # workload: (bytes per launch, kernel source sha256, profile summary)
+    "hair1m": (1.672598e9 + 0.246765e9,
+               "f93ef1433310915fbc949e4effa0dc5b63fc0cbd92ad57cd55a33b106e9d820a",
+               "profiles/waves_kernel_hair1m.md"),
+}
+
+
+def measured_traffic(workload: str):
+    import hashlib
+    entry = MEASURED_TRAFFIC.get(workload)
+    if entry is None:
+        return None, None
+    src = os.path.join(ROOT, "paper_2305_08343_gb300", "csrc", "cuda", "trace_kernel.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return (entry[0], entry[2]) if sha == entry[1] else (None, None)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -357,6 +379,18 @@ def run_gpu(args):
         torch.cuda.synchronize()
         print(json.dumps({"primary_only": True, "workload": args.workload, "rays": n}))
         return 0
+    if args.waves_once:
+        # one culled and one plain wave pipeline launch (default launch
+        # options) and nothing else: the command used for ncu captures of
+        # waves_kernel
+        for dbvh, cull in ((d_masked, 1), (d_plain, 0)):
+            b = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
+            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, b.outs(), b.ws, opts)
+            sizes = sc.sc_waves_poll(b.ws, bounces)
+            del b
+        print(json.dumps({"waves_once": True, "workload": args.workload, "rays": n,
+                          "wave_sizes": [int(x) for x in sizes]}))
+        return 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
@@ -514,8 +548,13 @@ def run_gpu(args):
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peaks = load_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic, traffic_src = measured_traffic(args.workload)
+    if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
+            or args.leaf_min or args.L != 3
+            or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)):
+        traffic, traffic_src = None, None  # measured for the default configuration only
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                 "peak_source": "measured" if peaks else "fallback",
                 "bytes_per_ray": b_ray, "kernel": "waves_kernel (culled)"}
 
@@ -602,6 +641,8 @@ def main():
                     help="test inner children only at depths that are multiples of this")
     ap.add_argument("--primary-only", action="store_true",
                     help="only a few single-batch traces (for ncu captures)")
+    ap.add_argument("--waves-once", action="store_true",
+                    help="one culled and one plain wave-pipeline launch (for ncu captures)")
     ap.add_argument("--leaf-min", type=int, default=0,
                     help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,
