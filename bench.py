@@ -76,6 +76,24 @@ def measured_traffic(workload: str):
     return (entry[0], entry[2]) if sha == entry[1] else (None, None)
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest value of x over all ranks (x itself without a process
+    group): the timed region of a multi-GPU run is the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mrays(rays_per_rank_step: int, steps: int, world: int, max_total_ms: float) -> float:
+    """Whole-job throughput: every rank traces its own copy of the workload
+    (replicas, weak scaling), so the job traces world x the rays of one rank
+    in the slowest rank's time."""
+    return rays_per_rank_step * steps * world / (max_total_ms * 1e-3) / 1e6
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -478,12 +496,8 @@ def run_gpu(args):
         ms_plain = timed(1, d_plain, 0, bufs_p)
     sc.sc_waves_poll(bufs_c.ws, bounces)
     sc.sc_waves_poll(bufs_p.ws, bounces)
-    tot_cull = float(np.sum(ms_cull))
-    if dist:
-        t = torch.tensor([tot_cull], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_cull = float(t.item())
-    value = rays_per_step * args.steps * world / (tot_cull * 1e-3) / 1e6
+    tot_cull = max_over_ranks(float(np.sum(ms_cull)), dist, dev)
+    value = whole_job_mrays(rays_per_step, args.steps, world, tot_cull)
     plain_value = rays_per_step * args.steps / (float(np.sum(ms_plain)) * 1e-3) / 1e6
 
     # primary wave alone (single-batch sc_trace), for context

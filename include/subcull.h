@@ -219,6 +219,11 @@ typedef struct {
   int64_t wave_chunk;/* waves: primary rays per chunk (the wave size); each
                         chunk runs through all its bounce waves before the
                         next; 0 = all primary rays in one chunk           */
+  int64_t wait_timeout_ns; /* waves: limit of each device-wide wait (the
+                        barrier between waves), 0 = 2 s.  A wait that runs
+                        out records SC_ERR_TIMEOUT, which sc_waves_poll
+                        returns, and the kernel returns; the context stays
+                        usable.                                           */
 } sc_trace_opts;
 
 /* Workspace bytes sc_trace needs (ray counter and device status word). */

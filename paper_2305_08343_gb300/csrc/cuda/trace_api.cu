@@ -264,7 +264,7 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   }
   wp.bounces = bounces;
   wp.seed = seed;
-  wp.timeout_ns = 2000000000ULL;
+  wp.timeout_ns = o.wait_timeout_ns > 0 ? (unsigned long long)o.wait_timeout_ns : 2000000000ULL;
   DevInfo di = device_info();
   int per_sm = 0;
   CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, block, 0));

@@ -67,7 +67,8 @@ SC_MAX_BOUNCES = 4
 
 class sc_trace_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int),
-                ("refill", C.c_int), ("stack", C.c_int), ("wave_chunk", C.c_int64)]
+                ("refill", C.c_int), ("stack", C.c_int), ("wave_chunk", C.c_int64),
+                ("wait_timeout_ns", C.c_int64)]
 
 
 class sc_tune_result(C.Structure):
@@ -313,8 +314,10 @@ def sc_bvh_upload(bvh: Bvh, layout: int, stream=None) -> DeviceBVH:
     return DeviceBVH(bvh, layout, stream=stream)
 
 
-def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO, refill=0, stack=0, wave_chunk=0):
-    return sc_trace_opts(block, blocks_per_sm, lut_mode, refill, stack, wave_chunk)
+def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO, refill=0, stack=0, wave_chunk=0,
+          wait_timeout_ns=0):
+    return sc_trace_opts(block, blocks_per_sm, lut_mode, refill, stack, wave_chunk,
+                         wait_timeout_ns)
 
 
 def sc_trace(dbvh: DeviceBVH, rays, hits, counts, mode: int, cull: int, work,

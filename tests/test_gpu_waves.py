@@ -148,3 +148,34 @@ def test_waves_edge_cases():
     assert sizes.tolist() == [len(miss), 0, 0]
     with pytest.raises(sc.SubcullError):
         sc.trace_waves(d, r, sc.SC_MAX_BOUNCES + 1, 1, 1)
+
+
+def test_wait_timeout_is_reported_and_the_context_survives():
+    """Failure detection without a fault: with a 1 ns limit the grid
+    barrier between waves gives up at once, every block records the timeout
+    and returns, sc_waves_poll reports SC_ERR_TIMEOUT, and the next launch
+    on the same context and buffers gives the normal results."""
+    tris = sg.hair(2048, 16, True, seed=5)
+    rays = sg.pinhole(256, 256)
+    b = sc.sc_bvh_build(tris, 6, 0)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    r = torch.from_numpy(rays).cuda()
+    bufs = sc.WaveBuffers(r.shape[0], 2, with_counts=True)
+    sc.sc_trace_waves(d, r, 2, 99, 1, bufs.outs(), bufs.ws, sc._opts(wait_timeout_ns=1))
+    with pytest.raises(sc.SubcullError) as e:
+        sc.sc_waves_poll(bufs.ws, 2)
+    assert e.value.code == sc.SC_ERR_TIMEOUT
+    # same context, same buffers, default limit: a normal run
+    _, sizes = sc.trace_waves(d, r, 2, 99, 1, bufs)
+    ref = sc.WaveBuffers(r.shape[0], 2, with_counts=True)
+    _, ref_sizes = sc.trace_waves(d, r, 2, 99, 1, ref)
+    torch.cuda.synchronize()
+    assert np.array_equal(sizes, ref_sizes) and sizes[1] > 0
+    for w in range(3):
+        m = int(sizes[w])
+        a = bufs.hits[w][:m].cpu().numpy().view(np.int32)
+        c = ref.hits[w][:m].cpu().numpy().view(np.int32)
+        pa = bufs.path[w][:m].cpu().numpy()
+        pc = ref.path[w][:m].cpu().numpy()
+        oa, oc = np.argsort(pa, kind="stable"), np.argsort(pc, kind="stable")
+        assert np.array_equal(pa[oa], pc[oc]) and np.array_equal(a[oa], c[oc])
