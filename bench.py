@@ -376,7 +376,8 @@ def run_gpu(args):
     bounces = args.bounces if args.bounces >= 0 else WORKLOAD_BOUNCES.get(args.workload, 1)
     t0 = time.perf_counter()
     bvh = sc.sc_bvh_build(tris, R, comp, skip_bits=args.skip_bits, L=args.L,
-                          test_stride=args.stride, leaf_min_tris=args.leaf_min)
+                          test_stride=args.stride, leaf_min_tris=args.leaf_min,
+                          max_leaf=args.max_leaf)
     build_s = time.perf_counter() - t0
     info = bvh.info()
     d_masked = sc.DeviceBVH(bvh, args.layout)
@@ -564,7 +565,7 @@ def run_gpu(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic, traffic_src = measured_traffic(args.workload)
     if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
-            or args.leaf_min or args.L != 3
+            or args.leaf_min or args.L != 3 or args.max_leaf != 4
             or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)):
         traffic, traffic_src = None, None  # measured for the default configuration only
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -607,7 +608,7 @@ def run_gpu(args):
                    "compressed": bool(comp), "L": args.L, "lut_mode": args.lut,
                    "layout": args.layout, "refill": args.refill,
                    "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
-                   "leaf_min_tris": args.leaf_min,
+                   "leaf_min_tris": args.leaf_min, "max_leaf": args.max_leaf,
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -657,6 +658,7 @@ def main():
                     help="only a few single-batch traces (for ncu captures)")
     ap.add_argument("--waves-once", action="store_true",
                     help="one culled and one plain wave-pipeline launch (for ncu captures)")
+    ap.add_argument("--max-leaf", type=int, default=4, help="triangles per BVH leaf (1..8)")
     ap.add_argument("--leaf-min", type=int, default=0,
                     help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,

@@ -129,6 +129,19 @@ def test_leaf_min(hair_small, leaf_min, stride, comp):
     assert_parity(g, o, f"leaf_min={leaf_min} stride={stride}")
 
 
+@pytest.mark.parametrize("max_leaf", [1, 8])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_leaf_sizes(hair_small, max_leaf, comp):
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, 6, comp, max_leaf=max_leaf)
+    ob = oracle.OracleBVH(tris, max_leaf=max_leaf).build_masks(6, 3)
+    if comp:
+        ob.compress(256, 8)
+    assert_parity(gpu_trace(b, rays, 0, 1), ob.trace(rays, 0, 2 if comp else 1),
+                  f"max_leaf={max_leaf}")
+    assert_parity(gpu_trace(b, rays, 0, 0), ob.trace(rays, 0, 0), f"plain max_leaf={max_leaf}")
+
+
 @pytest.mark.parametrize("refill", [1, 4, 16, 32])
 def test_refill_threshold_does_not_change_results(hair_small, refill):
     tris, rays = hair_small
