@@ -377,7 +377,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     bvh = sc.sc_bvh_build(tris, R, comp, skip_bits=args.skip_bits, L=args.L,
                           test_stride=args.stride, leaf_min_tris=args.leaf_min,
-                          max_leaf=args.max_leaf)
+                          max_leaf=args.max_leaf, gpu_masks=int(args.gpu_masks))
     build_s = time.perf_counter() - t0
     info = bvh.info()
     d_masked = sc.DeviceBVH(bvh, args.layout)
@@ -609,6 +609,7 @@ def run_gpu(args):
                    "layout": args.layout, "refill": args.refill,
                    "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
                    "leaf_min_tris": args.leaf_min, "max_leaf": args.max_leaf,
+                   "gpu_masks": bool(args.gpu_masks),
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -659,6 +660,8 @@ def main():
     ap.add_argument("--waves-once", action="store_true",
                     help="one culled and one plain wave-pipeline launch (for ncu captures)")
     ap.add_argument("--max-leaf", type=int, default=4, help="triangles per BVH leaf (1..8)")
+    ap.add_argument("--gpu-masks", action="store_true",
+                    help="build the object masks on the GPU (same bits as the host build)")
     ap.add_argument("--leaf-min", type=int, default=0,
                     help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,

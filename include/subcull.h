@@ -112,6 +112,10 @@ typedef struct {
   int leaf_min_tris; /* device images: leaf children holding fewer than this
                         many triangles are kept without a mask test (0 or 1:
                         every leaf is tested, the paper's method) */
+  int gpu_masks;   /* 1: the object masks are built on the current GPU (the
+                      same bits as the host build, which 0 selects); the
+                      tree and the compression stay on the host.  Needs a
+                      device: SC_ERR_CUDA without one. */
 } sc_build_opts;
 
 void sc_build_opts_default(sc_build_opts* o);

@@ -110,6 +110,7 @@ void sc_build_opts_default(sc_build_opts* o) {
   o->skip_bits = 0;
   o->test_stride = 1;
   o->leaf_min_tris = 0;
+  o->gpu_masks = 0;
 }
 
 sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
@@ -143,7 +144,10 @@ sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
     h->b.opts = o;
     build_bvh(h->b, tris, n, o.max_leaf, o.bins, T);
     if (grid_res > 0) {
-      build_masks(h->b, grid_res, o.L, scene_eps(tris, n, o.eps_rel), T);
+      if (o.gpu_masks)
+        build_masks_gpu(h->b, grid_res, o.L, scene_eps(tris, n, o.eps_rel));
+      else
+        build_masks(h->b, grid_res, o.L, scene_eps(tris, n, o.eps_rel), T);
       if (compress) build_compression(h->b, o.lut_size, o.chunk_bits, T);
     }
   } catch (...) {

@@ -69,6 +69,8 @@ struct Bvh {
 void build_bvh(Bvh& b, const float* tris, int64_t n, int max_leaf, int bins,
                int threads);
 void build_masks(Bvh& b, int R, int L, double eps, int threads);
+// The same masks built on the current GPU (bit-identical).
+void build_masks_gpu(Bvh& b, int R, int L, double eps);
 void build_compression(Bvh& b, int K, int bits, int threads);
 double scene_eps(const float* tris, int64_t n, double eps_rel);
 
