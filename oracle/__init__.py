@@ -94,6 +94,7 @@ def lib():
                                           C.c_int, _P(i32), _P(i32), _P(i32), _P(f), C.c_int,
                                           _P(f),
                                           _P(i32), _P(f), _P(u32)]),
+            "or_bvh_set_ideal": (None, [vp, C.c_int]),
             "or_pcg_hash": (u32, [u32]),
             "or_bounce_hash": (u32, [u32, u32, u32, u32]),
             "or_bounce": (C.c_int, [_P(f), f, _P(f), u32, u32, u32, _P(f)]),
@@ -337,6 +338,13 @@ def _trace_seeded(self, rays, cls, depth: int = 8, cull: int = 0, skip_bits=None
     return dict(t=t, id=hid, uv=uv, counts=cnt)
 
 
+def _set_ideal(self, ideal: bool = True):
+    """Culling tests use the exact ray mask (Sec. 4.1's ideal culling)."""
+    lib().or_bvh_set_ideal(self._h, int(bool(ideal)))
+    return self
+
+
+OracleBVH.set_ideal = _set_ideal
 OracleBVH.frontier = _frontier
 OracleBVH.trace_seeded = _trace_seeded
 

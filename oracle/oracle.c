@@ -432,6 +432,7 @@ struct OrBvh {
   uint32_t* clut;  /* [K][W] */
   uint8_t* cidx;   /* [nn][2] */
   uint32_t* raylut;
+  int ideal; /* 1: culling tests use the exact ray mask (ideal_ray_mask) */
 };
 
 typedef struct {
@@ -616,6 +617,8 @@ OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins) {
   free(rec);
   return b;
 }
+
+void or_bvh_set_ideal(OrBvh* b, int ideal) { b->ideal = ideal; }
 
 void or_bvh_free(OrBvh* b) {
   if (!b) return;
@@ -896,9 +899,69 @@ int or_cell_t(float t, float o, float d, float lo, float hi, int R) {
   return i;
 }
 
+/* "Ideal" ray mask (the paper's Sec. 4.1 reference, which creates the ray
+   mask by grid traversal): every cell whose closed box the segment [t0, t1]
+   of the ray meets, in double.  Per axis k the ray's cell coordinate is
+   u_k(t) = (o_k - lo_k) * s_k + t * d_k * s_k with s_k = R / extent; cell j
+   spans [j, j+1] (the first and last cells extend to -inf / +inf, since the
+   lookup path clamps the same way), and a cell is met iff the t-intervals
+   of its three axes and [t0, t1] share a point.  A flat axis (extent 0)
+   puts the segment in every cell along it. */
+static void ideal_ray_mask(const ORay* r, const float* bx, float tn, float tf, int R,
+                           uint32_t* m) {
+  const int W = or_mask_words(R);
+  const double t0 = tn, t1 = tf > tn ? tf : tn;
+  double lo[3][8], hi[3][8];
+  for (int k = 0; k < 3; ++k) {
+    const double ext = (double)bx[3 + k] - (double)bx[k];
+    for (int j = 0; j < R; ++j) {
+      lo[k][j] = t0;
+      hi[k][j] = t1;
+    }
+    if (!(ext > 0.0)) continue; /* flat: every cell along k */
+    const double sk = (double)R / ext;
+    const double a = ((double)r->o[k] - (double)bx[k]) * sk;
+    const double bb = (double)r->d[k] * sk;
+    for (int j = 0; j < R; ++j) {
+      const double ulo = j == 0 ? -INFINITY : (double)j;
+      const double uhi = j == R - 1 ? INFINITY : (double)(j + 1);
+      if (bb == 0.0) {
+        if (!(a >= ulo && a <= uhi)) { lo[k][j] = 1.0; hi[k][j] = 0.0; }
+        continue;
+      }
+      double ta = (ulo - a) / bb, tb = (uhi - a) / bb;
+      if (ta > tb) { const double x = ta; ta = tb; tb = x; }
+      if (ta > lo[k][j]) lo[k][j] = ta;
+      if (tb < hi[k][j]) hi[k][j] = tb;
+    }
+  }
+  memset(m, 0, sizeof(uint32_t) * (size_t)W);
+  for (int z = 0; z < R; ++z)
+    for (int y = 0; y < R; ++y)
+      for (int x = 0; x < R; ++x) {
+        double l = lo[0][x], h = hi[0][x];
+        if (lo[1][y] > l) l = lo[1][y];
+        if (lo[2][z] > l) l = lo[2][z];
+        if (hi[1][y] < h) h = hi[1][y];
+        if (hi[2][z] < h) h = hi[2][z];
+        /* a relative slack of 2^-40 keeps touching cells despite rounding */
+        if (l <= h + 1e-12 * (1.0 + fabs(h))) {
+          const int bit = cell_bit(R, x, y, z);
+          m[bit >> 5] |= 1u << (bit & 31);
+        }
+      }
+}
+
 static int cull_pass(const OrBvh* b, const ORay* r, const float* bx, float tn,
                      float tf, const uint32_t* objmask) {
   int R = b->R, W = b->W, R3 = R * R * R;
+  if (b->ideal) {
+    uint32_t rm[16];
+    ideal_ray_mask(r, bx, tn, tf, R, rm);
+    for (int w = 0; w < W; ++w)
+      if (rm[w] & objmask[w]) return 1;
+    return 0;
+  }
   int cb[3], ce[3];
   for (int k = 0; k < 3; ++k) {
     cb[k] = or_cell_t(tn, r->o[k], r->d[k], bx[k], bx[3 + k], R);

@@ -57,6 +57,10 @@ int or_encode_naive(const uint32_t* mask, const uint32_t* clut, int K, int R);
 typedef struct OrBvh OrBvh;
 OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins);
 void or_bvh_free(OrBvh* b);
+/* 1: every later culling test of this BVH uses the exact ray mask (the
+   cells the clipped segment meets, found in double) instead of the
+   lookup table -- the paper's "ideal culling" reference of Sec. 4.1. */
+void or_bvh_set_ideal(OrBvh* b, int ideal);
 int64_t or_bvh_num_nodes(const OrBvh* b);
 int or_bvh_max_depth(const OrBvh* b);
 void or_bvh_root(const OrBvh* b, int32_t* child, int32_t* count, float* box6);
