@@ -407,6 +407,16 @@ sc_status sc_mlp_to_bf16(const float* d_w, void* d_wb, void* stream);
 sc_status sc_mlp_forward(const void* d_wb, const float* d_rays, int64_t n,
                          const float* d_box, int32_t* d_cls, float* d_logits,
                          float min_prob, void* stream);
+/* The same top-1 / logits on the tensor cores: layers 2 and 3 run as
+   tcgen05 BF16 x BF16 -> FP32 matrix products over tiles of 128 rays, with
+   the hidden activations rounded to BF16 on entry (layer 1 and the
+   epilogues in FP32).  d_status: device uint32, set to 0 by the call and to
+   a non-zero value if a wait for the tensor cores ran out (the kernel then
+   stops early; poll it after synchronizing).  Logits agree with
+   sc_mlp_forward to the BF16 rounding of the activations. */
+sc_status sc_mlp_forward_tc(const void* d_wb, const float* d_rays, int64_t n,
+                            const float* d_box, int32_t* d_cls, float* d_logits,
+                            float min_prob, void* d_status, void* stream);
 /* Workspace bytes of one training batch. */
 size_t sc_mlp_train_workspace_bytes(int64_t batch);
 /* Gradient of the mean cross-entropy of a batch (d_labels: int32 classes)

@@ -108,5 +108,16 @@ def loss_only(flat, X, y) -> float:
     return float(np.mean(np.log(np.exp(z - m).sum(1)) + m[:, 0] - z[np.arange(len(y)), y]))
 
 
+def logits_bf16_activations(flat_bf16, X) -> np.ndarray:
+    """Logits when the hidden activations enter layers 2 and 3 rounded to
+    BF16 (round to nearest even) -- the tensor-core form of the forward."""
+    p = unpack(flat_bf16)
+    h1 = gelu(X @ p["W1"].T + p["b1"])
+    h1 = bf16_round(h1.astype(np.float32)).astype(np.float64)
+    h2 = gelu(h1 @ p["W2"].T + p["b2"])
+    h2 = bf16_round(h2.astype(np.float32)).astype(np.float64)
+    return h2 @ p["W3"].T + p["b3"]
+
+
 def top1(flat_bf16, X) -> np.ndarray:
     return forward(unpack(flat_bf16), X)[-1].argmax(1)

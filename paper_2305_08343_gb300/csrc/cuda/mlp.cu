@@ -323,6 +323,250 @@ __global__ void labels_kernel(const float4* rays, const float4* hits, long long 
   }
 }
 
+// ------------------------------------------------ tensor-core inference --
+// Layers 2 and 3 of the forward pass on the 5th-generation tensor cores:
+// per tile of 128 rays, tcgen05.mma (kind::f16, BF16 operands from shared
+// memory, FP32 accumulators in tensor memory) computes [128 x 64] x [64 x 64]
+// and [128 x 64] x [64 x 256]; the epilogues read the accumulators back with
+// tcgen05.ld (thread i of the CTA owns row i, i.e. TMEM lane i), add the
+// bias, apply GELU / take the top-1.  Layer 1 (K = 6) stays on the CUDA
+// cores.  The hidden activations enter the tensor cores rounded to BF16.
+//
+// Operands use the no-swizzle K-major layout of 8 x 8 "core matrices" (8
+// rows x 16 bytes, stored contiguously): element (row r, k) of a K = 64
+// operand sits at byte ((r / 8) * 8 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// so core matrices adjacent along K are 128 bytes apart and 8-row groups
+// 1024 bytes apart.  Every address a descriptor can reach stays inside the
+// operand's own buffer whichever way those two strides are read.
+namespace tc {
+
+constexpr int M = 128;           // rays per tile (TMEM lanes)
+constexpr int K = 64;            // hidden width = K of layers 2 and 3
+constexpr int kTmemCols = 256;   // accumulator columns (N of layer 3)
+constexpr unsigned kSpinLimit = 1u << 24;  // bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+  return (uint32_t)(((r >> 3) * 8 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+// Shared-memory matrix descriptor: start, leading-dimension (K) byte
+// offset, stride-dimension (8-row) byte offset, fixed field 0b001 at bit 46,
+// no swizzle.
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void commit(void* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ bool wait_parity(void* mbar, uint32_t parity) {
+  for (unsigned it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct __align__(1024) Smem {
+  __nv_bfloat16 w3[256 * K];  // B of layer 3 (N = 256), core-matrix layout
+  __nv_bfloat16 w2[64 * K];   // B of layer 2 (N = 64)
+  __nv_bfloat16 a[M * K];     // A of layer 2, then of layer 3
+  float w1[64 * IN], b1[64], b2[64], b3[256];
+  unsigned long long mbar;
+  uint32_t tmem_slot;
+  int err;
+};
+
+}  // namespace tc
+
+// Status bit of a tensor-core wait that ran out (the kernel then stops).
+constexpr unsigned kMlpTimeout = 1u;
+
+__global__ void __launch_bounds__(tc::M) infer_tc_kernel(const __nv_bfloat16* wb,
+                                                          const float4* rays, long long n,
+                                                          const float* box, int* cls,
+                                                          float* logits, float min_prob,
+                                                          unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw_tc[];
+  tc::Smem& sm = *reinterpret_cast<tc::Smem*>(smem_raw_tc);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // stage the weights: W2, W3 into the core-matrix layout, the rest as floats
+  for (int i = tid; i < 64 * tc::K; i += blockDim.x) {
+    const int r = i / tc::K, k = i % tc::K;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.w2) +
+                                      tc::core_off(r, k)) = wb[OFF_W2 + i];
+  }
+  for (int i = tid; i < 256 * tc::K; i += blockDim.x) {
+    const int r = i / tc::K, k = i % tc::K;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.w3) +
+                                      tc::core_off(r, k)) = wb[OFF_W3 + i];
+  }
+  for (int i = tid; i < 64 * IN; i += blockDim.x) sm.w1[i] = __bfloat162float(wb[OFF_W1 + i]);
+  for (int i = tid; i < 64; i += blockDim.x) {
+    sm.b1[i] = __bfloat162float(wb[OFF_B1 + i]);
+    sm.b2[i] = __bfloat162float(wb[OFF_B2 + i]);
+  }
+  for (int i = tid; i < 256; i += blockDim.x) sm.b3[i] = __bfloat162float(wb[OFF_B3 + i]);
+  if (tid == 0) {
+    sm.err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&sm.mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc::smem_u32(&sm.tmem_slot)),
+                 "r"(tc::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sm.tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t a_addr = tc::smem_u32(sm.a), w2_addr = tc::smem_u32(sm.w2),
+                 w3_addr = tc::smem_u32(sm.w3);
+  float bx[6];
+  for (int k = 0; k < 6; ++k) bx[k] = box[k];
+  uint32_t phase = 0;
+  for (long long t0 = (long long)blockIdx.x * tc::M; t0 < n; t0 += (long long)gridDim.x * tc::M) {
+    const long long r = t0 + tid;
+    // layer 1 on the CUDA cores: h1 = gelu(W1 x + b1) -> BF16 A tile
+    float x[IN];
+    if (r < n) {
+      features(__ldg(&rays[2 * r]), __ldg(&rays[2 * r + 1]), bx, x);
+    } else {
+      for (int i = 0; i < IN; ++i) x[i] = 0.0f;
+    }
+    unsigned char* abytes = reinterpret_cast<unsigned char*>(sm.a);
+#pragma unroll 8
+    for (int o = 0; o < 64; ++o) {
+      float acc = sm.b1[o];
+#pragma unroll
+      for (int i = 0; i < IN; ++i) acc += sm.w1[o * IN + i] * x[i];
+      *reinterpret_cast<__nv_bfloat16*>(abytes + tc::core_off(tid, o)) =
+          __float2bfloat16_rn(gelu(acc));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 2: [128 x 64] x [64 x 64] into TMEM columns 0..63
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < tc::K / 16; ++s)
+        tc::mma(tmem, tc::desc(a_addr + s * 256, 128, 1024), tc::desc(w2_addr + s * 256, 128, 1024),
+                tc::idesc(tc::M, 64), s > 0);
+      tc::commit(&sm.mbar);
+    }
+    if (!tc::wait_parity(&sm.mbar, phase)) {
+      if (tid == 0) atomicOr(status, kMlpTimeout);
+      sm.err = 1;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sm.err) break;
+    // epilogue 2: h2 = gelu(acc + b2) -> BF16 A tile (layer 2 is done with it)
+#pragma unroll
+    for (int c = 0; c < 64; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        *reinterpret_cast<__nv_bfloat16*>(abytes + tc::core_off(tid, c + j)) =
+            __float2bfloat16_rn(gelu(v[j] + sm.b2[c + j]));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 3: [128 x 64] x [64 x 256] into TMEM columns 0..255
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < tc::K / 16; ++s)
+        tc::mma(tmem, tc::desc(a_addr + s * 256, 128, 1024), tc::desc(w3_addr + s * 256, 128, 1024),
+                tc::idesc(tc::M, 256), s > 0);
+      tc::commit(&sm.mbar);
+    }
+    if (!tc::wait_parity(&sm.mbar, phase)) {
+      if (tid == 0) atomicOr(status, kMlpTimeout);
+      sm.err = 1;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sm.err) break;
+    // epilogue 3: logits = acc + b3; top-1 with the optional abstention
+    float best = -INFINITY, se = 0.0f;
+    int bi = 0;
+    for (int c = 0; c < 256; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float z = v[j] + sm.b3[c + j];
+        if (logits && r < n) logits[r * OUT + c + j] = z;
+        if (z > best) {
+          if (min_prob > 0.0f) se = se * expf(best - z) + 1.0f;
+          best = z;
+          bi = c + j;
+        } else if (min_prob > 0.0f) {
+          se += expf(z - best);
+        }
+      }
+    }
+    if (r < n) cls[r] = (min_prob > 0.0f && se * min_prob > 1.0f) ? -1 : bi;
+    // the next tile's layer 1 overwrites the A tile and layer 2 the
+    // accumulators only after every thread has read them
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tc::kTmemCols));
+}
+
 int num_sms() {
   static std::once_flag f;
   static int sms = 0;
@@ -407,6 +651,31 @@ sc_status sc_mlp_forward(const void* d_wb, const float* d_rays, int64_t n, const
                        reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const __nv_bfloat16*>(d_wb), reinterpret_cast<const float4*>(d_rays), n,
       d_box, d_cls, d_logits, min_prob);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_forward_tc(const void* d_wb, const float* d_rays, int64_t n,
+                            const float* d_box, int32_t* d_cls, float* d_logits, float min_prob,
+                            void* d_status, void* stream) {
+  SC_TRY
+  check_box(d_box);
+  if (n < 0 || (n > 0 && (!d_wb || !d_rays || !d_cls || !d_status)))
+    fail(SC_ERR_ARG, "sc_mlp_forward_tc: bad args");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_OK(cudaMemsetAsync(d_status, 0, sizeof(unsigned), st));
+  if (n == 0) return SC_OK;
+  const size_t smem = sizeof(mlpk::tc::Smem);
+  CUDA_OK(cudaFuncSetAttribute((const void*)mlpk::infer_tc_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  long long tiles = (n + mlpk::tc::M - 1) / mlpk::tc::M;
+  // two CTAs per SM share its 512 TMEM columns
+  const long long cap = 2LL * mlpk::num_sms();
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+  mlpk::infer_tc_kernel<<<grid, mlpk::tc::M, smem, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(d_wb), reinterpret_cast<const float4*>(d_rays), n,
+      d_box, d_cls, d_logits, min_prob, reinterpret_cast<unsigned*>(d_status));
   CUDA_OK(cudaGetLastError());
   return SC_OK;
   SC_CATCH

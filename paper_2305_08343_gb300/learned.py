@@ -66,6 +66,7 @@ class LearnedProposal:
         self.m = torch.zeros_like(self.grad)
         self.v = torch.zeros_like(self.grad)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self._status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.step = 0
         sc.sc_mlp_to_bf16(self.w, self.wb)
 
@@ -134,14 +135,24 @@ class LearnedProposal:
         return float(tail.mean().item())
 
     # ------------------------------------------------------- inference --
-    def predict(self, rays, cls=None, logits=None, min_prob: float = 0.0):
+    def predict(self, rays, cls=None, logits=None, min_prob: float = 0.0,
+                tensor_cores: bool = True):
         """Top-1 frontier index per ray (device int32[n]); -1 (no seed) where
-        the top-1 probability is below min_prob."""
+        the top-1 probability is below min_prob.  tensor_cores: layers 2 and
+        3 as tcgen05 products (BF16 activations), else FP32 CUDA cores."""
         import torch
         if cls is None:
             cls = torch.empty(rays.shape[0], dtype=torch.int32, device=self.device)
-        sc.sc_mlp_forward(self.wb, rays, self.box, cls, logits, min_prob)
+        if tensor_cores:
+            sc.sc_mlp_forward_tc(self.wb, rays, self.box, cls, self._status, logits, min_prob)
+        else:
+            sc.sc_mlp_forward(self.wb, rays, self.box, cls, logits, min_prob)
         return cls
+
+    def check(self):
+        """Raises if a tensor-core wait ran out in a forward pass."""
+        if int(self._status.item()) != 0:
+            raise RuntimeError("tensor-core forward: a wait for the tensor cores ran out")
 
     def trace(self, dbvh: sc.DeviceBVH, rays, cls, hits=None, counts=None, cull: int = 1,
               work=None):

@@ -130,6 +130,7 @@ def lib():
             "sc_mlp_to_bf16": (C.c_int, [vp, vp, vp]),
             "sc_mlp_forward": (C.c_int, [vp, vp, i64, vp, vp, vp, C.c_float, vp]),
             "sc_mlp_train_workspace_bytes": (C.c_size_t, [i64]),
+            "sc_mlp_forward_tc": (C.c_int, [vp, vp, i64, vp, vp, vp, C.c_float, vp, vp]),
             "sc_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_size_t, vp]),
             "sc_mlp_adam": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float,
                                       C.c_float, C.c_float, vp]),
@@ -528,6 +529,16 @@ def sc_mlp_forward(wb, rays, box, cls, logits=None, min_prob: float = 0.0, strea
                                 C.c_void_p(cls.data_ptr()),
                                 C.c_void_p(logits.data_ptr()) if logits is not None else None,
                                 min_prob, _stream_ptr(stream)))
+
+
+def sc_mlp_forward_tc(wb, rays, box, cls, status, logits=None, min_prob: float = 0.0,
+                      stream=None):
+    """Tensor-core forward (tcgen05); status: device int32[1] (0 = ok)."""
+    _check(lib().sc_mlp_forward_tc(C.c_void_p(wb.data_ptr()), C.c_void_p(rays.data_ptr()),
+                                   rays.shape[0], C.c_void_p(box.data_ptr()),
+                                   C.c_void_p(cls.data_ptr()),
+                                   C.c_void_p(logits.data_ptr()) if logits is not None else None,
+                                   min_prob, C.c_void_p(status.data_ptr()), _stream_ptr(stream)))
 
 
 def sc_mlp_train_workspace_bytes(batch: int) -> int:

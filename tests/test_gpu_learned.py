@@ -301,3 +301,39 @@ def test_trained_proposal_gain():
           f"of rays; node+tri tests/ray {tests}")
     assert acc["trained"] >= acc["majority"] + 0.08
     assert acc["trained"] >= acc["untrained"] + 0.5
+
+
+@pytest.mark.parametrize("n", [1, 127, 3001, 70000])
+def test_mlp_forward_tensor_cores(n):
+    """tcgen05 forward against the fp64 reference with BF16 activations;
+    ragged tile counts (1, 127, 3001) and more tiles than CTAs (70,000)."""
+    _need_gpu()
+    w = _params(5)
+    dw, wb = _upload_weights(w)
+    wr = omlp.bf16_round(w)
+    rays = sg.random_rays(n, seed=n)
+    r = torch.from_numpy(rays).cuda()
+    box = torch.from_numpy(BOX).cuda()
+    cls = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+    logits = torch.empty((n, 256), dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sc.sc_mlp_forward_tc(wb, r, box, cls, status, logits)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    z = omlp.logits_bf16_activations(wr.astype(np.float64), omlp.features(rays, BOX))
+    zg = logits.cpu().numpy()
+    err = np.abs(zg - z)
+    assert np.all(err <= 2e-2 + 1e-2 * np.abs(z)), float(err.max())
+    assert np.median(err) < 1e-3
+    top = np.sort(z, 1)
+    clear = (top[:, -1] - top[:, -2]) > 0.05
+    c = cls.cpu().numpy()
+    if clear.any():
+        assert (c == z.argmax(1))[clear].mean() >= 0.999
+    assert np.array_equal(c, zg.argmax(1))  # top-1 of the kernel's own logits
+    # abstention, and the CUDA-core forward agrees away from ties
+    cls2 = torch.empty(n, dtype=torch.int32, device="cuda")
+    sc.sc_mlp_forward(wb, r, box, cls2, None)
+    torch.cuda.synchronize()
+    if clear.any():
+        assert (cls2.cpu().numpy() == c)[clear].mean() >= 0.99
