@@ -76,6 +76,28 @@ def measured_traffic(workload: str):
     return (entry[0], entry[2]) if sha == entry[1] else (None, None)
 
 
+def mean_wide_children(bvh) -> float:
+    """Mean children of a 4-wide node: the nodes are the binary nodes at
+    even depth, each with 2 + (its inner children) children."""
+    e = bvh.export()
+    child, count = e["child"], e["count"]
+    nn = len(child)
+    if nn == 0:
+        return 2.0
+    depth = np.full(nn, -1, np.int64)
+    depth[0] = 0
+    level = np.array([0])
+    d = 0
+    while level.size:
+        inner = count[level] == 0
+        nxt = child[level][inner]
+        depth[nxt] = d + 1
+        level, d = nxt, d + 1
+    even = depth % 2 == 0
+    kids = 2 + (count[even] == 0).sum(1)
+    return float(kids.mean())
+
+
 def max_over_ranks(x: float, dist=None, device=None) -> float:
     """The largest value of x over all ranks (x itself without a process
     group): the timed region of a multi-GPU run is the slowest rank's."""
@@ -166,7 +188,7 @@ def cpu_count():
 
 
 def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, stride=1,
-                      leaf_min=0):
+                      leaf_min=0, width=2):
     """Times the oracle's traversal (threads split the rays statically) on a
     sample of rays sized to roughly budget_s seconds of CPU time."""
     import oracle  # noqa: F401  (the oracle package; CPU baseline only)
@@ -174,7 +196,8 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, s
     # calibrate on a small sample
     m = min(n, 512)
     t0 = time.perf_counter()
-    ob.trace(rays[:m], 0, cull, skip_bits=skip_bits, stride=stride, leaf_min=leaf_min)
+    ob.trace(rays[:m], 0, cull, skip_bits=skip_bits, stride=stride, leaf_min=leaf_min,
+             width=width)
     per_ray = (time.perf_counter() - t0) / m
     sample = int(min(n, max(threads * 256, budget_s * threads / max(per_ray, 1e-9))))
     idx = np.linspace(0, n - 1, sample).astype(np.int64)
@@ -185,7 +208,7 @@ def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, s
     bounds = np.linspace(0, sample, threads + 1).astype(np.int64)
     ts = [threading.Thread(target=ob.trace, args=(sub, 0, cull, int(bounds[i]),
                                                    int(bounds[i + 1]), out, skip_bits, stride,
-                                                   leaf_min))
+                                                   leaf_min, width))
           for i in range(threads)]
     t0 = time.perf_counter()
     for t in ts:
@@ -380,8 +403,9 @@ def run_gpu(args):
                           max_leaf=args.max_leaf, gpu_masks=int(args.gpu_masks))
     build_s = time.perf_counter() - t0
     info = bvh.info()
-    d_masked = sc.DeviceBVH(bvh, args.layout)
-    d_plain = sc.DeviceBVH(bvh, sc.SC_LAYOUT_PLAIN)
+    wide = args.width == 4
+    d_masked = sc.DeviceBVH(bvh, sc.SC_LAYOUT_MASKED4 if wide else args.layout)
+    d_plain = sc.DeviceBVH(bvh, sc.SC_LAYOUT_PLAIN4 if wide else sc.SC_LAYOUT_PLAIN)
     n = rays_np.shape[0]
     rays = torch.from_numpy(rays_np).to(dev)
     opts = sc._opts(lut_mode=args.lut, refill=args.refill)
@@ -553,11 +577,17 @@ def run_gpu(args):
 
     # roofline of the wave kernel: algorithmic bytes per ray (ray 32 + hit 16
     # + path 4 + node records + 48-B triangles; spawned rays add 32 + 4)
-    node_bytes = ((96 if args.layout == 1 else 64) +
-                  (0 if comp else 2 * {4: 8, 6: 32, 8: 64}[R]))
+    mstride = {4: 8, 6: 32, 8: 64}[R]
+    if wide:
+        # a 4-wide node is made from every binary node at even depth and
+        # holds 2 + its inner children: node tests / mean children = visits
+        node_bytes = 176 + (0 if comp else 4 * mstride)
+        visits = cnt_c[0] / mean_wide_children(bvh)
+    else:
+        node_bytes = (96 if args.layout == 1 else 64) + (0 if comp else 2 * mstride)
+        visits = cnt_c[0] / 2.0
     spawned = float(np.sum(sizes[1:])) / rays_per_step
-    b_ray = (32 + 16 + 4 + (cnt_c[0] / 2.0) * node_bytes + cnt_c[1] * 48
-             + spawned * (32 + 4))
+    b_ray = (32 + 16 + 4 + visits * node_bytes + cnt_c[1] * 48 + spawned * (32 + 4))
     per_launch_bytes = b_ray * rays_per_step
     avg_ms = float(np.mean(ms_cull))
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
@@ -565,7 +595,7 @@ def run_gpu(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic, traffic_src = measured_traffic(args.workload)
     if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
-            or args.leaf_min or args.L != 3 or args.max_leaf != 4
+            or args.leaf_min or args.L != 3 or args.max_leaf != 4 or wide
             or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)):
         traffic, traffic_src = None, None  # measured for the default configuration only
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -579,7 +609,8 @@ def run_gpu(args):
         if H == 0:
             learned_out = {"skipped": "the learned proposal is trained on camera rays"}
         else:
-            learned_out = run_learned(args, bvh, d_masked, dev, flush, W, H)
+            d_learn = sc.DeviceBVH(bvh, args.layout) if wide else d_masked  # binary frontier
+            learned_out = run_learned(args, bvh, d_learn, dev, flush, W, H)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -592,7 +623,7 @@ def run_gpu(args):
         thr = cpu_count()
         v, sample, dt, _ = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0,
                                              args.skip_bits or R ** 3, args.stride,
-                                             args.leaf_min)
+                                             args.leaf_min, args.width)
         cpu = {"value": v / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{sample} primary rays evenly spaced over the {n}, culled closest hit, "
                          f"{dt:.1f} s on {thr} threads (oracle's own BVH and masks)"}
@@ -609,6 +640,7 @@ def run_gpu(args):
                    "layout": args.layout, "refill": args.refill,
                    "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
                    "leaf_min_tris": args.leaf_min, "max_leaf": args.max_leaf,
+                   "node_width": args.width,
                    "gpu_masks": bool(args.gpu_masks),
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
@@ -660,6 +692,8 @@ def main():
     ap.add_argument("--waves-once", action="store_true",
                     help="one culled and one plain wave-pipeline launch (for ncu captures)")
     ap.add_argument("--max-leaf", type=int, default=4, help="triangles per BVH leaf (1..8)")
+    ap.add_argument("--width", type=int, default=2, choices=[2, 4],
+                    help="children per node record: 2 (binary) or 4 (4-wide layouts)")
     ap.add_argument("--gpu-masks", action="store_true",
                     help="build the object masks on the GPU (same bits as the host build)")
     ap.add_argument("--leaf-min", type=int, default=0,

@@ -174,6 +174,23 @@ enum {
                                   Alg. 1 scales R/extent precomputed in the
                                   node: 96 B compressed, 64+32+2*mask bytes
                                   uncompressed                             */
+  SC_LAYOUT_PLAIN4 = 3,        /* 4-wide nodes without masks (see below)         */
+  SC_LAYOUT_MASKED4 = 4,       /* 4-wide nodes with masks (or LUT indices) and
+                                  scales.  4-wide nodes (the paper's Sec. 3.2.4
+                                  setting): the node made from binary node n
+                                  holds, in order, for each child slot c of n,
+                                  the two child slots of c if c is inner, else
+                                  c itself (2..4 children, each keeping its
+                                  binary slot's box, mask and LUT index);
+                                  pre-order numbering.  Record: six float4 of
+                                  lo.x, lo.y, lo.z, hi.x, hi.y, hi.z of the
+                                  four children, the four slot words (unused:
+                                  0xFFFFFFFF), the four meta words, then (masked)
+                                  the four children's scales as three float4
+                                  and the four masks: 128 bytes plain, 176
+                                  compressed, 176 + 4 mask strides else.
+                                  Children are visited by entry distance,
+                                  ties by position. */
   SC_LAYOUT_MASKED_COMPACT = 2 /* masks (or LUT indices) only; the scales are
                                   divided on the fly: 64 B compressed,
                                   64+2*mask bytes uncompressed               */

@@ -95,6 +95,11 @@ def lib():
                                           _P(f),
                                           _P(i32), _P(f), _P(u32)]),
             "or_bvh_set_ideal": (None, [vp, C.c_int]),
+            "or_bvh_wide": (i64, [vp]),
+            "or_bvh_wide_export": (None, [vp, _P(i32), _P(i64), _P(i32), _P(i64)]),
+            "or_trace4_range": (C.c_int, [vp, _P(f), _P(f), i64, i64, C.c_int, C.c_int,
+                                          C.c_int, C.c_int, C.c_int, _P(f), _P(i32), _P(f),
+                                          _P(u32), _P(u32)]),
             "or_pcg_hash": (u32, [u32]),
             "or_bounce_hash": (u32, [u32, u32, u32, u32]),
             "or_bounce": (C.c_int, [_P(f), f, _P(f), u32, u32, u32, _P(f)]),
@@ -273,7 +278,7 @@ class OracleBVH:
 
     def trace(self, rays: np.ndarray, mode: int = 0, cull: int = 0,
               r_begin: int = 0, r_end: int | None = None, out=None, skip_bits: int | None = None,
-              stride: int = 1, leaf_min: int = 0):
+              stride: int = 1, leaf_min: int = 0, width: int = 2):
         """Alg. 4.  cull: 0 plain, 1 uncompressed masks, 2 compressed masks.
         skip_bits: children whose mask has at least this many bits set are
         kept untested (default R^3: only all-ones masks); stride: inner
@@ -290,7 +295,8 @@ class OracleBVH:
                        uv=np.zeros((n, 2), np.float32),
                        counts=np.zeros((n, 2), np.uint32),
                        mask_tests=np.zeros(n, np.uint32))
-        rc = lib().or_trace_range(self._h, _ptr(self.tris, C.c_float), _ptr(rays, C.c_float),
+        fn = lib().or_trace4_range if width == 4 else lib().or_trace_range
+        rc = fn(self._h, _ptr(self.tris, C.c_float), _ptr(rays, C.c_float),
                                   r_begin, r_end, mode, cull, skip_bits, stride, leaf_min,
                                   _ptr(out["t"], C.c_float),
                                   _ptr(out["id"], C.c_int32), _ptr(out["uv"], C.c_float),
@@ -344,6 +350,19 @@ def _set_ideal(self, ideal: bool = True):
     return self
 
 
+def _wide(self):
+    """4-wide view: dict(n[k], parent[k,4], child[k,4], next[k,4])."""
+    k = int(lib().or_bvh_wide(self._h))
+    n = np.zeros(max(k, 1), np.int32)
+    p = np.zeros((max(k, 1), 4), np.int64)
+    c = np.zeros((max(k, 1), 4), np.int32)
+    nx = np.zeros((max(k, 1), 4), np.int64)
+    lib().or_bvh_wide_export(self._h, _ptr(n, C.c_int32), _ptr(p, C.c_int64),
+                             _ptr(c, C.c_int32), _ptr(nx, C.c_int64))
+    return dict(n=n[:k], parent=p[:k], child=c[:k], next=nx[:k])
+
+
+OracleBVH.wide = _wide
 OracleBVH.set_ideal = _set_ideal
 OracleBVH.frontier = _frontier
 OracleBVH.trace_seeded = _trace_seeded

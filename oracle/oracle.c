@@ -433,6 +433,14 @@ struct OrBvh {
   uint8_t* cidx;   /* [nn][2] */
   uint32_t* raylut;
   int ideal; /* 1: culling tests use the exact ray mask (ideal_ray_mask) */
+  /* 4-wide view (or_bvh_wide): per 4-wide node its child slots as (binary
+     parent node, child index), and the 4-wide node of each inner child */
+  int64_t nn4;
+  int32_t* w4n;     /* [nn4] number of children (2..4) */
+  int64_t* w4p;     /* [nn4][4] */
+  int32_t* w4c;     /* [nn4][4] */
+  int64_t* w4next;  /* [nn4][4] 4-wide node of an inner child, -1 for a leaf */
+  int w4depth;      /* deepest 4-wide node (root 0) */
 };
 
 typedef struct {
@@ -631,6 +639,10 @@ void or_bvh_free(OrBvh* b) {
   free(b->cidx);
   free(b->raylut);
   free(b->ndepth);
+  free(b->w4n);
+  free(b->w4p);
+  free(b->w4c);
+  free(b->w4next);
   free(b);
 }
 
@@ -1104,6 +1116,205 @@ static void trace_one(const OrBvh* b, const float* tris, const float* ray8,
   counts[0] = ntest;
   counts[1] = ttest;
   if (mtests) *mtests = mtest;
+}
+
+/* ------------------------------------------------------- 4-wide nodes --- */
+/*
+ * 4-wide BVH (the paper's node layout is 4-wide, Sec. 3.2.4 / Fig. 5),
+ * made from the binary tree.  The 4-wide node made from binary node n takes,
+ * in order, for each child slot c of n: the two child slots of c when c is
+ * an inner node, else slot c itself -- 2 to 4 slots, each a slot (p, c) of
+ * the binary tree, so it keeps that slot's box, object mask and LUT index.
+ * An inner child slot (p, c) is the 4-wide node made from binary node
+ * child[p][c].  4-wide nodes are numbered in pre-order (root node 0).
+ */
+static int64_t wide_rec(OrBvh* b, int64_t n, int depth) {
+  int64_t q = b->nn4++;
+  int k = 0;
+  if (depth > b->w4depth) b->w4depth = depth;
+  for (int c = 0; c < 2; ++c) {
+    if (b->count[2 * n + c] == 0) {
+      int64_t m = b->child[2 * n + c];
+      for (int g = 0; g < 2; ++g) {
+        b->w4p[4 * q + k] = m;
+        b->w4c[4 * q + k] = g;
+        ++k;
+      }
+    } else {
+      b->w4p[4 * q + k] = n;
+      b->w4c[4 * q + k] = c;
+      ++k;
+    }
+  }
+  b->w4n[q] = k;
+  for (int i = 0; i < k; ++i) {
+    int64_t p = b->w4p[4 * q + i];
+    int c = b->w4c[4 * q + i];
+    b->w4next[4 * q + i] =
+        b->count[2 * p + c] == 0 ? wide_rec(b, b->child[2 * p + c], depth + 1) : -1;
+  }
+  return q;
+}
+
+int64_t or_bvh_wide(OrBvh* b) {
+  if (b->w4n) return b->nn4;
+  size_t cap = (size_t)(b->nnodes > 0 ? b->nnodes : 1);
+  b->w4n = (int32_t*)calloc(cap, sizeof(int32_t));
+  b->w4p = (int64_t*)calloc(4 * cap, sizeof(int64_t));
+  b->w4c = (int32_t*)calloc(4 * cap, sizeof(int32_t));
+  b->w4next = (int64_t*)calloc(4 * cap, sizeof(int64_t));
+  b->nn4 = 0;
+  b->w4depth = 0;
+  if (b->ntri > 0 && b->root_count == 0) wide_rec(b, b->root_child, 0);
+  return b->nn4;
+}
+
+void or_bvh_wide_export(const OrBvh* b, int32_t* n, int64_t* p, int32_t* c, int64_t* next) {
+  if (n) memcpy(n, b->w4n, sizeof(int32_t) * (size_t)b->nn4);
+  if (p) memcpy(p, b->w4p, sizeof(int64_t) * 4 * (size_t)b->nn4);
+  if (c) memcpy(c, b->w4c, sizeof(int32_t) * 4 * (size_t)b->nn4);
+  if (next) memcpy(next, b->w4next, sizeof(int64_t) * 4 * (size_t)b->nn4);
+}
+
+typedef struct {
+  int64_t q;              /* 4-wide node, or -1: a leaf */
+  int32_t first, count;   /* the leaf */
+  float tn;
+} Stack4;
+
+/*
+ * Alg. 4 on the 4-wide tree, with the readings of trace_one: the root is
+ * not tested; a visited 4-wide node costs one slab test per child
+ * (node_tests += its 2..4 children); the slab-passing children (after
+ * their culling tests, eager, as in Alg. 4) are ordered by entry distance,
+ * ties by position in the node; the nearest is visited next and the others
+ * are pushed farthest first, so the second nearest is popped first; the
+ * pop rule and the leaf tests are trace_one's.
+ */
+static void trace4_one(const OrBvh* b, const float* tris, const float* ray8, int mode,
+                       int cull, int skip_bits, int stride, int leaf_min, Stack4* stack,
+                       float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts,
+                       uint32_t* mtests) {
+  ORay r;
+  load_ray(ray8, &r);
+  float tcur = r.tmax, bu = 0.0f, bv = 0.0f, bt = INFINITY;
+  int32_t bid = -1;
+  uint32_t ntest = 0, ttest = 0, mtest = 0;
+  int sp = 0, have = b->ntri > 0, done = 0;
+  int64_t q = b->root_count == 0 ? 0 : -1;
+  int32_t lf = b->root_child, lc = b->root_count;
+  while (!done) {
+    if (have) {
+      if (q < 0) {
+        for (int32_t i = 0; i < lc; ++i) {
+          int32_t tid = b->perm[lf + i];
+          float t, u, v;
+          ++ttest;
+          if (mt_test(&r, tris + 9 * (size_t)tid, tcur, &t, &u, &v)) {
+            bt = t; bid = tid; bu = u; bv = v;
+            if (mode == 1) { done = 1; break; }
+            tcur = t;
+          }
+        }
+        have = 0;
+        continue;
+      }
+      const int k = b->w4n[q];
+      float tn[4], tf[4];
+      int hit[4], ord[4], nh = 0;
+      ntest += (uint32_t)k;
+      for (int i = 0; i < k; ++i) {
+        const int64_t p = b->w4p[4 * q + i];
+        const int c = b->w4c[4 * q + i];
+        hit[i] = slab_test(&r, b->box + 12 * p + 6 * c, tcur, &tn[i], &tf[i]);
+        if (hit[i] && cull) {
+          const uint32_t* om = cull == 2 ? b->clut + (size_t)b->cidx[2 * p + c] * b->W
+                                         : b->masks + ((size_t)p * 2 + c) * b->W;
+          const int32_t cnt = b->count[2 * p + c];
+          int test = popcount_mask(om, b->W) < skip_bits;
+          if (cnt == 0 && (b->ndepth[p] + 1) % stride != 0) test = 0;
+          if (cnt > 0 && cnt < leaf_min) test = 0;
+          if (test) {
+            ++mtest;
+            hit[i] = cull_pass(b, &r, b->box + 12 * p + 6 * c, tn[i], tf[i], om);
+          }
+        }
+        if (hit[i]) {
+          /* insertion by (tn, position) */
+          int j = nh++;
+          while (j > 0 && tn[ord[j - 1]] > tn[i]) {
+            ord[j] = ord[j - 1];
+            --j;
+          }
+          ord[j] = i;
+        }
+      }
+      if (nh == 0) {
+        have = 0;
+        continue;
+      }
+      for (int j = nh - 1; j >= 1; --j) {
+        const int i = ord[j];
+        const int64_t p = b->w4p[4 * q + i];
+        const int c = b->w4c[4 * q + i];
+        stack[sp].q = b->w4next[4 * q + i];
+        stack[sp].first = b->child[2 * p + c];
+        stack[sp].count = b->count[2 * p + c];
+        stack[sp].tn = tn[i];
+        ++sp;
+      }
+      {
+        const int i = ord[0];
+        const int64_t p = b->w4p[4 * q + i];
+        const int c = b->w4c[4 * q + i];
+        const int64_t nq = b->w4next[4 * q + i];
+        lf = b->child[2 * p + c];
+        lc = b->count[2 * p + c];
+        q = nq;
+      }
+      continue;
+    }
+    while (sp > 0) {
+      --sp;
+      if (stack[sp].tn > tcur * ROBUST) continue;
+      q = stack[sp].q;
+      lf = stack[sp].first;
+      lc = stack[sp].count;
+      have = 1;
+      break;
+    }
+    if (!have) done = 1;
+  }
+  *hit_t = bt;
+  *hit_id = bid;
+  hit_uv[0] = bu;
+  hit_uv[1] = bv;
+  counts[0] = ntest;
+  counts[1] = ttest;
+  if (mtests) *mtests = mtest;
+}
+
+int or_trace4_range(OrBvh* b, const float* tris, const float* rays, int64_t r_begin,
+                    int64_t r_end, int mode, int cull, int skip_bits, int stride, int leaf_min,
+                    float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts,
+                    uint32_t* mask_tests) {
+  if (stride < 1) return -3;
+  if (cull && !b->masks) return -1;
+  if (cull == 2 && !b->clut) return -2;
+  if (cull && !b->raylut) {
+    int R3 = b->R * b->R * b->R;
+    uint32_t* lut = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)R3 * R3 * b->W);
+    or_raylut(b->R, lut);
+    b->raylut = lut;
+  }
+  or_bvh_wide(b);
+  Stack4* stack = (Stack4*)malloc(sizeof(Stack4) * (size_t)(3 * (b->w4depth + 2) + 4));
+  for (int64_t i = r_begin; i < r_end; ++i)
+    trace4_one(b, tris, rays + 8 * i, mode, cull, skip_bits, stride, leaf_min, stack,
+               hit_t + i, hit_id + i, hit_uv + 2 * i, counts + 2 * i,
+               mask_tests ? mask_tests + i : NULL);
+  free(stack);
+  return 0;
 }
 
 int or_trace_range(const OrBvh* b, const float* tris, const float* rays,

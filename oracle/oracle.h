@@ -114,6 +114,21 @@ int or_trace_seeded(const OrBvh* b, const float* tris, const float* rays, int64_
                     const int32_t* fchild, const int32_t* fcount, const float* fbox, int nf,
                     float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts);
 
+/* 4-wide view of the binary tree (Sec. 3.2.4 / Fig. 5 use 4-wide nodes):
+   a 4-wide node made from binary node n holds, in order, for each child
+   slot c of n, the two child slots of c if c is inner, else c itself.
+   Returns the number of 4-wide nodes (pre-order, root 0).  Export: per node
+   its child count and per child slot (binary parent, child index, 4-wide
+   node of an inner child or -1). */
+int64_t or_bvh_wide(OrBvh* b);
+void or_bvh_wide_export(const OrBvh* b, int32_t* n, int64_t* p, int32_t* c, int64_t* next);
+/* Alg. 4 on the 4-wide tree (children ordered by entry distance, ties by
+   position); arguments as or_trace_range (builds the 4-wide view). */
+int or_trace4_range(OrBvh* b, const float* tris, const float* rays, int64_t r_begin,
+                    int64_t r_end, int mode, int cull, int skip_bits, int stride, int leaf_min,
+                    float* hit_t, int32_t* hit_id, float* hit_uv, uint32_t* counts,
+                    uint32_t* mask_tests);
+
 /* Single ray-triangle test and slab test, exposed for pins. */
 int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
                float* u, float* v);

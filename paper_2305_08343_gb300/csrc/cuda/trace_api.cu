@@ -19,6 +19,14 @@ WaveKernelFn get_waves_r4(int cull, int lutv, int scales);
 WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack);
 WaveKernelFn get_waves_r8(int cull, int lutv, int scales);
 SeededKernelFn get_seeded_plain();
+KernelFn get_kernel_w4_plain(int mode);
+KernelFn get_kernel_w4_r4(int cull, int mode, int lutv);
+KernelFn get_kernel_w4_r6(int cull, int mode, int lutv);
+KernelFn get_kernel_w4_r8(int cull, int mode, int lutv);
+WaveKernelFn get_waves_w4_plain(int block);
+WaveKernelFn get_waves_w4_r4(int cull, int lutv, int block);
+WaveKernelFn get_waves_w4_r6(int cull, int lutv, int block);
+WaveKernelFn get_waves_w4_r8(int cull, int lutv, int block);
 SeededKernelFn get_seeded_r4(int cull, int lutv, int scales);
 SeededKernelFn get_seeded_r6(int cull, int lutv, int scales);
 SeededKernelFn get_seeded_r8(int cull, int lutv, int scales);
@@ -75,6 +83,17 @@ int lut_variant(const sc_dbvh* d, int lut_mode) {
 }
 
 sct::KernelFn pick_kernel(const sc_dbvh* d, int mode, int cull, int lutv) {
+  if (d->lay.width == 4) {
+    if (!cull) return sct::get_kernel_w4_plain(mode);
+    const int c = d->lay.compress ? 2 : 1;
+    const int lv = lutv == 2 ? 2 : 0;  // 4-wide: global table or bit table
+    switch (d->lay.R) {
+      case 4: return sct::get_kernel_w4_r4(c, mode, lv);
+      case 6: return sct::get_kernel_w4_r6(c, mode, lv);
+      case 8: return sct::get_kernel_w4_r8(c, mode, lv);
+    }
+    fail(SC_ERR_UNSUPPORTED, "no 4-wide kernel for R = %d", d->lay.R);
+  }
   if (!cull) return sct::get_kernel_plain(mode);
   int c = d->lay.compress ? 2 : 1;
   const int sc = d->lay.scales;
@@ -179,6 +198,19 @@ void fill_params(const sc_dbvh* d, sct::Params& p) {
 }
 
 sct::WaveKernelFn pick_waves(const sc_dbvh* d, int cull, int lutv, int block, int stack) {
+  if (d->lay.width == 4) {
+    if (block == 64 || stack != 64)
+      fail(SC_ERR_UNSUPPORTED, "4-wide wave kernels: blocks of 128 / 256, stack 64");
+    if (!cull) return sct::get_waves_w4_plain(block);
+    const int c = d->lay.compress ? 2 : 1;
+    const int lv = lutv == 2 ? 2 : 0;
+    switch (d->lay.R) {
+      case 4: return sct::get_waves_w4_r4(c, lv, block);
+      case 6: return sct::get_waves_w4_r6(c, lv, block);
+      case 8: return sct::get_waves_w4_r8(c, lv, block);
+    }
+    fail(SC_ERR_UNSUPPORTED, "no 4-wide wave kernel for R = %d", d->lay.R);
+  }
   const bool tuned = block != kBlock || stack != sct::kStack;
   if (!cull) return sct::get_waves_plain(block, stack);
   const int c = d->lay.compress ? 2 : 1, sc = d->lay.scales;
@@ -355,10 +387,10 @@ sc_status sc_bvh_upload(const sc_bvh* h, int layout, void* d_buf, size_t nbytes,
   d->base = reinterpret_cast<const uint8_t*>(d_buf);
   d->lay = L;
   d->ntri = b.ntri;
-  d->nn = b.nn;
-  d->root_slot = root_slot_word(b);
+  d->nn = L.nodes;
+  d->root_slot = root_slot_word(b);  // the root node is record 0 at either width
   d->has_root = b.ntri > 0 ? 1 : 0;
-  d->stack_need = b.max_depth + 1;
+  d->stack_need = L.stack_need;
   *out = d;
   return SC_OK;
   SC_CATCH
@@ -393,6 +425,8 @@ sc_status sc_trace_seeded(const sc_dbvh* d, const float* d_rays, int64_t n, cons
       (reinterpret_cast<uintptr_t>(d_counts) & 7) || (reinterpret_cast<uintptr_t>(d_frontier) & 15))
     fail(SC_ERR_ARG, "sc_trace_seeded: misaligned buffer");
   if (cull && d->lay.R == 0) fail(SC_ERR_STATE, "sc_trace_seeded: culling needs a masked image");
+  if (d->lay.width != 2)
+    fail(SC_ERR_UNSUPPORTED, "sc_trace_seeded: the frontier refers to binary nodes (2-wide image)");
   if (d->stack_need > sct::kStack)
     fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
          sct::kStack);
@@ -548,6 +582,10 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
   std::vector<int> stacks;
   if (all_blocks && d->stack_need <= 32) stacks.push_back(32);
   stacks.push_back(64);
+  if (d->lay.width == 4) {
+    blocks = {128, 256};
+    stacks = {64};
+  }
   const int refills[3] = {4, 8, 16};
   std::vector<int64_t> chunks = {n0};
   for (int64_t c = n0 / 2; c >= 65536 && chunks.size() < 3; c /= 2) chunks.push_back(c);

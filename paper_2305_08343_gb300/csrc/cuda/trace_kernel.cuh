@@ -465,6 +465,211 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
   return done;
 }
 
+// Culling test of one child from its record data: Alg. 1 cells of the
+// segment [tn, tf] in the child's grid (lo, scales), the ray-mask lookup and
+// the AND with the object mask `obj` (uncompressed) or LUT entry `meta`.
+template <int R, int CULL, int LUTV>
+__device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R, LUTV>& sh,
+                                          const uint8_t* obj, unsigned meta, const float* lo,
+                                          const float* sk, const float* o, const float* d,
+                                          float tn, float tf) {
+  constexpr int R3 = R * R * R;
+  constexpr int MB = MaskTraits<R>::kStrideBytes;
+  int cb[3], ce[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
+    const float b = __fmul_rn(d[k], sk[k]);
+    cb[k] = cell_of_q<R>(__fmaf_rn(tn, b, a));
+    ce[k] = cell_of_q<R>(__fmaf_rn(tf, b, a));
+  }
+  const int beg = cb[0] + R * cb[1] + R * R * cb[2];
+  const int end = ce[0] + R * ce[1] + R * R * ce[2];
+  if constexpr (LUTV == 3) {
+    const uint2 rm = sh.full.lut[beg * R3 + end];
+    uint2 om;
+    if constexpr (CULL == 1) {
+      om = __ldg(reinterpret_cast<const uint2*>(obj));
+    } else {
+      om = sh.full.clut[meta & 0xFFu];
+    }
+    return ((rm.x & om.x) | (rm.y & om.y)) != 0u;
+  } else if constexpr (CULL == 2 && LUTV == 2) {
+    const unsigned j = meta & 0xFFu;
+    const uint32_t word = __ldg(p.bits + (size_t)(beg * R3 + end) * 8 + (j >> 5));
+    return (word >> (j & 31u)) & 1u;
+  } else {
+    if constexpr (CULL == 2) obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
+    if constexpr (LUTV == 1) {
+      return overlap_factored<R>(sh.f, cb, ce, obj);
+    } else {
+      const uint8_t* rm = reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
+      return masks_overlap<R>(rm, obj);
+    }
+  }
+}
+
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+
+// One traversal step on 4-wide nodes (SC_LAYOUT_PLAIN4 / MASKED4): a leaf
+// as in trace_step, or one node: the slab tests of its (2..4) children,
+// their culling tests, then the slab-passing children ordered by entry
+// distance (ties by position); the nearest is visited next, the others
+// pushed farthest first.  Counts: node_tests += the node's children.
+template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack>
+__device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2* stack,
+                                            const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
+  constexpr int RR = (R > 0 ? R : 4);
+  constexpr int MB = MaskTraits<RR>::kStrideBytes;
+  bool done = false;
+  if (s.have) {
+    if (s.cur & kLeaf) {
+      const int first = (int)(s.cur & 0x0FFFFFFFu);
+      const int left = (int)((s.cur >> 28) & 7u) + 1;
+      const int cnt = left < kTrisPerStep ? left : kTrisPerStep;
+      for (int i = 0; i < cnt; ++i) {
+        const float4* tp = p.tris + 3 * (long long)(first + i);
+        const float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
+        ++s.ttest;
+        float t, u, v;
+        if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
+          s.ht = t;
+          s.hu = u;
+          s.hv = v;
+          s.hid = __float_as_int(A.w);
+          s.hpos = first + i;
+          if (MODE == 1) {
+            done = true;
+            break;
+          }
+          s.tcur = t;
+        }
+      }
+      if (!done && left > cnt) {
+        s.cur = kLeaf | ((uint32_t)(left - cnt - 1) << 28) | (uint32_t)(first + cnt);
+      } else {
+        s.have = false;
+      }
+    } else {
+      const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
+      const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
+      const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5);
+      const uint4 sl = __ldg(reinterpret_cast<const uint4*>(nd + 6));
+      const uint32_t slot[4] = {sl.x, sl.y, sl.z, sl.w};
+      const float lo[4][3] = {{lx.x, ly.x, lz.x}, {lx.y, ly.y, lz.y}, {lx.z, ly.z, lz.z},
+                              {lx.w, ly.w, lz.w}};
+      const float hi[4][3] = {{hx.x, hy.x, hz.x}, {hx.y, hy.y, hz.y}, {hx.z, hy.z, hz.z},
+                              {hx.w, hy.w, hz.w}};
+      const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+      float tn[4], tf[4];
+      bool hit[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float a0[3], a1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a0[k] = __fmul_rn(__fsub_rn(lo[c][k], o[k]), inv[k]);
+          a1[k] = __fmul_rn(__fsub_rn(hi[c][k], o[k]), inv[k]);
+        }
+        tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
+                      fmaxf(fminf(a0[2], a1[2]), s.tmin));
+        tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
+                      fminf(fmaxf(a0[2], a1[2]), s.tcur));
+        hit[c] = slot[c] != kNoSlot && tn[c] <= __fmul_rn(tf[c], kRobust);
+      }
+      s.ntest += (slot[2] != kNoSlot ? 1u : 0u) + (slot[3] != kNoSlot ? 1u : 0u) + 2u;
+      if constexpr (CULL != 0) {
+        const uint4 me = __ldg(reinterpret_cast<const uint4*>(nd + 7));
+        const unsigned meta[4] = {me.x, me.y, me.z, me.w};
+        unsigned need = 0u;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (hit[c] && !(meta[c] & kMetaFull)) need |= 1u << c;
+        if (need) {
+          const float4 sx = __ldg(nd + 8), sy = __ldg(nd + 9), sz = __ldg(nd + 10);
+          const float scl[4][3] = {{sx.x, sy.x, sz.x}, {sx.y, sy.y, sz.y}, {sx.z, sy.z, sz.z},
+                                   {sx.w, sy.w, sz.w}};
+          const float d[3] = {s.dx, s.dy, s.dz};
+          const uint8_t* objs = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4);
+          // one test per needed child; a lane runs only its own
+          while (need) {
+            const int c = __ffs(need) - 1;
+            need &= need - 1u;
+            float l3[3], s3[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              l3[k] = c == 0 ? lo[0][k] : c == 1 ? lo[1][k] : c == 2 ? lo[2][k] : lo[3][k];
+              s3[k] = c == 0 ? scl[0][k] : c == 1 ? scl[1][k] : c == 2 ? scl[2][k] : scl[3][k];
+            }
+            const float tnc = c == 0 ? tn[0] : c == 1 ? tn[1] : c == 2 ? tn[2] : tn[3];
+            const float tfc = c == 0 ? tf[0] : c == 1 ? tf[1] : c == 2 ? tf[2] : tf[3];
+            const unsigned mc = c == 0 ? meta[0] : c == 1 ? meta[1] : c == 2 ? meta[2] : meta[3];
+            if (!cull_test<RR, CULL, LUTV>(p, sh, objs + c * MB, mc, l3, s3, o, d, tnc, tfc)) {
+              if (c == 0) hit[0] = false;
+              else if (c == 1) hit[1] = false;
+              else if (c == 2) hit[2] = false;
+              else hit[3] = false;
+            }
+          }
+        }
+      }
+      // order the surviving children by (tn, position)
+      int ord[4];
+      int nh = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (!hit[c]) continue;
+        if (!slot_ok(slot[c], (long long)s.cur, p)) {
+          atomicOr(p.status, (unsigned)ST_BAD_NODE);
+          done = true;
+        }
+        int j = nh++;
+        while (j > 0 && tn[ord[j - 1]] > tn[c]) {
+          ord[j] = ord[j - 1];
+          --j;
+        }
+        ord[j] = c;
+      }
+      if (!done) {
+        if (nh == 0) {
+          s.have = false;
+        } else if (s.sp + nh - 1 > STACK) {
+          atomicOr(p.status, (unsigned)ST_STACK);
+          done = true;
+        } else {
+          for (int j = nh - 1; j >= 1; --j) {
+            stack[s.sp] = make_uint2(slot[ord[j]], __float_as_uint(tn[ord[j]]));
+            ++s.sp;
+          }
+          s.cur = slot[ord[0]];
+        }
+      }
+    }
+  }
+  if (!done && !s.have) {
+    while (s.sp > 0) {
+      --s.sp;
+      if (__uint_as_float(stack[s.sp].y) > __fmul_rn(s.tcur, kRobust)) continue;
+      s.cur = stack[s.sp].x;
+      s.have = true;
+      break;
+    }
+    if (!s.have) done = true;
+  }
+  return done;
+}
+
+// The step of a trace or wave kernel of the given node width.
+template <int WIDTH, int R, int CULL, int MODE, int LUTV, int SCALES, int STACK>
+__device__ __forceinline__ bool step_w(const Params& p, RayState& s, uint2* stack,
+                                       const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
+  if constexpr (WIDTH == 4) {
+    return trace_step4<R, CULL, MODE, LUTV, SCALES, STACK>(p, s, stack, sh);
+  } else {
+    return trace_step<R, CULL, MODE, LUTV, SCALES, STACK>(p, s, stack, sh);
+  }
+}
+
 // Warp-level ray fetch: once at least `refill` lanes are idle (or all are),
 // the warp takes that many ray indices with one atomicAdd; returns the index
 // for this lane (or -1).  `exhausted` turns warp-uniformly true once the
@@ -491,7 +696,7 @@ __device__ __forceinline__ long long warp_fetch(bool active, unsigned* counter, 
 // 3 (R = 4 only) the full table and the LUT in shared memory.
 // SCALES: 1 = the per-child Alg. 1 scales R/extent are precomputed in the
 // node record, 0 = divided.
-template <int R, int CULL, int MODE, int LUTV, int SCALES>
+template <int R, int CULL, int MODE, int LUTV, int SCALES, int WIDTH = 2>
 __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
@@ -513,7 +718,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
     }
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
-    if (trace_step<R, CULL, MODE, LUTV, SCALES>(p, s, stack, sh)) {
+    if (step_w<WIDTH, R, CULL, MODE, LUTV, SCALES, kStack>(p, s, stack, sh)) {
       p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
@@ -664,7 +869,8 @@ static __device__ __noinline__ bool make_bounce(float ox, float oy, float oz, fl
 // queue holds only spawned rays: compacted).  A bounded grid barrier
 // separates the waves.  Outputs: wave 0 by primary index; wave w >= 1 after
 // the entries of the previous chunks.
-template <int R, int CULL, int LUTV, int SCALES, int BLOCK = kBlock, int STACK = kStack>
+template <int R, int CULL, int LUTV, int SCALES, int BLOCK = kBlock, int STACK = kStack,
+          int WIDTH = 2>
 __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_kernel(WaveParams wp) {
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
@@ -706,7 +912,7 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
         }
         if (!__any_sync(0xffffffffu, active)) break;
         const bool done =
-            active && trace_step<R, CULL, 0, LUTV, SCALES, STACK>(p, s, stack, sh);
+            active && step_w<WIDTH, R, CULL, 0, LUTV, SCALES, STACK>(p, s, stack, sh);
         if (!__any_sync(0xffffffffu, done)) continue;
         bool spawn = false;
         float4 b0, b1;

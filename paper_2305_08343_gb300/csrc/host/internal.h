@@ -96,6 +96,9 @@ constexpr int64_t kMaxTris = int64_t(1) << 28;
 
 struct ImageLayout {
   int layout = 0;          // SC_LAYOUT_*
+  int width = 2;           // children per node record (2, or 4 for the *4 layouts)
+  int64_t nodes = 0;       // node records in the image
+  int stack_need = 0;      // deepest possible traversal stack
   int R = 0, W = 0, mstride = 0, compress = 0, K = 0;
   int scales = 0;          // per-child Alg. 1 scales stored at +64
   int mask_off = 64;       // first object mask inside a node record

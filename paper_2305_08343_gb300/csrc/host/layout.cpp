@@ -39,9 +39,88 @@ static uint32_t slot_word(int32_t child, int32_t count) {
   return (uint32_t)child;
 }
 
+// 4-wide view: the node made from binary node n takes, in order, for each
+// child slot c of n, the two child slots of c if c is inner, else c itself;
+// inner children are the nodes made from their binary nodes; pre-order.
+struct Wide {
+  std::vector<int32_t> n;     // [nodes] children (2..4)
+  std::vector<int64_t> p;     // [nodes][4] binary parent of each child slot
+  std::vector<int32_t> c;     // [nodes][4] child index in that parent
+  std::vector<int64_t> next;  // [nodes][4] wide node of an inner child, -1 leaf
+  int depth = 0;
+};
+
+static void wide_build(const Bvh& b, Wide& w) {
+  if (b.ntri == 0 || b.root_count > 0) return;
+  struct Item {
+    int64_t n;       // binary node the wide node is made from
+    int depth;
+    int64_t parent;  // wide parent (-1: the root) and its child index
+    int slot;
+  };
+  // pre-order: a node, then the whole subtree of its first inner child,
+  // then the next (a stack with the children pushed in reverse)
+  std::vector<Item> st{Item{b.root_child, 0, -1, 0}};
+  while (!st.empty()) {
+    const Item it = st.back();
+    st.pop_back();
+    const int64_t q = (int64_t)w.n.size();
+    if (it.parent >= 0) w.next[4 * it.parent + it.slot] = q;
+    w.depth = std::max(w.depth, it.depth);
+    w.n.push_back(0);
+    for (int k = 0; k < 4; ++k) {
+      w.p.push_back(-1);
+      w.c.push_back(0);
+      w.next.push_back(-1);
+    }
+    int k = 0;
+    for (int c = 0; c < 2; ++c) {
+      if (b.count[2 * it.n + c] == 0) {
+        const int64_t m = b.child[2 * it.n + c];
+        for (int g = 0; g < 2; ++g, ++k) {
+          w.p[4 * q + k] = m;
+          w.c[4 * q + k] = g;
+        }
+      } else {
+        w.p[4 * q + k] = it.n;
+        w.c[4 * q + k] = c;
+        ++k;
+      }
+    }
+    w.n[q] = k;
+    for (int i = k - 1; i >= 0; --i) {
+      const int64_t pp = w.p[4 * q + i];
+      const int cc = w.c[4 * q + i];
+      if (b.count[2 * pp + cc] == 0) st.push_back(Item{b.child[2 * pp + cc], it.depth + 1, q, i});
+    }
+  }
+}
+
 ImageLayout image_layout(const Bvh& b, int layout) {
   ImageLayout L;
   L.layout = layout;
+  if (layout == SC_LAYOUT_PLAIN4 || layout == SC_LAYOUT_MASKED4) {
+    Wide w;
+    wide_build(b, w);
+    L.width = 4;
+    L.nodes = (int64_t)w.n.size();
+    L.stack_need = 3 * (w.depth + 1) + 1;
+    L.node_bytes = 128;
+    if (layout == SC_LAYOUT_MASKED4) {
+      if (b.R <= 0) fail(SC_ERR_STATE, "masked layout requested for a BVH built without masks");
+      L.R = b.R;
+      L.W = mask_words(b.R);
+      L.mstride = mask_stride(b.R);
+      L.compress = b.compress;
+      L.K = b.K;
+      L.scales = 1;
+      L.mask_off = 176;
+      L.node_bytes = b.compress ? 176 : 176 + 4 * L.mstride;
+    }
+  } else {
+    L.nodes = b.nn;
+    L.stack_need = b.max_depth + 1;
+  }
   if (layout == SC_LAYOUT_MASKED || layout == SC_LAYOUT_MASKED_COMPACT) {
     if (b.R <= 0) fail(SC_ERR_STATE, "masked layout requested for a BVH built without masks");
     L.R = b.R;
@@ -52,12 +131,13 @@ ImageLayout image_layout(const Bvh& b, int layout) {
     L.scales = layout == SC_LAYOUT_MASKED ? 1 : 0;
     L.mask_off = L.scales ? 96 : 64;
     L.node_bytes = b.compress ? L.mask_off : L.mask_off + 2 * L.mstride;
-  } else if (layout != SC_LAYOUT_PLAIN) {
+  } else if (layout != SC_LAYOUT_PLAIN && layout != SC_LAYOUT_PLAIN4 &&
+             layout != SC_LAYOUT_MASKED4) {
     fail(SC_ERR_ARG, "unknown layout %d", layout);
   }
   size_t off = 256;
   L.off_nodes = off;
-  off = align256(off + (size_t)b.nn * L.node_bytes);
+  off = align256(off + (size_t)L.nodes * L.node_bytes);
   L.off_tris = off;
   off = align256(off + (size_t)b.ntri * 48);
   if (L.R > 0) {
@@ -89,6 +169,60 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
   hdr[4] = (uint32_t)b.nn;
   hdr[5] = (uint32_t)b.ntri;
   hdr[6] = root_slot_word(b);
+  // meta word of binary child slot (n, c): LUT index and "keep untested"
+  auto meta_of = [&](int64_t n, int c) -> uint32_t {
+    const uint32_t* m = L.compress ? &b.clut[(size_t)b.cidx[2 * n + c] * L.W]
+                                   : &b.masks[((size_t)n * 2 + c) * L.W];
+    uint32_t meta = L.compress ? (uint32_t)b.cidx[2 * n + c] : 0u;
+    const int stride = b.opts.test_stride > 1 ? b.opts.test_stride : 1;
+    const int32_t cnt = b.count[2 * n + c];
+    const bool inner = cnt == 0;
+    if (skip_test(m, L.R, b.opts.skip_bits) || (inner && (b.ndepth[n] + 1) % stride != 0) ||
+        (!inner && cnt < b.opts.leaf_min_tris))
+      meta |= kMetaFull;
+    return meta;
+  };
+  if (L.width == 4) {
+    Wide w;
+    wide_build(b, w);
+    parallel_for((int64_t)w.n.size(), resolve_threads(0), 8192, [&](int64_t q) {
+      uint8_t* rec = base + L.off_nodes + (size_t)q * L.node_bytes;
+      float* f = reinterpret_cast<float*>(rec);
+      uint32_t* slots = reinterpret_cast<uint32_t*>(rec + 96);
+      uint32_t* metas = reinterpret_cast<uint32_t*>(rec + 112);
+      for (int i = 0; i < 4; ++i) {
+        if (i >= w.n[q]) {
+          for (int k = 0; k < 3; ++k) {
+            f[4 * k + i] = 1.0f;       // an empty box (lo > hi); never tested:
+            f[4 * (3 + k) + i] = 0.0f;  // the slot word marks the child unused
+          }
+          slots[i] = 0xFFFFFFFFu;
+          metas[i] = kMetaFull;
+          if (L.scales)
+            for (int k = 0; k < 3; ++k) reinterpret_cast<float*>(rec + 128)[4 * k + i] = 0.0f;
+          continue;
+        }
+        const int64_t pn = w.p[4 * q + i];
+        const int c = w.c[4 * q + i];
+        const float* bx = &b.box[12 * pn + 6 * c];
+        for (int k = 0; k < 3; ++k) {
+          f[4 * k + i] = bx[k];
+          f[4 * (3 + k) + i] = bx[3 + k];
+        }
+        const int32_t cnt = b.count[2 * pn + c];
+        slots[i] = cnt > 0 ? slot_word(b.child[2 * pn + c], cnt) : (uint32_t)w.next[4 * q + i];
+        metas[i] = L.R > 0 ? meta_of(pn, c) : 0u;
+        if (L.R > 0) {
+          float* sc = reinterpret_cast<float*>(rec + 128);
+          for (int k = 0; k < 3; ++k)
+            sc[4 * k + i] = (float)L.R / std::fmax(bx[3 + k] - bx[k], 1e-30f);
+          if (!L.compress)
+            std::memcpy(rec + L.mask_off + i * L.mstride, &b.masks[((size_t)pn * 2 + c) * L.W],
+                        4 * L.W);
+        }
+      }
+    });
+  } else
   parallel_for(b.nn, resolve_threads(0), 16384, [&](int64_t n) {
     uint8_t* rec = base + L.off_nodes + (size_t)n * L.node_bytes;
     float* f = reinterpret_cast<float*>(rec);
@@ -103,17 +237,10 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
     u[2] = u[3] = 0u;
     if (L.R > 0) {
       for (int c = 0; c < 2; ++c) {
-        const uint32_t* m = L.compress ? &b.clut[(size_t)b.cidx[2 * n + c] * L.W]
-                                       : &b.masks[((size_t)n * 2 + c) * L.W];
-        uint32_t meta = L.compress ? (uint32_t)b.cidx[2 * n + c] : 0u;
-        const int stride = b.opts.test_stride > 1 ? b.opts.test_stride : 1;
-        const int32_t cnt = b.count[2 * n + c];
-        const bool inner = cnt == 0;
-        if (skip_test(m, L.R, b.opts.skip_bits) || (inner && (b.ndepth[n] + 1) % stride != 0) ||
-            (!inner && cnt < b.opts.leaf_min_tris))
-          meta |= kMetaFull;
-        u[2 + c] = meta;
-        if (!L.compress) std::memcpy(rec + L.mask_off + c * L.mstride, m, 4 * L.W);
+        u[2 + c] = meta_of(n, c);
+        if (!L.compress)
+          std::memcpy(rec + L.mask_off + c * L.mstride, &b.masks[((size_t)n * 2 + c) * L.W],
+                      4 * L.W);
       }
       if (L.scales) {
         float* sc = reinterpret_cast<float*>(rec + 64);

@@ -21,6 +21,7 @@ SC_ERR_STACK, SC_ERR_UNSUPPORTED, SC_ERR_STATE, SC_ERR_IO = -5, -6, -7, -8
 SC_SCENE_HAIR, SC_SCENE_SOUP = 0, 1
 SC_RAYS_PINHOLE, SC_RAYS_RANDOM = 0, 1
 SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED, SC_LAYOUT_MASKED_COMPACT = 0, 1, 2
+SC_LAYOUT_PLAIN4, SC_LAYOUT_MASKED4 = 3, 4
 SC_CLOSEST, SC_ANY = 0, 1
 SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED, SC_LUT_BITTABLE = 0, 1, 2, 3
 STATUS_NAMES = {0: "SC_OK", -1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_NOMEM",

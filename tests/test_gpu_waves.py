@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _oracle_waves(tris, rays, bounces, seed, R, comp, cull, skip_bits=None):
+def _oracle_waves(tris, rays, bounces, seed, R, comp, cull, skip_bits=None, width=2):
     ob = oracle.OracleBVH(tris)
     if R:
         ob.build_masks(R, 3)
@@ -24,7 +24,7 @@ def _oracle_waves(tris, rays, bounces, seed, R, comp, cull, skip_bits=None):
     waves = []
     cur, path = rays, np.arange(len(rays))
     for w in range(bounces + 1):
-        o = ob.trace(cur, 0, mode, skip_bits=skip_bits)
+        o = ob.trace(cur, 0, mode, skip_bits=skip_bits, width=width)
         waves.append(dict(path=path, **o))
         if w < bounces:
             cur, path = oracle.bounce_wave(cur, o["t"], o["id"], tris, seed, w + 1, path)
@@ -179,3 +179,19 @@ def test_wait_timeout_is_reported_and_the_context_survives():
         pc = ref.path[w][:m].cpu().numpy()
         oa, oc = np.argsort(pa, kind="stable"), np.argsort(pc, kind="stable")
         assert np.array_equal(pa[oa], pc[oc]) and np.array_equal(a[oa], c[oc])
+
+
+@pytest.mark.parametrize("cull,comp,lut", [(0, 0, 0), (1, 0, 0), (1, 1, sc.SC_LUT_BITTABLE),
+                                           (1, 1, sc.SC_LUT_GLOBAL)])
+@pytest.mark.parametrize("block", [128, 256])
+def test_wide_waves_match_oracle(cull, comp, lut, block):
+    tris = sg.hair(400, 16, True, seed=31)
+    rays = sg.pinhole(64, 48)
+    lay = sc.SC_LAYOUT_MASKED4 if cull else sc.SC_LAYOUT_PLAIN4
+    g = _gpu_waves(tris, rays, 2, 1234, 6, comp, cull, lay, lut, block=block, stack=64)
+    o = _oracle_waves(tris, rays, 2, 1234, 6, comp, cull, width=4)
+    for w in range(3):
+        assert np.array_equal(g[w]["path"], o[w]["path"]), w
+        assert np.array_equal(g[w]["id"], o[w]["id"]), w
+        assert np.array_equal(g[w]["t"], o[w]["t"]), w
+        assert np.array_equal(g[w]["counts"], o[w]["counts"]), w
