@@ -290,6 +290,10 @@ def _sorted_waves(bufs, sizes):
     return out
 
 
+# FLOPs of one network evaluation: 2 (6*64 + 64*64 + 64*256)
+NET_FLOPS_PER_RAY = 2 * (6 * 64 + 64 * 64 + 64 * 256)
+
+
 def run_learned(args, bvh, d_masked, dev, flush, W, H):
     """Learned proposal against plain culled traversal on held-out rays:
     train on the GPU (training pairs from the plain traversal of jittered
@@ -366,7 +370,15 @@ def run_learned(args, bvh, d_masked, dev, flush, W, H):
             ms_l.append(ev[0].elapsed_time(ev[2]))
             ms_p.append(ev[3].elapsed_time(e4))
         sc.sc_status_poll(work)
+        peaks = load_peaks() or {}
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        net_tflops = n * NET_FLOPS_PER_RAY / (np.mean(ms_net) * 1e-3) / 1e12
         out[key] = {
+            "network_roofline": {"bound": "tensor", "achieved": net_tflops, "peak": bf16,
+                                 "unit": "TFLOP/s", "frac": net_tflops / bf16,
+                                 "peak_source": "measured" if "bf16_tflops" in peaks
+                                 else "fallback", "flops_per_ray": NET_FLOPS_PER_RAY,
+                                 "kernel": "infer_tc_kernel (tcgen05)"},
             "identical_hits": same,
             "seeded_fraction": float((cls >= 0).double().mean().item()),
             "learned_mrays_s": n / (np.mean(ms_l) * 1e-3) / 1e6,
