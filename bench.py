@@ -461,6 +461,18 @@ def run_gpu(args):
     cat_c = torch.cat([x[2] for x in wc]).double()
     cat_p = torch.cat([x[2] for x in wpl]).double()
     cnt_c, cnt_p = cat_c.mean(0).tolist(), cat_p.mean(0).tolist()
+
+    def pct(cat):
+        # p50 / p99 of node, tri and node + tri tests per ray
+        q = torch.tensor([0.5, 0.99], dtype=torch.float64, device=cat.device)
+        both = torch.cat([cat, cat.sum(1, keepdim=True)], 1)
+        sample = both[torch.linspace(0, both.shape[0] - 1, min(both.shape[0], 1 << 22),
+                                     device=cat.device).long()]
+        v = torch.quantile(sample, q, dim=0).cpu().numpy()
+        return {"p50": {"node": v[0, 0], "tri": v[0, 1], "node_plus_tri": v[0, 2]},
+                "p99": {"node": v[1, 0], "tri": v[1, 1], "node_plus_tri": v[1, 2]}}
+
+    pct_c, pct_p = pct(cat_c), pct(cat_p)
     rays_per_step = int(np.sum(sizes))
     del ref_c, ref_p, wc, wpl, cat_c, cat_p
 
@@ -662,9 +674,13 @@ def run_gpu(args):
         "autotuned": tuned or None,
         "identical_hits": same, "culled_counts_le_plain": le,
         "tests_per_ray": {"culled": {"node": cnt_c[0], "tri": cnt_c[1],
-                                     "node_plus_tri": cnt_c[0] + cnt_c[1]},
+                                     "node_plus_tri": cnt_c[0] + cnt_c[1],
+                                     **{k: {a: float(b) for a, b in v.items()}
+                                        for k, v in pct_c.items()}},
                           "plain": {"node": cnt_p[0], "tri": cnt_p[1],
-                                    "node_plus_tri": cnt_p[0] + cnt_p[1]}},
+                                    "node_plus_tri": cnt_p[0] + cnt_p[1],
+                                    **{k: {a: float(b) for a, b in v.items()}
+                                       for k, v in pct_p.items()}}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "learned_proposal": learned_out,
         "gpu_launches": args.steps,

@@ -149,6 +149,21 @@ class LearnedProposal:
             sc.sc_mlp_forward(self.wb, rays, self.box, cls, logits, min_prob)
         return cls
 
+    def state_dict(self) -> dict:
+        """Weights, Adam moments and step (host tensors) for torch.save."""
+        return {"w": self.w.cpu(), "m": self.m.cpu(), "v": self.v.cpu(), "step": self.step,
+                "depth": self.depth, "n_frontier": self.n_frontier}
+
+    def load_state_dict(self, st: dict):
+        """Restores a state_dict made for a BVH with the same frontier."""
+        if st["depth"] != self.depth or st["n_frontier"] != self.n_frontier:
+            raise ValueError("the state belongs to another frontier")
+        self.w.copy_(st["w"])
+        self.m.copy_(st["m"])
+        self.v.copy_(st["v"])
+        self.step = int(st["step"])
+        sc.sc_mlp_to_bf16(self.w, self.wb)
+
     def check(self):
         """Raises if a tensor-core wait ran out in a forward pass."""
         if int(self._status.item()) != 0:

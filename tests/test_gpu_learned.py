@@ -337,3 +337,21 @@ def test_mlp_forward_tensor_cores(n):
     torch.cuda.synchronize()
     if clear.any():
         assert (cls2.cpu().numpy() == c)[clear].mean() >= 0.99
+
+
+def test_proposal_state_round_trip(tmp_path):
+    _need_gpu()
+    tris = sg.hair(512, 16, True, seed=6)
+    b = sc.sc_bvh_build(tris, 6, 0)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    lp = learned.LearnedProposal(b, depth=8, seed=3)
+    r, l = lp.collect(d, [learned.primary_rays(64, 64, 1)], bounces=1, seed=5)
+    lp.fit(r, l, steps=20, batch=1024)
+    p = tmp_path / "proposal.pt"
+    torch.save(lp.state_dict(), p)
+    lp2 = learned.LearnedProposal(b, depth=8, seed=99)
+    lp2.load_state_dict(torch.load(p))
+    c1, c2 = lp.predict(r), lp2.predict(r)
+    torch.cuda.synchronize()
+    assert torch.equal(c1, c2) and lp2.step == lp.step
+    assert torch.equal(lp.wb.view(torch.int16), lp2.wb.view(torch.int16))
