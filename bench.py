@@ -577,27 +577,51 @@ def run_gpu(args):
             torch.cuda.synchronize()
             anyhit[name] = 3 * n / (ev[2].elapsed_time(ev[3]) * 1e-3) / 1e6
 
-    # end to end through the public API: pinned host rays -> device, the wave
-    # pipeline, every wave's hit buffer -> pinned host
+    # end to end through the public API: every step copies its rays from
+    # pinned host memory, runs the wave pipeline and copies every wave's hit
+    # buffer back to pinned host memory.  Two buffer sets and three streams
+    # (upload, traversal, download) let step i+1's upload and step i-1's
+    # download overlap step i's traversal.
     h_rays = torch.from_numpy(rays_np).pin_memory()
-    h_hits = [torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in range(bounces + 1)]
-    d_rays = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    h_hits = [[torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in range(bounces + 1)]
+              for _ in range(2)]
+    d_rays2 = [torch.empty((n, 8), dtype=torch.float32, device=dev) for _ in range(2)]
+    bufs2 = [bufs_c, sc.WaveBuffers(n, bounces, with_counts=False, device=dev)]
+    s_up, s_run, s_down = (torch.cuda.Stream(device=dev) for _ in range(3))
 
-    def e2e_step():
-        d_rays.copy_(h_rays, non_blocking=True)
-        sc.sc_trace_waves(d_masked, d_rays, bounces, seed, 1, bufs_c.outs(), bufs_c.ws, opts_c)
-        for w in range(bounces + 1):
-            h_hits[w].copy_(bufs_c.hits[w], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+    def e2e_run(k_steps):
+        up = [torch.cuda.Event() for _ in range(2)]
+        ran = [torch.cuda.Event() for _ in range(2)]
+        down = [None, None]
+        for i in range(k_steps):
+            k = i & 1
+            with torch.cuda.stream(s_up):
+                if down[k] is not None:  # the slot's previous hits have left
+                    s_up.wait_event(down[k])
+                d_rays2[k].copy_(h_rays, non_blocking=True)
+                up[k].record(s_up)
+            s_run.wait_event(up[k])
+            sc.sc_trace_waves(d_masked, d_rays2[k], bounces, seed, 1, bufs2[k].outs(), bufs2[k].ws,
+                              opts_c, stream=s_run)
+            ran[k].record(s_run)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(ran[k])
+                for w in range(bounces + 1):
+                    h_hits[k][w].copy_(bufs2[k].hits[w], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_down)
+                down[k] = ev
+        for st in (s_up, s_run, s_down):
+            st.synchronize()
 
-    for _ in range(args.warmup):
-        e2e_step()
+    e2e_run(max(2, args.warmup))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    e2e_run(args.steps)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": rays_per_step * args.steps / e2e_s / 1e6, "unit": "Mrays/s",
-           "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 16 * (bounces + 1)}
+           "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 16 * (bounces + 1),
+           "overlap": "double-buffered: upload i+1 and download i-1 overlap traversal i"}
+    sc.sc_waves_poll(bufs2[1].ws, bounces)
 
     # roofline of the wave kernel: algorithmic bytes per ray (ray 32 + hit 16
     # + path 4 + node records + 48-B triangles; spawned rays add 32 + 4)
