@@ -1,9 +1,9 @@
 // masks_gpu.cu — the object masks of every child slot built on the GPU
-// (sc_build_opts.gpu_masks): the same per-slot computation as the host
-// builder (host/mask_math.h, one source), one thread per child slot, the
-// levels of the tree processed from the deepest so that each level reads
-// only finished masks of deeper nodes.  The bits are identical to the host
-// build's.
+// (sc_build_opts.gpu_masks): the same per-voxel and per-cell computation as
+// the host builder (host/mask_math.h, one source), one warp per child slot,
+// the levels of the tree processed from the deepest so that each level
+// reads only finished masks of deeper nodes.  The bits are identical to the
+// host build's.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,10 +15,115 @@
 namespace sc {
 namespace {
 
+// One warp per child slot: the lanes split each triangle's candidate voxels
+// (SAT tests) and each descendant's child cells (Alg. 2 fill), each lane
+// collecting bits in its own copy of the mask, OR-reduced at the end.  The
+// per-voxel and per-cell arithmetic is mask_math.h's, so the bits are those
+// of the host build.
+__device__ void voxelize_warp(const float* t9, const mm::Grid& g, uint32_t* acc, int W,
+                              int lane) {
+  double v[9];
+  for (int i = 0; i < 9; ++i) v[i] = (double)t9[i];
+  int r0[3], r1[3];
+  for (int k = 0; k < 3; ++k) {
+    const double tlo = mm::mn(mm::mn(v[k], v[3 + k]), v[6 + k]);
+    const double thi = mm::mx(mm::mx(v[k], v[3 + k]), v[6 + k]);
+    g.candidates(k, tlo, thi, r0[k], r1[k]);
+  }
+  const int R = g.R, nx = r1[0] - r0[0] + 1, ny = r1[1] - r0[1] + 1, nz = r1[2] - r0[2] + 1;
+  // voxels an earlier triangle set need no test (the bits are an OR)
+  uint32_t have[16];
+  for (int w = 0; w < W; ++w) have[w] = __reduce_or_sync(0xffffffffu, acc[w]);
+  for (int i = lane; i < nx * ny * nz; i += 32) {
+    const int x = r0[0] + i % nx, y = r0[1] + (i / nx) % ny, z = r0[2] + i / (nx * ny);
+    if (mm::get_bit(have, x + R * y + R * R * z)) continue;
+    const double bmin[3] = {g.b0[0][x], g.b0[1][y], g.b0[2][z]};
+    const double bmax[3] = {g.b1[0][x], g.b1[1][y], g.b1[2][z]};
+    if (mm::tri_box_overlap(v, bmin, bmax)) mm::set_bit(acc, x + R * y + R * R * z);
+  }
+}
+
+__device__ void fill_warp(uint32_t* acc, const float* pbox, const uint32_t* cmask,
+                          const float* cbox, int R, double eps, int lane) {
+  int lo_i[3][9], hi_i[3][9];
+  for (int k = 0; k < 3; ++k) {
+    const double cl = (double)cbox[k], cext = (double)cbox[3 + k] - (double)cbox[k];
+    const double pl = (double)pbox[k], pext = (double)pbox[3 + k] - (double)pbox[k];
+    for (int i = 0; i <= R; ++i) {
+      const double border = cl + (cext * (double)i) / (double)R;
+      if (pext > 0.0) {
+        lo_i[k][i] = mm::parent_idx(border - eps, pl, pext, R);
+        hi_i[k][i] = mm::parent_idx(border + eps, pl, pext, R);
+      } else {
+        lo_i[k][i] = 0;
+        hi_i[k][i] = R - 1;
+      }
+    }
+  }
+  for (int cell = lane; cell < R * R * R; cell += 32) {
+    if (!mm::get_bit(cmask, cell)) continue;
+    const int x = cell % R, y = (cell / R) % R, z = cell / (R * R);
+    for (int pz = lo_i[2][z]; pz <= hi_i[2][z + 1]; ++pz)
+      for (int py = lo_i[1][y]; py <= hi_i[1][y + 1]; ++py)
+        for (int px = lo_i[0][x]; px <= hi_i[0][x + 1]; ++px)
+          mm::set_bit(acc, px + R * py + R * R * pz);
+  }
+}
+
+__device__ void leaf_warp(const mm::MaskInputs& b, int32_t first, int32_t count,
+                          const mm::Grid& g, uint32_t* acc, int lane) {
+  for (int32_t i = 0; i < count; ++i)
+    voxelize_warp(&b.tris[9 * (size_t)b.perm[first + i]], g, acc, b.W, lane);
+}
+
 __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64_t nslots) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nslots) return;
-  mm::slot_mask(in, nodes[i >> 1], (int)(i & 1));
+  const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slot >= nslots) return;  // uniform across the warp
+  const int64_t n = nodes[slot >> 1];
+  const int c = (int)(slot & 1);
+  const float* gbox = &in.box[12 * n + 6 * c];
+  mm::Grid g;
+  g.init(gbox, in.R, in.eps);
+  uint32_t acc[16];
+  for (int w = 0; w < 16; ++w) acc[w] = 0u;
+  const int32_t ch = in.child[2 * n + c], cn = in.count[2 * n + c];
+  if (cn > 0) {
+    leaf_warp(in, ch, cn, g, acc, lane);
+  } else {
+    // the descendants of mm::collect, visited in the same order by every lane
+    int64_t node[mm::kMaxL];
+    int depth[mm::kMaxL], next[mm::kMaxL];
+    int sp = 0;
+    node[0] = ch;
+    depth[0] = 1;
+    next[0] = 0;
+    while (sp >= 0) {
+      if (next[sp] == 2) {
+        --sp;
+        continue;
+      }
+      const int64_t m = node[sp];
+      const int cc = next[sp]++;
+      const int32_t mch = in.child[2 * m + cc], mcn = in.count[2 * m + cc];
+      const float* cbox = &in.box[12 * m + 6 * cc];
+      if (depth[sp] == in.L) {
+        fill_warp(acc, gbox, &in.masks[((size_t)m * 2 + cc) * in.W], cbox, in.R, in.eps, lane);
+      } else if (mcn > 0) {
+        leaf_warp(in, mch, mcn, g, acc, lane);
+      } else {
+        node[sp + 1] = mch;
+        depth[sp + 1] = depth[sp] + 1;
+        next[sp + 1] = 0;
+        ++sp;
+      }
+    }
+  }
+  uint32_t* out = &in.masks[((size_t)n * 2 + c) * in.W];
+  for (int w = 0; w < in.W; ++w) {
+    const uint32_t v = __reduce_or_sync(0xffffffffu, acc[w]);
+    if (lane == 0) out[w] = v;
+  }
 }
 
 #define CUDA_OK(call)                                                        \
@@ -98,9 +203,10 @@ void build_masks_gpu(Bvh& b, int R, int L, double eps) {
   for (int dep = b.max_depth; dep >= 0; --dep) {
     const int64_t nslots = 2 * (int64_t)(start[dep + 1] - start[dep]);
     if (nslots == 0) continue;
-    const int threads = 128;
-    slot_masks_kernel<<<(unsigned)((nslots + threads - 1) / threads), threads, 0, st>>>(
-        in, d_order + start[dep], nslots);
+    const int threads = 128;  // four slots per block, a warp each
+    const int64_t warps_per_block = threads / 32;
+    slot_masks_kernel<<<(unsigned)((nslots + warps_per_block - 1) / warps_per_block), threads, 0,
+                        st>>>(in, d_order + start[dep], nslots);
     CUDA_OK(cudaGetLastError());
   }
   CUDA_OK(cudaMemcpyAsync(b.masks.data(), in.masks, b.masks.size() * sizeof(uint32_t),
