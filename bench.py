@@ -60,8 +60,8 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "
 # SHA-256 of the traversal kernel header.
 MEASURED_TRAFFIC = {
     # workload: (bytes per launch, kernel source sha256, profile summary)
-    "hair1m": (1.681389e9 + 0.244879e9,
-               "c11e8b6583e943e6b32f1158972bae3c188ced3fff63d4340ca2a0af7004c43c",
+    "hair1m": (1.681966e9 + 0.244761e9,
+               "8906f2646f634e6ee3684a6968ba08b4b7e2ef6e72a48844bebe430d723f3b71",
                "profiles/waves_kernel_hair1m.md"),
 }
 

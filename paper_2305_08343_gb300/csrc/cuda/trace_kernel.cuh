@@ -295,6 +295,50 @@ __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const flo
   s.have = p.has_root != 0;
 }
 
+// Culling test of one child from its record data: Alg. 1 cells of the
+// segment [tn, tf] in the child's grid (lo, scales), the ray-mask lookup and
+// the AND with the object mask `obj` (uncompressed) or LUT entry `meta`.
+template <int R, int CULL, int LUTV>
+__device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R, LUTV>& sh,
+                                          const uint8_t* obj, unsigned meta, const float* lo,
+                                          const float* sk, const float* o, const float* d,
+                                          float tn, float tf) {
+  constexpr int R3 = R * R * R;
+  constexpr int MB = MaskTraits<R>::kStrideBytes;
+  int cb[3], ce[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
+    const float b = __fmul_rn(d[k], sk[k]);
+    cb[k] = cell_of_q<R>(__fmaf_rn(tn, b, a));
+    ce[k] = cell_of_q<R>(__fmaf_rn(tf, b, a));
+  }
+  const int beg = cb[0] + R * cb[1] + R * R * cb[2];
+  const int end = ce[0] + R * ce[1] + R * R * ce[2];
+  if constexpr (LUTV == 3) {
+    const uint2 rm = sh.full.lut[beg * R3 + end];
+    uint2 om;
+    if constexpr (CULL == 1) {
+      om = __ldg(reinterpret_cast<const uint2*>(obj));
+    } else {
+      om = sh.full.clut[meta & 0xFFu];
+    }
+    return ((rm.x & om.x) | (rm.y & om.y)) != 0u;
+  } else if constexpr (CULL == 2 && LUTV == 2) {
+    const unsigned j = meta & 0xFFu;
+    const uint32_t word = __ldg(p.bits + (size_t)(beg * R3 + end) * 8 + (j >> 5));
+    return (word >> (j & 31u)) & 1u;
+  } else {
+    if constexpr (CULL == 2) obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
+    if constexpr (LUTV == 1) {
+      return overlap_factored<R>(sh.f, cb, ce, obj);
+    } else {
+      const uint8_t* rm = reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
+      return masks_overlap<R>(rm, obj);
+    }
+  }
+}
+
 // One traversal step of one ray: either the triangles of one leaf or one
 // inner node, then a pop if nothing is left to visit.  Returns true when the
 // ray has finished (or was stopped by a recorded device error).
@@ -302,7 +346,6 @@ template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack>
 __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* stack,
                                            const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
   constexpr int RR = (R > 0 ? R : 4);
-  constexpr int R3 = RR * RR * RR;
   constexpr int MB = MaskTraits<RR>::kStrideBytes;
   bool done = false;
   if (s.have) {
@@ -376,54 +419,18 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
           if (!hit[c] || (meta & kMetaFull)) continue;
           const float* lo = c ? lo1 : lo0;
           const float* hi = c ? hi1 : hi0;
-          int cb[3], ce[3];
+          float sk[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            float sk;
             if constexpr (SCALES) {
-              sk = sc[c][k];
+              sk[k] = sc[c][k];
             } else {
-              sk = scale_of<RR>(lo[k], hi[k]);
-            }
-            const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk);
-            const float b = __fmul_rn(d[k], sk);
-            cb[k] = cell_of_q<RR>(__fmaf_rn(tn[c], b, a));
-            ce[k] = cell_of_q<RR>(__fmaf_rn(tf[c], b, a));
-          }
-          const int beg = cb[0] + RR * cb[1] + RR * RR * cb[2];
-          const int end = ce[0] + RR * ce[1] + RR * RR * ce[2];
-          if constexpr (LUTV == 3) {
-            // R = 4: table and LUT from shared memory
-            const uint2 rm = sh.full.lut[beg * R3 + end];
-            uint2 om;
-            if constexpr (CULL == 1) {
-              om = __ldg(reinterpret_cast<const uint2*>(nd + p.mask_off_f4) + c);
-            } else {
-              om = sh.full.clut[meta & 0xFFu];
-            }
-            hit[c] = ((rm.x & om.x) | (rm.y & om.y)) != 0u;
-          } else if constexpr (CULL == 2 && LUTV == 2) {
-            // Sec. 3.2.2: precomputed bit table (ray-mask row, LUT entry)
-            const unsigned j = meta & 0xFFu;
-            const uint32_t word = __ldg(p.bits + (size_t)(beg * R3 + end) * 8 + (j >> 5));
-            hit[c] = (word >> (j & 31u)) & 1u;
-          } else {
-            const uint8_t* obj;
-            if constexpr (CULL == 1) {
-              obj = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB;
-            } else {
-              obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
-            }
-            if constexpr (LUTV == 0 || LUTV == 2) {
-              const uint8_t* rm =
-                  reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
-              hit[c] = masks_overlap<RR>(rm, obj);
-            } else {
-              if constexpr (LUTV == 1) {
-                hit[c] = overlap_factored<RR>(sh.f, cb, ce, obj);
-              }
+              sk[k] = scale_of<RR>(lo[k], hi[k]);
             }
           }
+          hit[c] = cull_test<RR, CULL, LUTV>(
+              p, sh, reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB, meta, lo, sk,
+              o, d, tn[c], tf[c]);
         }
       }
       const uint32_t s0 = f3.x, s1 = f3.y;
@@ -463,50 +470,6 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
     if (!s.have) done = true;
   }
   return done;
-}
-
-// Culling test of one child from its record data: Alg. 1 cells of the
-// segment [tn, tf] in the child's grid (lo, scales), the ray-mask lookup and
-// the AND with the object mask `obj` (uncompressed) or LUT entry `meta`.
-template <int R, int CULL, int LUTV>
-__device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R, LUTV>& sh,
-                                          const uint8_t* obj, unsigned meta, const float* lo,
-                                          const float* sk, const float* o, const float* d,
-                                          float tn, float tf) {
-  constexpr int R3 = R * R * R;
-  constexpr int MB = MaskTraits<R>::kStrideBytes;
-  int cb[3], ce[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
-    const float b = __fmul_rn(d[k], sk[k]);
-    cb[k] = cell_of_q<R>(__fmaf_rn(tn, b, a));
-    ce[k] = cell_of_q<R>(__fmaf_rn(tf, b, a));
-  }
-  const int beg = cb[0] + R * cb[1] + R * R * cb[2];
-  const int end = ce[0] + R * ce[1] + R * R * ce[2];
-  if constexpr (LUTV == 3) {
-    const uint2 rm = sh.full.lut[beg * R3 + end];
-    uint2 om;
-    if constexpr (CULL == 1) {
-      om = __ldg(reinterpret_cast<const uint2*>(obj));
-    } else {
-      om = sh.full.clut[meta & 0xFFu];
-    }
-    return ((rm.x & om.x) | (rm.y & om.y)) != 0u;
-  } else if constexpr (CULL == 2 && LUTV == 2) {
-    const unsigned j = meta & 0xFFu;
-    const uint32_t word = __ldg(p.bits + (size_t)(beg * R3 + end) * 8 + (j >> 5));
-    return (word >> (j & 31u)) & 1u;
-  } else {
-    if constexpr (CULL == 2) obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
-    if constexpr (LUTV == 1) {
-      return overlap_factored<R>(sh.f, cb, ce, obj);
-    } else {
-      const uint8_t* rm = reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
-      return masks_overlap<R>(rm, obj);
-    }
-  }
 }
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
