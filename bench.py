@@ -412,7 +412,8 @@ def run_gpu(args):
     t0 = time.perf_counter()
     bvh = sc.sc_bvh_build(tris, R, comp, skip_bits=args.skip_bits, L=args.L,
                           test_stride=args.stride, leaf_min_tris=args.leaf_min,
-                          max_leaf=args.max_leaf, gpu_masks=int(args.gpu_masks))
+                          max_leaf=args.max_leaf, gpu_masks=int(args.gpu_masks),
+                          gpu_bvh=int(args.gpu_bvh))
     build_s = time.perf_counter() - t0
     info = bvh.info()
     wide = args.width == 4
@@ -689,7 +690,7 @@ def run_gpu(args):
                    "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
                    "leaf_min_tris": args.leaf_min, "max_leaf": args.max_leaf,
                    "node_width": args.width,
-                   "gpu_masks": bool(args.gpu_masks),
+                   "gpu_masks": bool(args.gpu_masks), "gpu_bvh": bool(args.gpu_bvh),
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -748,6 +749,8 @@ def main():
                     help="children per node record: 2 (binary) or 4 (4-wide layouts)")
     ap.add_argument("--gpu-masks", action="store_true",
                     help="build the object masks on the GPU (same bits as the host build)")
+    ap.add_argument("--gpu-bvh", action="store_true",
+                    help="build the SAH tree on the GPU (the same tree as the host build)")
     ap.add_argument("--leaf-min", type=int, default=0,
                     help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,

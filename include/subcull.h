@@ -95,7 +95,7 @@ sc_status sc_rays_generate(int kind, const sc_ray_params* p, uint64_t seed,
 
 /* ------------------------------------------------------------- build --- */
 typedef struct {
-  int max_leaf;   /* triangles per leaf (<= 4), default 4                   */
+  int max_leaf;   /* triangles per leaf (1..8), default 4                   */
   int bins;       /* SAH bins per axis, default 32                          */
   int L;          /* mask approximation depth (Sec. 3.2.1), default 3       */
   int lut_size;   /* compression LUT entries (Sec. 4.4), default 256        */
@@ -116,6 +116,12 @@ typedef struct {
                       same bits as the host build, which 0 selects); the
                       tree and the compression stay on the host.  Needs a
                       device: SC_ERR_CUDA without one. */
+  int gpu_bvh;     /* 1: the binned-SAH tree is built on the current GPU:
+                      the same tree (numbering, child boxes, leaf ranges,
+                      triangle order; a zero bound may differ in sign) as
+                      the host build, which 0 selects.  Needs bins <= 32
+                      (SC_ERR_UNSUPPORTED otherwise) and a device
+                      (SC_ERR_CUDA without one). */
 } sc_build_opts;
 
 void sc_build_opts_default(sc_build_opts* o);

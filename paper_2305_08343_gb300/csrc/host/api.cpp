@@ -111,6 +111,7 @@ void sc_build_opts_default(sc_build_opts* o) {
   o->test_stride = 1;
   o->leaf_min_tris = 0;
   o->gpu_masks = 0;
+  o->gpu_bvh = 0;
 }
 
 sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
@@ -135,6 +136,8 @@ sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
   if (o.skip_bits < 0) fail(SC_ERR_ARG, "skip_bits must be >= 0");
   if (o.test_stride < 0) fail(SC_ERR_ARG, "test_stride must be >= 0");
   if (o.leaf_min_tris < 0) fail(SC_ERR_ARG, "leaf_min_tris must be >= 0");
+  if (o.gpu_bvh && o.bins > 32)
+    fail(SC_ERR_UNSUPPORTED, "the GPU tree builder takes at most 32 bins (got %d)", o.bins);
   for (int64_t i = 0; i < 9 * n; ++i)
     if (!std::isfinite(tris[i])) fail(SC_ERR_ARG, "triangle %lld has a non-finite coordinate",
                                       (long long)(i / 9));
@@ -142,7 +145,10 @@ sc_status sc_bvh_build(const float* tris, int64_t n, int grid_res, int compress,
   sc_bvh* h = new sc_bvh();
   try {
     h->b.opts = o;
-    build_bvh(h->b, tris, n, o.max_leaf, o.bins, T);
+    if (o.gpu_bvh)
+      build_bvh_gpu(h->b, tris, n, o.max_leaf, o.bins);
+    else
+      build_bvh(h->b, tris, n, o.max_leaf, o.bins, T);
     if (grid_res > 0) {
       if (o.gpu_masks)
         build_masks_gpu(h->b, grid_res, o.L, scene_eps(tris, n, o.eps_rel));

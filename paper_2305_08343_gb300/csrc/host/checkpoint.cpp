@@ -20,7 +20,7 @@ using namespace sc;
 namespace {
 
 constexpr char kMagic[8] = {'S', 'C', 'B', 'V', 'H', 'C', 'K', '1'};
-constexpr uint32_t kVersion = 2, kOrder = 0x01020304u;
+constexpr uint32_t kVersion = 3, kOrder = 0x01020304u;
 
 struct Writer {
   std::vector<uint8_t> buf;
@@ -76,14 +76,14 @@ uint64_t fnv1a(const uint8_t* p, size_t n) {
 void put_opts(Writer& w, const sc_build_opts& o) {
   w.val(o.max_leaf); w.val(o.bins); w.val(o.L); w.val(o.lut_size); w.val(o.chunk_bits);
   w.val(o.eps_rel); w.val(o.threads); w.val(o.skip_bits); w.val(o.test_stride);
-  w.val(o.leaf_min_tris); w.val(o.gpu_masks);
+  w.val(o.leaf_min_tris); w.val(o.gpu_masks); w.val(o.gpu_bvh);
 }
 
 void get_opts(Reader& r, sc_build_opts& o) {
   o.max_leaf = r.val<int>(); o.bins = r.val<int>(); o.L = r.val<int>();
   o.lut_size = r.val<int>(); o.chunk_bits = r.val<int>(); o.eps_rel = r.val<double>();
   o.threads = r.val<int>(); o.skip_bits = r.val<int>(); o.test_stride = r.val<int>();
-  o.leaf_min_tris = r.val<int>(); o.gpu_masks = r.val<int>();
+  o.leaf_min_tris = r.val<int>(); o.gpu_masks = r.val<int>(); o.gpu_bvh = r.val<int>();
 }
 
 // The tree must be one a build could have made: pre-order node numbering

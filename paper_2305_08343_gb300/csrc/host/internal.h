@@ -68,6 +68,8 @@ struct Bvh {
 
 void build_bvh(Bvh& b, const float* tris, int64_t n, int max_leaf, int bins,
                int threads);
+// The same tree built on the current GPU (bins <= 32).
+void build_bvh_gpu(Bvh& b, const float* tris, int64_t n, int max_leaf, int bins);
 void build_masks(Bvh& b, int R, int L, double eps, int threads);
 // The same masks built on the current GPU (bit-identical).
 void build_masks_gpu(Bvh& b, int R, int L, double eps);

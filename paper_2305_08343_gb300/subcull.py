@@ -48,7 +48,7 @@ class sc_build_opts(C.Structure):
     _fields_ = [("max_leaf", C.c_int), ("bins", C.c_int), ("L", C.c_int),
                 ("lut_size", C.c_int), ("chunk_bits", C.c_int), ("eps_rel", C.c_double),
                 ("threads", C.c_int), ("skip_bits", C.c_int), ("test_stride", C.c_int),
-                ("leaf_min_tris", C.c_int), ("gpu_masks", C.c_int)]
+                ("leaf_min_tris", C.c_int), ("gpu_masks", C.c_int), ("gpu_bvh", C.c_int)]
 
 
 class sc_bvh_info(C.Structure):

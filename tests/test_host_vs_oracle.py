@@ -115,6 +115,9 @@ def test_errors_are_reported_not_raised_through_the_abi():
     assert e.value.code == -1
     with pytest.raises(sc.SubcullError):
         sc.sc_bvh_build(tris, 0, 1)  # compression without masks
+    with pytest.raises(sc.SubcullError) as e:  # rejected before any device call
+        sc.sc_bvh_build(tris, 0, 0, gpu_bvh=1, bins=64)
+    assert e.value.code == -6 and "32 bins" in str(e.value)
     b = sc.sc_bvh_build(tris, 0, 0)
     with pytest.raises(sc.SubcullError) as e:
         sc.sc_bvh_device_bytes(b, sc.SC_LAYOUT_MASKED)
