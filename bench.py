@@ -633,7 +633,7 @@ def run_gpu(args):
         node_bytes = 176 + (0 if comp else 4 * mstride)
         visits = cnt_c[0] / mean_wide_children(bvh)
     else:
-        node_bytes = (96 if args.layout == 1 else 64) + (0 if comp else 2 * mstride)
+        node_bytes = (96 if args.layout in (1, 5) else 64) + (0 if comp else 2 * mstride)
         visits = cnt_c[0] / 2.0
     spawned = float(np.sum(sizes[1:])) / rays_per_step
     b_ray = (32 + 16 + 4 + visits * node_bytes + cnt_c[1] * 48 + spawned * (32 + 4))
@@ -729,9 +729,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hair1m", choices=sorted(WORKLOADS))
-    ap.add_argument("--lut", type=int, default=0, help="0 auto, 1 global table, 2 shared")
+    ap.add_argument("--lut", type=int, default=0,
+                    help="0 auto, 1 global table, 2 shared, 3 bit table, 4 the R_ray = 2R table")
     ap.add_argument("--layout", type=int, default=1,
-                    help="1 masked (Alg. 1 scales stored per child), 2 compact (scales divided)")
+                    help="1 masked (Alg. 1 scales stored per child), 2 compact (scales "
+                         "divided), 5 masked plus the R_ray = 2R table")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--refill", type=int, default=0, help="idle lanes before a warp refills")
     ap.add_argument("--no-cpu-baseline", action="store_true")

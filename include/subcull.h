@@ -173,6 +173,14 @@ sc_status sc_bvh_load(const char* path, sc_bvh** out);
    sweep tables of each pair of axes (Helly's theorem on intervals of t). */
 sc_status sc_raylut(int R, uint32_t* lut);
 
+/* The ray-mask table at R_ray = 2R (Sec. 4.2), R in {2, 3, 4, 6}:
+   uint32[(2R)^6][W] (W = words of an R^3-bit mask), row beg*(2R)^3 + end
+   with beg, end cells x + 2R*y + 4R^2*z of the 2R grid; mask cell v is set
+   iff the sweep test on the 2R grid sets one of v's eight sub-cells (each
+   2R cell lies in one mask cell).  The caller owns lut; SC_ERR_ARG for
+   another R or a NULL lut. */
+sc_status sc_raylut2r(int R, uint32_t* lut);
+
 /* ------------------------------------------------------ device image --- */
 enum {
   SC_LAYOUT_PLAIN = 0,         /* 64-B nodes without masks (unculled baseline) */
@@ -197,9 +205,18 @@ enum {
                                   compressed, 176 + 4 mask strides else.
                                   Children are visited by entry distance,
                                   ties by position. */
-  SC_LAYOUT_MASKED_COMPACT = 2 /* masks (or LUT indices) only; the scales are
+  SC_LAYOUT_MASKED_COMPACT = 2, /* masks (or LUT indices) only; the scales are
                                   divided on the fly: 64 B compressed,
                                   64+2*mask bytes uncompressed               */
+  SC_LAYOUT_MASKED_RAY2R = 5   /* SC_LAYOUT_MASKED plus the ray-mask table at
+                                  R_ray = 2R (Sec. 4.2): begin and end cells
+                                  on the 2R grid (twice the R-grid coordinate,
+                                  rounded down), one R^3-bit row per pair, a
+                                  mask cell set iff the sweep test on the 2R
+                                  grid sets one of its eight sub-cells;
+                                  (2R)^6 rows: 2 MB at R = 4, 96 MB at R = 6.
+                                  Uncompressed masks, R = 4 or 6 only
+                                  (SC_ERR_UNSUPPORTED otherwise).           */
 };
 
 /* Bytes of the device image of `b` in `layout` (a multiple of 256). */
@@ -227,7 +244,8 @@ typedef struct {
 
 enum { SC_CLOSEST = 0, SC_ANY = 1 };
 
-enum { SC_LUT_AUTO = 0, SC_LUT_GLOBAL = 1, SC_LUT_SHARED = 2, SC_LUT_BITTABLE = 3 };
+enum { SC_LUT_AUTO = 0, SC_LUT_GLOBAL = 1, SC_LUT_SHARED = 2, SC_LUT_BITTABLE = 3,
+       SC_LUT_RAY2R = 4 };
 
 typedef struct {
   int block;         /* threads per block: 0 (= 128) or 128               */
@@ -238,8 +256,11 @@ typedef struct {
                         per-axis-pair tables, single-batch traces only);
                         SC_LUT_BITTABLE (compressed images) = the
                         precomputed bit table of Sec. 3.2.2, one bit per
-                        (ray mask, LUT entry); SC_LUT_AUTO = bit table when
-                        compressed, else the full table                    */
+                        (ray mask, LUT entry); SC_LUT_RAY2R (images in
+                        SC_LAYOUT_MASKED_RAY2R) = the R_ray = 2R table;
+                        SC_LUT_AUTO = the 2R table when the image holds it,
+                        else the bit table when compressed, else the full
+                        table                                             */
   int refill;        /* a warp fetches new rays once this many of its lanes
                         are idle (1..32), 0 = default                     */
   int stack;         /* waves: traversal stack entries, 32 or 64 (0 = 64)  */

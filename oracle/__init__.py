@@ -61,6 +61,9 @@ def lib():
             "or_mask_words": (C.c_int, [C.c_int]),
             "or_raylut_cell": (C.c_int, [C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_int)]),
             "or_raylut": (None, [C.c_int, _P(u32)]),
+            "or_raylut2r_rows": (None, [C.c_int, i64, i64, _P(u32)]),
+            "or_cell2_t": (C.c_int, [f, f, f, f, f, C.c_int]),
+            "or_bvh_set_raylut2r": (None, [vp, _P(u32)]),
             "or_tri_box": (C.c_int, [_P(d), _P(d), _P(d)]),
             "or_voxelize": (None, [_P(f), _P(f), _P(f), C.c_int, d, _P(u32)]),
             "or_fill": (None, [_P(u32), _P(f), _P(f), _P(u32), _P(f), _P(f), C.c_int, d]),
@@ -137,6 +140,27 @@ def raylut(R: int) -> np.ndarray:
     R3 = R ** 3
     out = np.zeros((R3 * R3, mask_words(R)), dtype=np.uint32)
     lib().or_raylut(R, _ptr(out, C.c_uint32))
+    return out
+
+
+_LUT2R = {}
+
+
+def raylut2r(R: int, threads: int = 0) -> np.ndarray:
+    """Ray-mask table at R_ray = 2R (Sec. 4.2), uint32[(2R)^6, W]: row
+    beg * (2R)^3 + end, beg and end cells of the 2R grid, each row an
+    R^3-bit mask.  Rows are split across threads; the table is kept per R."""
+    if R in _LUT2R:
+        return _LUT2R[R]
+    from concurrent.futures import ThreadPoolExecutor
+    rows = (2 * R) ** 6
+    out = np.zeros((rows, mask_words(R)), dtype=np.uint32)
+    nt = threads or (os.cpu_count() or 1)
+    cuts = np.linspace(0, rows, nt + 1).astype(np.int64)
+    with ThreadPoolExecutor(nt) as ex:
+        list(ex.map(lambda i: lib().or_raylut2r_rows(R, int(cuts[i]), int(cuts[i + 1]),
+                                                     _ptr(out, C.c_uint32)), range(nt)))
+    _LUT2R[R] = out
     return out
 
 
@@ -362,6 +386,19 @@ def _wide(self):
     return dict(n=n[:k], parent=p[:k], child=c[:k], next=nx[:k])
 
 
+def _set_ray2r(self, on: bool = True):
+    """Culling tests look up the R_ray = 2R table (Sec. 4.2) instead of the
+    R table."""
+    if on:
+        self._lut2r = raylut2r(self.R)
+        lib().or_bvh_set_raylut2r(self._h, _ptr(self._lut2r, C.c_uint32))
+    else:
+        lib().or_bvh_set_raylut2r(self._h, None)
+        self._lut2r = None
+    return self
+
+
+OracleBVH.set_ray2r = _set_ray2r
 OracleBVH.wide = _wide
 OracleBVH.set_ideal = _set_ideal
 OracleBVH.frontier = _frontier
@@ -408,6 +445,11 @@ def cell(p: float, lo: float, hi: float, R: int) -> int:
 
 def cell_t(t: float, o: float, d: float, lo: float, hi: float, R: int) -> int:
     return int(lib().or_cell_t(float(t), float(o), float(d), float(lo), float(hi), R))
+
+
+def cell2_t(t: float, o: float, d: float, lo: float, hi: float, R: int) -> int:
+    """Cell on the 2R grid (R_ray = 2R) of the point at parameter t."""
+    return int(lib().or_cell2_t(float(t), float(o), float(d), float(lo), float(hi), R))
 
 
 # -------------------------------------------------------------- bounce rays --

@@ -88,6 +88,40 @@ void or_raylut(int R, uint32_t* lut) {
     }
 }
 
+/*
+ * Ray-mask table at the finer resolution R_ray = 2R (Sec. 4.2).  The begin
+ * and end positions are discretised on the 2R grid; each 2R cell lies in
+ * exactly one mask cell (the one holding its 2x2x2 block), so the row of
+ * (beg, end) sets mask cell v iff the sweep test above, run on the 2R grid,
+ * sets one of v's eight sub-cells.  Rows are indexed beg * (2R)^3 + end with
+ * beg = x + 2R y + 4R^2 z; each row is an R^3-bit mask of W words.  Only
+ * sub-cells within one of the segment's bounding box on every axis can pass
+ * (|b_k + t (e_k - b_k) - v_k| < 1 keeps v_k strictly between min - 1 and
+ * max + 1), so the scan stops there.  Rows [row_begin, row_end) are filled,
+ * so that callers can split the table across threads.
+ */
+void or_raylut2r_rows(int R, int64_t row_begin, int64_t row_end, uint32_t* lut) {
+  const int R2 = 2 * R, R23 = R2 * R2 * R2, W = or_mask_words(R);
+  for (int64_t row = row_begin; row < row_end; ++row) {
+    const int beg = (int)(row / R23), end = (int)(row % R23);
+    const int b[3] = {beg % R2, (beg / R2) % R2, beg / (R2 * R2)};
+    const int e[3] = {end % R2, (end / R2) % R2, end / (R2 * R2)};
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = (b[k] < e[k] ? b[k] : e[k]);
+      hi[k] = (b[k] > e[k] ? b[k] : e[k]);
+    }
+    uint32_t* m = lut + (size_t)row * W;
+    memset(m, 0, sizeof(uint32_t) * (size_t)W);
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          const int v[3] = {x, y, z};
+          if (or_raylut_cell(R2, b, e, v)) bit_set(m, cell_bit(R, x / 2, y / 2, z / 2));
+        }
+  }
+}
+
 /* ----------------------------- conservative voxelization (Sec. 3.1.1) --- */
 /*
  * Triangle-box overlap by the separating axis theorem (Akenine-Moeller,
@@ -433,6 +467,7 @@ struct OrBvh {
   uint8_t* cidx;   /* [nn][2] */
   uint32_t* raylut;
   int ideal; /* 1: culling tests use the exact ray mask (ideal_ray_mask) */
+  const uint32_t* raylut2r; /* R_ray = 2R table (caller-owned), or NULL */
   /* 4-wide view (or_bvh_wide): per 4-wide node its child slots as (binary
      parent node, child index), and the 4-wide node of each inner child */
   int64_t nn4;
@@ -627,6 +662,8 @@ OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins) {
 }
 
 void or_bvh_set_ideal(OrBvh* b, int ideal) { b->ideal = ideal; }
+
+void or_bvh_set_raylut2r(OrBvh* b, const uint32_t* lut2r) { b->raylut2r = lut2r; }
 
 void or_bvh_free(OrBvh* b) {
   if (!b) return;
@@ -964,12 +1001,40 @@ static void ideal_ray_mask(const ORay* r, const float* bx, float tn, float tf, i
       }
 }
 
+/* Cell of the point at parameter t on the 2R grid (R_ray = 2R): twice the
+   R-grid coordinate q of or_cell_t (doubling is exact), clamped to
+   [0, 2R-1]. */
+int or_cell2_t(float t, float o, float d, float lo, float hi, int R) {
+  float ext = hi - lo;
+  float s = (float)R / fmaxf(ext, 1e-30f);
+  float q = 2.0f * fmaf(t, d * s, (o - lo) * s);
+  q = fminf(fmaxf(q, -1.0f), (float)(2 * R));
+  int i = (int)floorf(q);
+  if (i < 0) i = 0;
+  if (i > 2 * R - 1) i = 2 * R - 1;
+  return i;
+}
+
 static int cull_pass(const OrBvh* b, const ORay* r, const float* bx, float tn,
                      float tf, const uint32_t* objmask) {
   int R = b->R, W = b->W, R3 = R * R * R;
   if (b->ideal) {
     uint32_t rm[16];
     ideal_ray_mask(r, bx, tn, tf, R, rm);
+    for (int w = 0; w < W; ++w)
+      if (rm[w] & objmask[w]) return 1;
+    return 0;
+  }
+  if (b->raylut2r) {
+    const int R2 = 2 * R, R23 = R2 * R2 * R2;
+    int b2[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+      b2[k] = or_cell2_t(tn, r->o[k], r->d[k], bx[k], bx[3 + k], R);
+      e2[k] = or_cell2_t(tf, r->o[k], r->d[k], bx[k], bx[3 + k], R);
+    }
+    const int beg = b2[0] + R2 * b2[1] + R2 * R2 * b2[2];
+    const int end = e2[0] + R2 * e2[1] + R2 * R2 * e2[2];
+    const uint32_t* rm = b->raylut2r + ((size_t)beg * R23 + end) * W;
     for (int w = 0; w < W; ++w)
       if (rm[w] & objmask[w]) return 1;
     return 0;

@@ -33,6 +33,9 @@ int or_mask_words(int R);
    cell v is met by the sweep of cell beg towards cell end. */
 int or_raylut_cell(int R, const int* b, const int* e, const int* v);
 void or_raylut(int R, uint32_t* lut /* [R^3 * R^3][W] */);
+/* R_ray = 2R table (Sec. 4.2): rows [row_begin, row_end) of [(2R)^6][W]. */
+void or_raylut2r_rows(int R, int64_t row_begin, int64_t row_end, uint32_t* lut);
+int or_cell2_t(float t, float o, float d, float lo, float hi, int R);
 
 /* Conservative voxelization (Sec. 3.1.1): triangle-box overlap by the
    separating axis theorem, in double. */
@@ -61,6 +64,8 @@ void or_bvh_free(OrBvh* b);
    cells the clipped segment meets, found in double) instead of the
    lookup table -- the paper's "ideal culling" reference of Sec. 4.1. */
 void or_bvh_set_ideal(OrBvh* b, int ideal);
+/* Culling tests look up the R_ray = 2R table (caller-owned; NULL: off). */
+void or_bvh_set_raylut2r(OrBvh* b, const uint32_t* lut2r);
 int64_t or_bvh_num_nodes(const OrBvh* b);
 int or_bvh_max_depth(const OrBvh* b);
 void or_bvh_root(const OrBvh* b, int32_t* child, int32_t* count, float* box6);

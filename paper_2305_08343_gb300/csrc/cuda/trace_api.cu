@@ -68,16 +68,20 @@ DevInfo device_info() {
 
 // Ray-mask lookup variant: 0 full table (global), 1 shared memory (the full
 // table at R = 4, the factored tables otherwise), 2 bit table (compressed
-// images only).  AUTO: the bit table when compressed, else the full table
-// (shared-memory tables take the L1 capacity the node fetches need).
+// images only), 4 the R_ray = 2R table (images that hold it).  AUTO: the 2R
+// table when present, else the bit table when compressed, else the full
+// table (shared-memory tables take the L1 capacity the node fetches need).
 int lut_variant(const sc_dbvh* d, int lut_mode) {
   switch (lut_mode) {
-    case SC_LUT_AUTO: return d->lay.compress ? 2 : 0;
+    case SC_LUT_AUTO: return d->lay.ray2r ? 4 : (d->lay.compress ? 2 : 0);
     case SC_LUT_GLOBAL: return 0;
     case SC_LUT_SHARED: return 1;
     case SC_LUT_BITTABLE:
       if (!d->lay.compress) fail(SC_ERR_ARG, "the bit table needs a compressed image");
       return 2;
+    case SC_LUT_RAY2R:
+      if (!d->lay.ray2r) fail(SC_ERR_ARG, "the R_ray = 2R table needs an SC_LAYOUT_MASKED_RAY2R image");
+      return 4;
   }
   fail(SC_ERR_ARG, "bad lut_mode %d", lut_mode);
 }
@@ -149,6 +153,7 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
   p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
   p.bits = d->lay.compress ? reinterpret_cast<const uint32_t*>(base + d->lay.off_bits) : nullptr;
+  p.lut2 = d->lay.ray2r ? reinterpret_cast<const uint4*>(base + d->lay.off_lut2) : nullptr;
   p.rays = reinterpret_cast<const float4*>(d_rays);
   p.hits = reinterpret_cast<float4*>(d_hits);
   p.counts = reinterpret_cast<uint2*>(d_counts);
@@ -191,6 +196,7 @@ void fill_params(const sc_dbvh* d, sct::Params& p) {
   p.pair = d->lay.R ? reinterpret_cast<const uint2*>(base + d->lay.off_pair) : nullptr;
   p.clut = d->lay.compress ? reinterpret_cast<const uint4*>(base + d->lay.off_clut) : nullptr;
   p.bits = d->lay.compress ? reinterpret_cast<const uint32_t*>(base + d->lay.off_bits) : nullptr;
+  p.lut2 = d->lay.ray2r ? reinterpret_cast<const uint4*>(base + d->lay.off_lut2) : nullptr;
   p.num_nodes = d->nn;
   p.num_tris = d->ntri;
   p.root_slot = d->root_slot;

@@ -49,6 +49,7 @@ struct Params {
   const uint2* pair;        // factored 2-D table, R^4 x 64 bits
   const uint4* clut;        // compression LUT
   const uint32_t* bits;     // compressed: [R^6][8] words, bit j of row = ray mask AND LUT entry j
+  const uint4* lut2;        // R_ray = 2R table ((2R)^6 rows, mask-stride bytes), or nullptr
   const float4* rays;       // 2 float4 per ray
   float4* hits;             // {t, id bits, u, v}
   uint2* counts;            // or nullptr
@@ -306,6 +307,23 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
   constexpr int R3 = R * R * R;
   constexpr int MB = MaskTraits<R>::kStrideBytes;
   int cb[3], ce[3];
+  if constexpr (LUTV == 4) {
+    // R_ray = 2R (Sec. 4.2): cells of the 2R grid, twice the R-grid
+    // coordinate (doubling is exact), one row per (begin, end) pair
+    constexpr int R2 = 2 * R;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
+      const float b = __fmul_rn(d[k], sk[k]);
+      cb[k] = cell_of_q<R2>(__fmul_rn(2.0f, __fmaf_rn(tn, b, a)));
+      ce[k] = cell_of_q<R2>(__fmul_rn(2.0f, __fmaf_rn(tf, b, a)));
+    }
+    const int beg2 = cb[0] + R2 * cb[1] + R2 * R2 * cb[2];
+    const int end2 = ce[0] + R2 * ce[1] + R2 * R2 * ce[2];
+    const uint8_t* rm =
+        reinterpret_cast<const uint8_t*>(p.lut2) + ((size_t)beg2 * (R2 * R2 * R2) + end2) * MB;
+    return masks_overlap<R>(rm, obj);
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
@@ -656,7 +674,8 @@ __device__ __forceinline__ long long warp_fetch(bool active, unsigned* counter, 
 // 1 any.  LUTV: 0 full table in global memory (one entry per lookup through
 // L1/L2), 1 factored tables in shared memory, 2 (compressed only) the
 // precomputed bit table of Sec. 3.2.2 (one bit per ray mask and LUT entry),
-// 3 (R = 4 only) the full table and the LUT in shared memory.
+// 3 (R = 4 only) the full table and the LUT in shared memory, 4
+// (uncompressed, R = 4 or 6) the R_ray = 2R table in global memory.
 // SCALES: 1 = the per-child Alg. 1 scales R/extent are precomputed in the
 // node record, 0 = divided.
 template <int R, int CULL, int MODE, int LUTV, int SCALES, int WIDTH = 2>

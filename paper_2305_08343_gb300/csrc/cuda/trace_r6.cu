@@ -1,7 +1,8 @@
 // trace_r6.cu — culled traversal variants for R = 6 (object masks of
 // 6^3 bits): {uncompressed, compressed} x {closest, any} x {global table,
 // shared-memory factored table, bit table (compressed)} x {scales divided,
-// scales stored}; and the wave pipeline kernels.
+// scales stored}, the R_ray = 2R table (uncompressed, scales stored); and
+// the wave pipeline kernels.
 #include "trace_kernel.cuh"
 
 namespace sct {
@@ -13,12 +14,14 @@ KernelFn get_kernel_r6(int cull, int mode, int lutv, int scales) {
   static const KernelFn comp[2][3][2] = {
       {SCT_V(2, 0, 0), SCT_V(2, 0, 1), SCT_V(2, 0, 2)},
       {SCT_V(2, 1, 0), SCT_V(2, 1, 1), SCT_V(2, 1, 2)}};
+  if (cull == 1 && lutv == 4) return mode ? trace_kernel<6, 1, 1, 4, 1> : trace_kernel<6, 1, 0, 4, 1>;
   if (cull == 1) return unc[mode][lutv == 1 ? 1 : 0][scales];
   return comp[mode][lutv][scales];
 }
 #undef SCT_V
 
 WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack) {
+  if (cull == 1 && lutv == 4) return WaveVariants<6, 1, 4, 1>::get(block, stack);
   if (cull == 1)
     return scales ? WaveVariants<6, 1, 0, 1>::get(block, stack)
                   : WaveVariants<6, 1, 0, 0>::get(block, stack);
@@ -30,6 +33,7 @@ WaveKernelFn get_waves_r6(int cull, int lutv, int scales, int block, int stack) 
 }
 
 SeededKernelFn get_seeded_r6(int cull, int lutv, int scales) {
+  if (cull == 1 && lutv == 4) return seeded_kernel<6, 1, 4, 1>;
   if (cull == 1) return scales ? seeded_kernel<6, 1, 0, 1> : seeded_kernel<6, 1, 0, 0>;
   if (lutv == 2) return scales ? seeded_kernel<6, 2, 2, 1> : seeded_kernel<6, 2, 2, 0>;
   return scales ? seeded_kernel<6, 2, 0, 1> : seeded_kernel<6, 2, 0, 0>;

@@ -281,6 +281,15 @@ sc_status sc_raylut(int R, uint32_t* lut) {
   SC_CATCH
 }
 
+sc_status sc_raylut2r(int R, uint32_t* lut) {
+  SC_TRY
+  if (!(R == 2 || R == 3 || R == 4 || R == 6) || !lut)
+    fail(SC_ERR_ARG, "sc_raylut2r: R must be 2, 3, 4 or 6 and lut non-NULL");
+  raylut2r_full(R, lut);
+  return SC_OK;
+  SC_CATCH
+}
+
 sc_status sc_bvh_device_bytes(const sc_bvh* h, int layout, size_t* nbytes) {
   SC_TRY
   if (!h || !nbytes) fail(SC_ERR_ARG, "sc_bvh_device_bytes: NULL argument");

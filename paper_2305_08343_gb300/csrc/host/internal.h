@@ -80,6 +80,9 @@ double scene_eps(const float* tris, int64_t n, double eps_rel);
 // index ((ba*R + bb)*R + ea)*R + eb, bit va + R*vb.  full: [R^6][W].
 void raylut_pair2d(int R, std::vector<uint64_t>& out);
 void raylut_full(int R, uint32_t* out);
+// The R_ray = 2R table (Sec. 4.2): [(2R)^6][W], row beg*(2R)^3 + end over
+// cells of the 2R grid, each row an R^3-bit mask.
+void raylut2r_full(int R, uint32_t* out);
 
 // ---------------------------------------------------------- device image --
 // Node record (child pair), 16-byte aligned, fetched as float4s:
@@ -103,9 +106,11 @@ struct ImageLayout {
   int stack_need = 0;      // deepest possible traversal stack
   int R = 0, W = 0, mstride = 0, compress = 0, K = 0;
   int scales = 0;          // per-child Alg. 1 scales stored at +64
+  int ray2r = 0;           // the image also holds the R_ray = 2R table
   int mask_off = 64;       // first object mask inside a node record
   int node_bytes = 64;
   size_t off_nodes = 0, off_tris = 0, off_lut = 0, off_pair = 0, off_clut = 0, off_bits = 0;
+  size_t off_lut2 = 0;
   size_t total = 0;
 };
 ImageLayout image_layout(const Bvh& b, int layout);

@@ -12,6 +12,7 @@
 // v2 - v0}.  Every region starts on a 256-byte boundary.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -121,14 +122,20 @@ ImageLayout image_layout(const Bvh& b, int layout) {
     L.nodes = b.nn;
     L.stack_need = b.max_depth + 1;
   }
-  if (layout == SC_LAYOUT_MASKED || layout == SC_LAYOUT_MASKED_COMPACT) {
+  if (layout == SC_LAYOUT_MASKED || layout == SC_LAYOUT_MASKED_COMPACT ||
+      layout == SC_LAYOUT_MASKED_RAY2R) {
     if (b.R <= 0) fail(SC_ERR_STATE, "masked layout requested for a BVH built without masks");
+    if (layout == SC_LAYOUT_MASKED_RAY2R && (b.compress || b.R > 6))
+      fail(SC_ERR_UNSUPPORTED,
+           "the R_ray = 2R table needs uncompressed masks and R = 4 or 6 (R = %d%s)", b.R,
+           b.compress ? ", compressed" : "");
     L.R = b.R;
     L.W = mask_words(b.R);
     L.mstride = mask_stride(b.R);
     L.compress = b.compress;
     L.K = b.K;
-    L.scales = layout == SC_LAYOUT_MASKED ? 1 : 0;
+    L.scales = layout == SC_LAYOUT_MASKED_COMPACT ? 0 : 1;
+    L.ray2r = layout == SC_LAYOUT_MASKED_RAY2R ? 1 : 0;
     L.mask_off = L.scales ? 96 : 64;
     L.node_bytes = b.compress ? L.mask_off : L.mask_off + 2 * L.mstride;
   } else if (layout != SC_LAYOUT_PLAIN && layout != SC_LAYOUT_PLAIN4 &&
@@ -152,10 +159,32 @@ ImageLayout image_layout(const Bvh& b, int layout) {
       L.off_bits = off;
       off = align256(off + R3 * R3 * 32);
     }
+    if (L.ray2r) {
+      const size_t R23 = (size_t)8 * R3;
+      L.off_lut2 = off;
+      off = align256(off + R23 * R23 * L.mstride);
+    }
   }
   L.total = off;
   return L;
 }
+
+namespace {
+// The R_ray = 2R table depends on R alone (about a second to build at R = 6):
+// built once per R and kept.
+const std::vector<uint32_t>& raylut2r_cached(int R) {
+  static std::mutex mu;
+  static std::vector<uint32_t> tables[9];
+  std::lock_guard<std::mutex> lock(mu);
+  std::vector<uint32_t>& t = tables[R];
+  if (t.empty()) {
+    const size_t R23 = (size_t)8 * R * R * R;
+    t.assign(R23 * R23 * mask_words(R), 0u);
+    raylut2r_full(R, t.data());
+  }
+  return t;
+}
+}  // namespace
 
 void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
   img.assign(L.total, 0);
@@ -271,6 +300,13 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
     std::vector<uint64_t> P;
     raylut_pair2d(R, P);
     std::memcpy(base + L.off_pair, P.data(), 8 * P.size());
+    if (L.ray2r) {
+      const std::vector<uint32_t>& t2 = raylut2r_cached(R);
+      const int64_t rows = (int64_t)(t2.size() / L.W);
+      parallel_for(rows, resolve_threads(0), 65536, [&](int64_t e) {
+        std::memcpy(base + L.off_lut2 + (size_t)e * L.mstride, &t2[(size_t)e * L.W], 4 * L.W);
+      });
+    }
     if (L.compress) {
       for (int j = 0; j < b.K; ++j)
         std::memcpy(base + L.off_clut + (size_t)j * L.mstride, &b.clut[(size_t)j * L.W], 4 * L.W);

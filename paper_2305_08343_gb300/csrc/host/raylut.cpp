@@ -72,4 +72,65 @@ void raylut_full(int R, uint32_t* out) {
   }
 }
 
+// The table at R_ray = 2R (Sec. 4.2): begin and end cells on the 2R grid
+// (x + 2R y + 4R^2 z), one R^3-bit row per pair, a mask cell set iff the
+// sweep on the 2R grid sets one of its eight sub-cells.  Same construction as
+// raylut_full one level finer: per axis pair a 2-D table of 2R rows of 2R
+// bits (exact scan of t), the Helly product row by row, and each 2R row
+// folded to R bits (bit i kept iff sub-bit 2i or 2i+1 is set).
+void raylut2r_full(int R, uint32_t* out) {
+  const int R2 = 2 * R, W = mask_words(R);
+  if (R2 > 16) fail(SC_ERR_UNSUPPORTED, "R_ray = 2R table for R = %d", R);
+  const int64_t R23 = (int64_t)R2 * R2 * R2;
+  const long M = 2L * (R2 - 1) * (R2 - 1) + 1;
+  // Q[((ba*R2 + bb)*R2 + ea)*R2 + eb][vb]: bits va
+  std::vector<uint16_t> Q((size_t)R2 * R2 * R2 * R2 * R2, 0);
+  parallel_for((int64_t)R2 * R2, resolve_threads(0), 1, [&](int64_t ab) {
+    const int ba = (int)(ab / R2), bb = (int)(ab % R2);
+    for (int ea = 0; ea < R2; ++ea)
+      for (int eb = 0; eb < R2; ++eb) {
+        uint16_t* q = &Q[((((size_t)ba * R2 + bb) * R2 + ea) * R2 + eb) * R2];
+        for (int vb = 0; vb < R2; ++vb)
+          for (int va = 0; va < R2; ++va)
+            for (long k = 0; k <= M; ++k) {
+              const long qa = M * (ba - va) + k * (ea - ba);
+              const long qb = M * (bb - vb) + k * (eb - bb);
+              if (std::labs(qa) < M && std::labs(qb) < M) {
+                q[vb] |= (uint16_t)(1u << va);
+                break;
+              }
+            }
+      }
+  });
+  auto rows = [&](int ba, int bb, int ea, int eb) {
+    return &Q[((((size_t)ba * R2 + bb) * R2 + ea) * R2 + eb) * R2];
+  };
+  auto fold = [R](uint32_t x) {
+    uint32_t f = 0;
+    for (int i = 0; i < R; ++i)
+      if ((x >> (2 * i)) & 3u) f |= 1u << i;
+    return f;
+  };
+  parallel_for(R23 * R23, resolve_threads(0), 4096, [&](int64_t row) {
+    const int beg = (int)(row / R23), end = (int)(row % R23);
+    const int bx = beg % R2, by = (beg / R2) % R2, bz = beg / (R2 * R2);
+    const int ex = end % R2, ey = (end / R2) % R2, ez = end / (R2 * R2);
+    const uint16_t* xy = rows(bx, by, ex, ey);  // [y] -> x bits
+    const uint16_t* yz = rows(by, bz, ey, ez);  // [z] -> y bits
+    const uint16_t* xz = rows(bx, bz, ex, ez);  // [z] -> x bits
+    uint32_t* m = out + (size_t)row * W;
+    std::memset(m, 0, sizeof(uint32_t) * W);
+    for (int z = 0; z < R2; ++z)
+      for (int y = 0; y < R2; ++y) {
+        if (!((yz[z] >> y) & 1u)) continue;
+        const uint32_t xs = fold((uint32_t)(xy[y] & xz[z]));
+        for (int x = 0; x < R; ++x)
+          if ((xs >> x) & 1u) {
+            const int bit = x + R * (y / 2) + R * R * (z / 2);
+            m[bit >> 5] |= 1u << (bit & 31);
+          }
+      }
+  });
+}
+
 }  // namespace sc

@@ -22,8 +22,9 @@ SC_SCENE_HAIR, SC_SCENE_SOUP = 0, 1
 SC_RAYS_PINHOLE, SC_RAYS_RANDOM = 0, 1
 SC_LAYOUT_PLAIN, SC_LAYOUT_MASKED, SC_LAYOUT_MASKED_COMPACT = 0, 1, 2
 SC_LAYOUT_PLAIN4, SC_LAYOUT_MASKED4 = 3, 4
+SC_LAYOUT_MASKED_RAY2R = 5
 SC_CLOSEST, SC_ANY = 0, 1
-SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED, SC_LUT_BITTABLE = 0, 1, 2, 3
+SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED, SC_LUT_BITTABLE, SC_LUT_RAY2R = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "SC_OK", -1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_NOMEM",
                 -4: "SC_ERR_TIMEOUT", -5: "SC_ERR_STACK", -6: "SC_ERR_UNSUPPORTED",
                 -7: "SC_ERR_STATE", -8: "SC_ERR_IO"}
@@ -267,6 +268,13 @@ def sc_raylut(R: int) -> np.ndarray:
     R3 = R ** 3
     out = np.zeros((R3 * R3, (R3 + 31) // 32), np.uint32)
     _check(lib().sc_raylut(R, _ptr(out, C.c_uint32)))
+    return out
+
+
+def sc_raylut2r(R: int) -> np.ndarray:
+    R23 = (2 * R) ** 3
+    out = np.zeros((R23 * R23, (R ** 3 + 31) // 32), np.uint32)
+    _check(lib().sc_raylut2r(R, _ptr(out, C.c_uint32)))
     return out
 
 

@@ -63,6 +63,11 @@ def test_raylut_matches_oracle(R):
     assert np.array_equal(sc.sc_raylut(R), oracle.raylut(R))
 
 
+@pytest.mark.parametrize("R", [2, 3, 4, 6])
+def test_raylut2r_matches_oracle(R):
+    assert np.array_equal(sc.sc_raylut2r(R), oracle.raylut2r(R))
+
+
 def test_thread_count_does_not_change_the_build():
     tris = sg.hair(3000, 16, True, seed=6)
     a = sc.sc_bvh_build(tris, 6, 1, threads=1).export()
