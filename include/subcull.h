@@ -168,6 +168,26 @@ sc_status sc_bvh_export(const sc_bvh* b, int32_t* root2, int32_t* child,
 sc_status sc_bvh_save(const sc_bvh* b, const char* path);
 sc_status sc_bvh_load(const char* path, sc_bvh** out);
 
+/* Refit for moved triangles (dynamic scenes, whose mask updates the paper
+   leaves to future work).  tris: host float[n_tris][9], the new positions
+   of the same triangles in input order (n_tris must equal the build's).
+   The topology and triangle order are kept; triangles whose coordinates
+   changed (bit for bit) make every slot above them dirty; those slots'
+   boxes are refit bottom-up (unions of triangle boxes, as the build takes
+   them) and their object masks are computed again (on the GPU when the
+   build used gpu_masks), and compressed BVHs encode them again (Alg. 3)
+   against the LUT chosen at build time.  A change of the scene's dilation
+   eps makes every slot dirty.  The masks then equal a mask build from
+   scratch on the refit tree.  Device images are not touched: upload again.
+   info (may be NULL) receives the counts and timings.  SC_ERR_ARG for a
+   NULL bvh, another triangle count or a non-finite coordinate. */
+typedef struct {
+  int64_t moved_tris;   /* triangles whose coordinates changed            */
+  int64_t dirty_nodes;  /* nodes whose boxes / masks were computed again  */
+  double ms_boxes, ms_masks, ms_compress;
+} sc_refit_info;
+sc_status sc_bvh_refit(sc_bvh* b, const float* tris, int64_t n_tris, sc_refit_info* info);
+
 /* The ray-mask table (Sec. 3.1.1): uint32[R^3 * R^3][W], row
    beg*R^3 + end, cell index x + R*y + R*R*z.  Built here from the 2-D
    sweep tables of each pair of axes (Helly's theorem on intervals of t). */

@@ -64,6 +64,8 @@ def lib():
             "or_raylut2r_rows": (None, [C.c_int, i64, i64, _P(u32)]),
             "or_cell2_t": (C.c_int, [f, f, f, f, f, C.c_int]),
             "or_bvh_set_raylut2r": (None, [vp, _P(u32)]),
+            "or_bvh_refit": (C.c_int, [vp, _P(f)]),
+            "or_bvh_reencode": (C.c_int, [vp]),
             "or_tri_box": (C.c_int, [_P(d), _P(d), _P(d)]),
             "or_voxelize": (None, [_P(f), _P(f), _P(f), C.c_int, d, _P(u32)]),
             "or_fill": (None, [_P(u32), _P(f), _P(f), _P(u32), _P(f), _P(f), C.c_int, d]),
@@ -398,6 +400,27 @@ def _set_ray2r(self, on: bool = True):
     return self
 
 
+def _refit(self, tris):
+    """Moved triangles (same count, input order): slot boxes refit over the
+    same topology.  Masks are rebuilt by build_masks, compression indices
+    by reencode."""
+    t = _f32(tris).reshape(-1, 9)
+    if t.shape[0] != self.ntri:
+        raise ValueError("refit needs the same number of triangles")
+    self.tris = t
+    lib().or_bvh_refit(self._h, _ptr(self.tris, C.c_float))
+    return self
+
+
+def _reencode(self):
+    """Alg. 3 for every slot against the compression LUT already chosen."""
+    if lib().or_bvh_reencode(self._h) != 0:
+        raise ValueError("or_bvh_reencode needs masks and a compression LUT")
+    return self
+
+
+OracleBVH.refit = _refit
+OracleBVH.reencode = _reencode
 OracleBVH.set_ray2r = _set_ray2r
 OracleBVH.wide = _wide
 OracleBVH.set_ideal = _set_ideal

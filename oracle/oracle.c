@@ -663,6 +663,55 @@ OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins) {
 
 void or_bvh_set_ideal(OrBvh* b, int ideal) { b->ideal = ideal; }
 
+/* Refit for moved triangles (dynamic scenes, which the paper leaves to
+   future work): the tree's topology and triangle order stay; every child
+   slot's box becomes the union of the boxes of the triangles below it, each
+   triangle's box taken from `tris` (new positions, input order) exactly as
+   the build takes it.  Object masks and compression indices are then
+   recomputed by the caller (or_bvh_masks, or_bvh_reencode). */
+static void refit_slot(OrBvh* b, const float* tris, int32_t child, int32_t count,
+                       float* box) {
+  box_empty(box);
+  if (count > 0) {
+    for (int32_t i = 0; i < count; ++i) {
+      const float* t = tris + 9 * (size_t)b->perm[child + i];
+      float lo[3], hi[3];
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(fminf(t[k], t[3 + k]), t[6 + k]);
+        hi[k] = fmaxf(fmaxf(t[k], t[3 + k]), t[6 + k]);
+      }
+      box_grow(box, lo, hi);
+    }
+    return;
+  }
+  for (int c = 0; c < 2; ++c) {
+    float* cb = b->box + 12 * (size_t)child + 6 * c;
+    refit_slot(b, tris, b->child[2 * (size_t)child + c], b->count[2 * (size_t)child + c], cb);
+    box_grow(box, cb, cb + 3);
+  }
+}
+
+int or_bvh_refit(OrBvh* b, const float* tris) {
+  if (b->ntri == 0) return 0;
+  refit_slot(b, tris, b->root_child, b->root_count, b->root_box);
+  return 0;
+}
+
+/* Alg. 3 again for every slot against the LUT already chosen (after the
+   masks changed); the LUT itself is kept. */
+int or_bvh_reencode(OrBvh* b) {
+  if (!b->clut || !b->masks) return -1;
+  int W = b->W, R = b->R;
+  int64_t ns = b->nnodes * 2;
+  int nchunk = (R * R * R + b->bits - 1) / b->bits;
+  uint32_t* req = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nchunk * (1u << b->bits) * 8);
+  or_req_luts(b->clut, b->K, R, b->bits, req);
+  for (int64_t s = 0; s < ns; ++s)
+    b->cidx[s] = (uint8_t)or_encode(b->masks + (size_t)s * W, req, R, b->bits);
+  free(req);
+  return 0;
+}
+
 void or_bvh_set_raylut2r(OrBvh* b, const uint32_t* lut2r) { b->raylut2r = lut2r; }
 
 void or_bvh_free(OrBvh* b) {

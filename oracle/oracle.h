@@ -64,6 +64,10 @@ void or_bvh_free(OrBvh* b);
    cells the clipped segment meets, found in double) instead of the
    lookup table -- the paper's "ideal culling" reference of Sec. 4.1. */
 void or_bvh_set_ideal(OrBvh* b, int ideal);
+/* Refit: slot boxes from moved triangles, topology kept (masks: or_bvh_masks). */
+int or_bvh_refit(OrBvh* b, const float* tris);
+/* Alg. 3 for every slot against the existing compression LUT. */
+int or_bvh_reencode(OrBvh* b);
 /* Culling tests look up the R_ray = 2R table (caller-owned; NULL: off). */
 void or_bvh_set_raylut2r(OrBvh* b, const uint32_t* lut2r);
 int64_t or_bvh_num_nodes(const OrBvh* b);

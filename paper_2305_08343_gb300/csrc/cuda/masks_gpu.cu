@@ -157,22 +157,19 @@ T* upload(DevBufs& d, const std::vector<T>& v, cudaStream_t st) {
 
 }  // namespace
 
-void build_masks_gpu(Bvh& b, int R, int L, double eps) {
-  const double t0 = now_ms();
-  b.R = R;
-  b.L = L;
-  b.W = mask_words(R);
-  b.eps = eps;
-  b.masks.assign((size_t)b.nn * 2 * b.W, 0u);
-  if (b.nn == 0) {
-    b.ms_masks = now_ms() - t0;
-    return;
-  }
+namespace {
+
+// The masks of every node (node_dirty NULL: b.masks starts at zero) or of
+// the marked nodes only (the other masks are uploaded and kept), level by
+// level from the deepest.  Uses b.R, b.L, b.W, b.eps.
+void masks_gpu_levels(Bvh& b, const std::vector<uint8_t>* node_dirty) {
+  const int L = b.L;
   if (std::min(L, b.max_depth + 1) > mm::kMaxL)
     fail(SC_ERR_UNSUPPORTED, "mask depth L = %d over a tree %d deep exceeds %d", L,
          b.max_depth, mm::kMaxL);
   std::vector<std::vector<int64_t>> levels(b.max_depth + 1);
-  for (int64_t n = 0; n < b.nn; ++n) levels[b.ndepth[n]].push_back(n);
+  for (int64_t n = 0; n < b.nn; ++n)
+    if (!node_dirty || (*node_dirty)[n]) levels[b.ndepth[n]].push_back(n);
   std::vector<int64_t> order;
   std::vector<size_t> start(b.max_depth + 2, 0);
   for (int d = 0; d <= b.max_depth; ++d) {
@@ -193,12 +190,16 @@ void build_masks_gpu(Bvh& b, int R, int L, double eps) {
   in.child = upload(d, b.child, st);
   in.count = upload(d, b.count, st);
   in.box = upload(d, b.box, st);
-  in.masks = d.alloc<uint32_t>(b.masks.size());
-  CUDA_OK(cudaMemsetAsync(in.masks, 0, b.masks.size() * sizeof(uint32_t), st));
-  in.R = R;
+  if (node_dirty) {
+    in.masks = upload(d, b.masks, st);
+  } else {
+    in.masks = d.alloc<uint32_t>(b.masks.size());
+    CUDA_OK(cudaMemsetAsync(in.masks, 0, b.masks.size() * sizeof(uint32_t), st));
+  }
+  in.R = b.R;
   in.L = std::min(L, b.max_depth + 1);
   in.W = b.W;
-  in.eps = eps;
+  in.eps = b.eps;
   const int64_t* d_order = upload(d, order, st);
   for (int dep = b.max_depth; dep >= 0; --dep) {
     const int64_t nslots = 2 * (int64_t)(start[dep + 1] - start[dep]);
@@ -212,6 +213,24 @@ void build_masks_gpu(Bvh& b, int R, int L, double eps) {
   CUDA_OK(cudaMemcpyAsync(b.masks.data(), in.masks, b.masks.size() * sizeof(uint32_t),
                           cudaMemcpyDeviceToHost, st));
   CUDA_OK(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+void build_masks_gpu(Bvh& b, int R, int L, double eps) {
+  const double t0 = now_ms();
+  b.R = R;
+  b.L = L;
+  b.W = mask_words(R);
+  b.eps = eps;
+  b.masks.assign((size_t)b.nn * 2 * b.W, 0u);
+  if (b.nn > 0) masks_gpu_levels(b, nullptr);
+  b.ms_masks = now_ms() - t0;
+}
+
+void refit_masks_gpu(Bvh& b, const std::vector<uint8_t>& node_dirty) {
+  const double t0 = now_ms();
+  if (b.nn > 0) masks_gpu_levels(b, &node_dirty);
   b.ms_masks = now_ms() - t0;
 }
 

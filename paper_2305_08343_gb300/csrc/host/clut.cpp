@@ -131,6 +131,16 @@ void build_compression(Bvh& b, int K, int bits, int threads) {
   b.K = (int)table.size();
   b.clut.assign((size_t)b.K * W, 0u);
   for (int j = 0; j < b.K; ++j) std::memcpy(&b.clut[(size_t)j * W], table[j].m, 4 * W);
+  encode_slots(b, threads, nullptr);
+  b.ms_compress = now_ms() - t0;
+}
+
+// Alg. 3 for the slots of the nodes marked in node_dirty (every slot when
+// NULL) against the LUT in b.clut: the requirement LUTs of Sec. 3.2.3, then
+// per slot the first entry every chunk of its mask allows.
+void encode_slots(Bvh& b, int threads, const std::vector<uint8_t>* node_dirty) {
+  const int W = b.W, R = b.R, R3 = R * R * R, bits = b.bits;
+  const int64_t ns = b.nn * 2;
   // 4. requirement LUTs: req[i][p] = 256-bit list of entries
   const int nchunk = (R3 + bits - 1) / bits, np = 1 << bits;
   auto chunk_of = [&](const uint32_t* m, int i) -> unsigned {
@@ -150,10 +160,11 @@ void build_compression(Bvh& b, int K, int bits, int threads) {
           req[((size_t)i * np + p) * 8 + (j >> 5)] |= 1u << (j & 31);
     }
   });
-  // 5. Alg. 3 for every slot
-  b.cidx.assign((size_t)ns, 0);
+  // 5. Alg. 3 for every (marked) slot
+  if (!node_dirty) b.cidx.assign((size_t)ns, 0);
   const bool bytewise = (bits == 8);
   parallel_for(ns, threads, 4096, [&](int64_t s) {
+    if (node_dirty && !(*node_dirty)[s >> 1]) return;
     const uint32_t* m = &b.masks[(size_t)s * W];
     const uint8_t* bytes = reinterpret_cast<const uint8_t*>(m);
     uint32_t list[8];
@@ -169,7 +180,6 @@ void build_compression(Bvh& b, int K, int bits, int threads) {
     if (idx < 0) fail(SC_ERR_STATE, "compression: no conservative LUT entry");
     b.cidx[s] = (uint8_t)idx;
   });
-  b.ms_compress = now_ms() - t0;
 }
 
 }  // namespace sc

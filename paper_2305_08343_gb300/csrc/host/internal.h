@@ -74,6 +74,11 @@ void build_masks(Bvh& b, int R, int L, double eps, int threads);
 // The same masks built on the current GPU (bit-identical).
 void build_masks_gpu(Bvh& b, int R, int L, double eps);
 void build_compression(Bvh& b, int K, int bits, int threads);
+// Refit support: masks of the marked nodes only (host or GPU), and Alg. 3
+// against the existing LUT for the marked nodes' slots (all when NULL).
+void refit_masks(Bvh& b, const std::vector<uint8_t>& node_dirty, int threads);
+void refit_masks_gpu(Bvh& b, const std::vector<uint8_t>& node_dirty);
+void encode_slots(Bvh& b, int threads, const std::vector<uint8_t>* node_dirty);
 double scene_eps(const float* tris, int64_t n, double eps_rel);
 
 // Ray-mask tables (Sec. 3.1.1).  pair2d: [R^4] entries of R^2 bits,

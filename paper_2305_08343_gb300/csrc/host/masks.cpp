@@ -48,4 +48,28 @@ void build_masks(Bvh& b, int R, int L, double eps, int threads) {
   b.ms_masks = now_ms() - t0;
 }
 
+// Masks of the nodes marked in node_dirty only (both slots of each), deepest
+// level first; every other mask is kept.  A slot's mask depends only on its
+// box and what lies below it, so after a refit only slots above a moved
+// triangle need it again.
+void refit_masks(Bvh& b, const std::vector<uint8_t>& node_dirty, int threads) {
+  double t0 = now_ms();
+  std::vector<std::vector<int64_t>> levels(b.max_depth + 1);
+  for (int64_t n = 0; n < b.nn; ++n)
+    if (node_dirty[n]) levels[b.ndepth[n]].push_back(n);
+  const mm::MaskInputs in{b.tris.data(), b.perm.data(), b.child.data(), b.count.data(),
+                          b.box.data(),      b.masks.data(), b.R, std::min(b.L, b.max_depth + 1),
+                          b.W,               b.eps};
+  for (int d = b.max_depth; d >= 0; --d) {
+    const auto& lv = levels[d];
+    parallel_for((int64_t)lv.size() * 2, threads, 256, [&](int64_t i) {
+      const int64_t n = lv[i >> 1];
+      const int c = (int)(i & 1);
+      std::memset(&b.masks[((size_t)n * 2 + c) * b.W], 0, sizeof(uint32_t) * b.W);
+      mm::slot_mask(in, n, c);
+    });
+  }
+  b.ms_masks = now_ms() - t0;
+}
+
 }  // namespace sc

@@ -104,6 +104,8 @@ def lib():
             "sc_bvh_get_info": (C.c_int, [vp, P(sc_bvh_info)]),
             "sc_bvh_export": (C.c_int, [vp, i32p, i32p, i32p, f32p, i32p, u32p, u32p, u8p]),
             "sc_raylut": (C.c_int, [C.c_int, u32p]),
+            "sc_raylut2r": (C.c_int, [C.c_int, u32p]),
+            "sc_bvh_refit": (C.c_int, [vp, f32p, i64, P(sc_refit_info)]),
             "sc_bvh_save": (C.c_int, [vp, C.c_char_p]),
             "sc_bvh_load": (C.c_int, [C.c_char_p, P(vp)]),
             "sc_bvh_device_bytes": (C.c_int, [vp, C.c_int, P(C.c_size_t)]),
@@ -250,6 +252,21 @@ def sc_bvh_build(tris: np.ndarray, grid_res: int = 6, compress: int = 0,
     _check(lib().sc_bvh_build(_ptr(t, C.c_float) if len(t) else None, t.shape[0], grid_res,
                               compress, C.byref(o), C.byref(h)))
     return Bvh(h, t.shape[0])
+
+
+class sc_refit_info(C.Structure):
+    _fields_ = [("moved_tris", C.c_int64), ("dirty_nodes", C.c_int64), ("ms_boxes", C.c_double),
+                ("ms_masks", C.c_double), ("ms_compress", C.c_double)]
+
+
+def sc_bvh_refit(bvh: Bvh, tris: np.ndarray) -> sc_refit_info:
+    """Moves the BVH's triangles to `tris` (same count, input order): boxes,
+    masks and compression indices above moved triangles are computed again."""
+    t = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    info = sc_refit_info()
+    _check(lib().sc_bvh_refit(bvh.handle, _ptr(t, C.c_float) if len(t) else None, t.shape[0],
+                              C.byref(info)))
+    return info
 
 
 def sc_bvh_save(bvh: Bvh, path: str):

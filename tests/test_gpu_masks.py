@@ -43,3 +43,37 @@ def test_gpu_masks_compressed_and_timing_fields():
     for k in ("masks", "clut", "cidx"):
         assert np.array_equal(ea[k], eb[k]), k
     assert b.info().ms_masks > 0.0
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_gpu_refit_equals_host_refit_and_traces_like_the_oracle(comp):
+    """sc_bvh_refit on a BVH built with gpu_masks recomputes the dirty slots'
+    masks on the GPU: the same bits as the host refit.  The refit image,
+    uploaded again, traces like the oracle's refit BVH (ids, t, counts)."""
+    _need_gpu()
+    import oracle
+    tris = sg.hair(1024, 16, True, seed=13)
+    moved = tris.copy()
+    moved[32 * 200:32 * 203] += np.float32(0.02)  # three strands
+    host = sc.sc_bvh_build(tris, 6, comp)
+    dev = sc.sc_bvh_build(tris, 6, comp, gpu_masks=1)
+    ih, idv = sc.sc_bvh_refit(host, moved), sc.sc_bvh_refit(dev, moved)
+    assert ih.dirty_nodes == idv.dirty_nodes and 0 < idv.dirty_nodes
+    eh, ed = host.export(), dev.export()
+    for k in eh:
+        assert np.array_equal(eh[k], ed[k]), k
+    ob = oracle.OracleBVH(tris).build_masks(6, 3)
+    if comp:
+        ob.compress(256, 8)
+    ob.refit(moved).build_masks(6, 3)
+    if comp:
+        ob.reencode()
+    rays = sg.pinhole(96, 64)
+    o = ob.trace(rays, 0, 2 if comp else 1)
+    d = sc.DeviceBVH(dev, sc.SC_LAYOUT_MASKED)
+    hits, counts = sc.trace(d, torch.from_numpy(rays).cuda(), sc.SC_CLOSEST, 1)
+    torch.cuda.synchronize()
+    h = hits.cpu().numpy()
+    assert np.array_equal(h[:, 1].view(np.int32), o["id"])
+    assert np.array_equal(h[:, 0].view(np.int32), o["t"].view(np.int32))
+    assert np.array_equal(counts.cpu().numpy().view(np.uint32), o["counts"])
