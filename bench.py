@@ -63,6 +63,9 @@ MEASURED_TRAFFIC = {
     "hair1m": (1.681529e9 + 0.245082e9,
                "4ceeb1bf8057b738464c49fd38c8e76afd7bd25785121df83d8411c6c80bd499",
                "profiles/waves_kernel_hair1m.md"),
+    "hair12m": (1.852002e9 + 0.380839e9,
+                "4ceeb1bf8057b738464c49fd38c8e76afd7bd25785121df83d8411c6c80bd499",
+                "profiles/waves_kernel_hair12m.md"),
 }
 
 
