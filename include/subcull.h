@@ -505,6 +505,21 @@ sc_status sc_mlp_labels(const float* d_rays, const void* d_hits, int64_t n,
    (SC_OK, or SC_ERR_STACK if a ray's stack overflowed). */
 sc_status sc_status_poll(const void* d_work, void* stream);
 
+/* ------------------------------------------------ L2 bandwidth probe --- */
+/* The roofline denominator for work whose data stays in L2 (not in the
+   paper).  sc_l2_read launches sc_l2_probe_blocks() blocks on `stream` that
+   read the bytes at d_buf (device, 16-byte aligned, a non-zero multiple of
+   16 bytes) `reps` times through L2 only (no L1 allocation), each block
+   XOR-folding the 32-bit words it read into d_sink[block] (device uint64,
+   at least sc_l2_probe_blocks() entries; with an odd reps the XOR of all
+   sinks is the XOR of the buffer's words).  Time it with events on the
+   stream; bytes * reps were read.  SC_ERR_ARG for a NULL or misaligned
+   buffer or reps < 1, SC_ERR_CUDA without a device.  sc_l2_probe_blocks
+   returns 0 without a device. */
+int sc_l2_probe_blocks(void);
+sc_status sc_l2_read(const void* d_buf, size_t bytes, int reps, uint64_t* d_sink,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

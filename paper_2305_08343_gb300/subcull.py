@@ -106,6 +106,8 @@ def lib():
             "sc_raylut": (C.c_int, [C.c_int, u32p]),
             "sc_raylut2r": (C.c_int, [C.c_int, u32p]),
             "sc_bvh_refit": (C.c_int, [vp, f32p, i64, P(sc_refit_info)]),
+            "sc_l2_probe_blocks": (C.c_int, []),
+            "sc_l2_read": (C.c_int, [vp, C.c_size_t, C.c_int, vp, vp]),
             "sc_bvh_save": (C.c_int, [vp, C.c_char_p]),
             "sc_bvh_load": (C.c_int, [C.c_char_p, P(vp)]),
             "sc_bvh_device_bytes": (C.c_int, [vp, C.c_int, P(C.c_size_t)]),
@@ -267,6 +269,17 @@ def sc_bvh_refit(bvh: Bvh, tris: np.ndarray) -> sc_refit_info:
     _check(lib().sc_bvh_refit(bvh.handle, _ptr(t, C.c_float) if len(t) else None, t.shape[0],
                               C.byref(info)))
     return info
+
+
+def sc_l2_probe_blocks() -> int:
+    return int(lib().sc_l2_probe_blocks())
+
+
+def sc_l2_read(buf, reps: int, sink, stream=None):
+    """Reads the device tensor `buf` reps times through L2 (see the header);
+    sink: device int64 tensor of >= sc_l2_probe_blocks() entries."""
+    _check(lib().sc_l2_read(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(), reps,
+                            C.c_void_p(sink.data_ptr()), _stream_ptr(stream)))
 
 
 def sc_bvh_save(bvh: Bvh, path: str):
