@@ -128,3 +128,22 @@ def test_refit_errors(scene):
     with pytest.raises(sc.SubcullError) as e:
         sc.sc_bvh_refit(b, bad)
     assert e.value.code == sc.SC_ERR_ARG
+
+
+def test_refit_then_checkpoint_round_trip(scene, tmp_path):
+    t1 = _move_strand(scene, 77)
+    b = sc.sc_bvh_build(scene, 6, 1)
+    sc.sc_bvh_refit(b, t1)
+    path = str(tmp_path / "refit.ckpt")
+    sc.sc_bvh_save(b, path)
+    c = sc.sc_bvh_load(path)
+    ea, ec = b.export(), c.export()
+    for k in ea:
+        assert np.array_equal(ea[k], ec[k]), k
+    # the loaded BVH refits further like the original
+    t2 = _move_strand(t1, 78)
+    ia, ic = sc.sc_bvh_refit(b, t2), sc.sc_bvh_refit(c, t2)
+    assert (ia.moved_tris, ia.dirty_nodes) == (ic.moved_tris, ic.dirty_nodes)
+    ea, ec = b.export(), c.export()
+    for k in ea:
+        assert np.array_equal(ea[k], ec[k]), k
