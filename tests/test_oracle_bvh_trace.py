@@ -130,14 +130,22 @@ def test_cell_index_alg1():
 
 
 def _check_against_brute(tris, rays, near_tie_rel=1e-6):
+    """Closest hits equal brute force: t on every ray, the triangle id on
+    every ray without an exact tie (equal t, where brute force takes the
+    lowest index and traversal the first met).  Rays whose second-closest
+    hit lies within near_tie_rel of the closest are listed separately."""
     b = oracle.OracleBVH(tris)
     o = b.trace(rays, 0, 0)
     bt, bid, t2 = oracle.brute(tris, rays, 0)
     assert np.array_equal(o["t"], bt)
     with np.errstate(invalid="ignore"):
-        tie = (t2 - bt) <= near_tie_rel * np.abs(bt)
+        near = (t2 - bt) <= near_tie_rel * np.abs(bt)
+    exact = (t2 == bt) & (bid >= 0)
     diff = o["id"] != bid
-    assert not (diff & ~tie).any(), "hit id differs on a ray without a near tie"
+    assert not (diff & ~exact).any(), "hit id differs on a ray without an exact tie"
+    print(f"\n{len(rays)} rays: {int(near.sum())} near-tie (second hit within "
+          f"{near_tie_rel:g}), {int(exact.sum())} exact ties, {int(diff.sum())} ids differ "
+          f"(exact ties only): rays {np.nonzero(near)[0][:10].tolist()}")
     return b, o
 
 
@@ -290,3 +298,30 @@ def test_dense_mask_skip_keeps_hits_and_orders_counts(hair_small):
             # nodes are culled the same way; only leaf triangles can be added
             assert np.array_equal(o["counts"][:, 0], full["counts"][:, 0])
             prev = o
+
+
+def test_exact_and_near_ties_against_brute_force():
+    """A duplicated triangle (exact tie: any of the two is right) and a copy
+    moved about one float step (2.5e-7 at t = 3) along the ray: a near tie
+    that is not exact, so the closer copy must win."""
+    base = sg.hair(64, 16, False, seed=29)
+    tri = np.array([[-0.5, -0.5, 0.0, 0.5, -0.5, 0.0, 0.0, 0.5, 0.0]], np.float32)
+    near = tri.copy()
+    near[0, 2::3] += np.float32(2.5e-7)  # z of the three vertices
+    tris = np.concatenate([base, tri, tri, near]).astype(np.float32)
+    rays = np.zeros((64, 8), np.float32)
+    g = np.linspace(-0.2, 0.2, 8, dtype=np.float32)
+    rays[:, 0] = np.repeat(g, 8)
+    rays[:, 1] = np.tile(g, 8)
+    rays[:, 2] = 3.0
+    rays[:, 6] = -1.0           # towards -z
+    rays[:, 7] = np.inf
+    b, o = _check_against_brute(tris, rays)
+    n = len(base)
+    on = (o["id"] >= n)
+    assert on.sum() > 40
+    # the moved copy is closer to rays coming from +z: it is the hit
+    assert (o["id"][on] == n + 2).all()
+    # without it, the two copies tie exactly: either is right
+    b2, o2 = _check_against_brute(tris[:-1], rays)
+    assert np.isin(o2["id"][on], [n, n + 1]).all()
