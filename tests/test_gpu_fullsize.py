@@ -75,7 +75,7 @@ def _check_culled_equals_plain(culled, plain):
         assert (c["counts"][oc] <= p["counts"][op]).all(), f"wave {w}: culled counts > plain"
 
 
-def _check_brute(tris, rays, hits):
+def _check_brute(tris, rays, hits, near_tie_rel=1e-6):
     t, hid, t2 = oracle.brute(tris, rays, 0)
     g_t, g_id = hits[:, 0], _bits(hits[:, 1])
     assert np.array_equal(_bits(g_t), _bits(t)), "closest t differs from brute force"
@@ -84,6 +84,10 @@ def _check_brute(tris, rays, hits):
     for i in np.nonzero(tie & (hid >= 0))[0]:  # exact ties: any tied triangle is right
         ok, tt, _, _ = oracle.ray_tri(rays[i], tris[g_id[i]])
         assert ok and tt == t[i]
+    with np.errstate(invalid="ignore"):
+        near = (t2 - t) <= near_tie_rel * np.abs(t)
+    print(f"\n{len(rays)} sampled rays: {int(near.sum())} near-tie (second hit within "
+          f"{near_tie_rel:g}), {int((tie & (hid >= 0)).sum())} exact ties")
 
 
 def test_hair1m_full_size_sampled_oracle_parity():
