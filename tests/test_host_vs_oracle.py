@@ -154,3 +154,20 @@ def test_device_image_sizes():
             masked = sc.sc_bvh_device_bytes(b, sc.SC_LAYOUT_MASKED)
             assert plain % 256 == 0 and masked % 256 == 0
             assert masked - plain >= nn * (nb - 64)
+
+
+def test_ray2r_image_sizes_and_limits():
+    """SC_LAYOUT_MASKED_RAY2R adds the (2R)^6-row table (one mask stride per
+    row) to SC_LAYOUT_MASKED, for uncompressed masks at R = 4 and 6 only."""
+    tris = sg.hair(64, 16, False)
+    for R, stride in ((4, 8), (6, 32)):
+        b = sc.sc_bvh_build(tris, R, 0)
+        extra = (sc.sc_bvh_device_bytes(b, sc.SC_LAYOUT_MASKED_RAY2R)
+                 - sc.sc_bvh_device_bytes(b, sc.SC_LAYOUT_MASKED))
+        rows = (2 * R) ** 6
+        assert rows * stride <= extra < rows * stride + 256
+    for R, comp in ((8, 0), (6, 1)):
+        b = sc.sc_bvh_build(tris, R, comp)
+        with pytest.raises(sc.SubcullError) as e:
+            sc.sc_bvh_device_bytes(b, sc.SC_LAYOUT_MASKED_RAY2R)
+        assert e.value.code == sc.SC_ERR_UNSUPPORTED
