@@ -171,3 +171,17 @@ def test_ray2r_image_sizes_and_limits():
         with pytest.raises(sc.SubcullError) as e:
             sc.sc_bvh_device_bytes(b, sc.SC_LAYOUT_MASKED_RAY2R)
         assert e.value.code == sc.SC_ERR_UNSUPPORTED
+
+
+def test_probe_and_refit_argument_errors_without_a_device():
+    L = sc.lib()
+    # NULL buffers are refused before any device call
+    assert L.sc_l2_read(None, 16, 1, None, None) == sc.SC_ERR_ARG
+    assert L.sc_bvh_refit(None, None, 0, None) == sc.SC_ERR_ARG
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if not has_gpu:
+        assert L.sc_l2_probe_blocks() == 0
