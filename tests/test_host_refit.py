@@ -147,3 +147,27 @@ def test_refit_then_checkpoint_round_trip(scene, tmp_path):
     ea, ec = b.export(), c.export()
     for k in ea:
         assert np.array_equal(ea[k], ec[k]), k
+
+
+def test_refit_edge_cases():
+    # no triangles
+    b = sc.sc_bvh_build(np.zeros((0, 9), np.float32), 6, 0)
+    i = sc.sc_bvh_refit(b, np.zeros((0, 9), np.float32))
+    assert (i.moved_tris, i.dirty_nodes) == (0, 0)
+    # one triangle: the root is a leaf, its box moves with it
+    t = np.array([[0, 0, 0, 1, 0, 0, 0, 1, 0]], np.float32)
+    t2 = t + np.float32(0.5)
+    b = sc.sc_bvh_build(t, 6, 1)
+    i = sc.sc_bvh_refit(b, t2)
+    assert (i.moved_tris, i.dirty_nodes) == (1, 0)
+    ob = oracle.OracleBVH(t).build_masks(6, 3)
+    ob.refit(t2)
+    assert np.array_equal(np.array(b.info().root_box[:], np.float32), ob.root()[2])
+    # five triangles: one node, compressed
+    t5 = sg.soup(5, seed=2)
+    m = t5.copy()
+    m[2] += np.float32(0.1)
+    b = sc.sc_bvh_build(t5, 6, 1)
+    i = sc.sc_bvh_refit(b, m)
+    assert (i.moved_tris, i.dirty_nodes) == (1, 1)
+    _same_as_oracle(b, _oracle_refit(t5, m, 6, 1), 1)
