@@ -26,7 +26,7 @@ _SO = os.path.join(_HERE, "_build", platform.machine() or "unknown", "liboracle.
 _lock = threading.Lock()
 _lib = None
 
-CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
           "-fno-fast-math", "-fno-strict-aliasing"]
 
 
@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", *CFLAGS, src, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", *CFLAGS, src, "-o", tmp, "-lm", "-lpthread"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -94,6 +94,10 @@ def lib():
             "or_slab": (C.c_int, [_P(f), _P(f), f, _P(f), _P(f)]),
             "or_cell": (C.c_int, [f, f, f, C.c_int]),
             "or_cell_t": (C.c_int, [f, f, f, f, f, C.c_int]),
+            "or_cell_at": (C.c_int, [f, f, f, f, f, C.c_int]),
+            "or_cell2_at": (C.c_int, [f, f, f, f, f, C.c_int, C.c_int]),
+            "or_bvh_set_cellform": (None, [vp, C.c_int]),
+            "or_set_threads": (None, [C.c_int, i64]),
             "or_bvh_frontier": (C.c_int, [vp, C.c_int, _P(i32), _P(i32), _P(f), _P(u8)]),
             "or_trace_seeded": (C.c_int, [vp, _P(f), _P(f), i64, C.c_int, C.c_int, C.c_int,
                                           C.c_int, _P(i32), _P(i32), _P(i32), _P(f), C.c_int,
@@ -124,6 +128,13 @@ def _ptr(a: np.ndarray, t):
 
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def set_threads(threads: int = 0, task_tris: int = 0):
+    """Threads of the oracle's build (0: every online core) and the largest
+    triangle range built as one subtree task (0: automatic).  Results do not
+    depend on either."""
+    lib().or_set_threads(int(threads), int(task_tris))
 
 
 def mask_words(R: int) -> int:
@@ -370,6 +381,13 @@ def _trace_seeded(self, rays, cls, depth: int = 8, cull: int = 0, skip_bits=None
     return dict(t=t, id=hid, uv=uv, counts=cnt)
 
 
+def _set_cellform(self, form: int = 0):
+    """Cell form of the culling tests: 0 = Alg. 1 as written (default),
+    1 = the fused multiply-add form, mirroring the GPU option."""
+    lib().or_bvh_set_cellform(self._h, int(form))
+    return self
+
+
 def _set_ideal(self, ideal: bool = True):
     """Culling tests use the exact ray mask (Sec. 4.1's ideal culling)."""
     lib().or_bvh_set_ideal(self._h, int(bool(ideal)))
@@ -424,6 +442,7 @@ OracleBVH.reencode = _reencode
 OracleBVH.set_ray2r = _set_ray2r
 OracleBVH.wide = _wide
 OracleBVH.set_ideal = _set_ideal
+OracleBVH.set_cellform = _set_cellform
 OracleBVH.frontier = _frontier
 OracleBVH.trace_seeded = _trace_seeded
 
@@ -467,12 +486,24 @@ def cell(p: float, lo: float, hi: float, R: int) -> int:
 
 
 def cell_t(t: float, o: float, d: float, lo: float, hi: float, R: int) -> int:
-    return int(lib().or_cell_t(float(t), float(o), float(d), float(lo), float(hi), R))
+    """Alg. 1 cell by the fused form (an option of the traversal)."""
+    return int(lib().or_cell_t(t, o, d, lo, hi, R))
+
+
+def cell_at(t: float, o: float, d: float, lo: float, hi: float, R: int) -> int:
+    """Alg. 1 cell as written: p = o + t d, then floor(R/extent (p - lo))."""
+    return int(lib().or_cell_at(t, o, d, lo, hi, R))
 
 
 def cell2_t(t: float, o: float, d: float, lo: float, hi: float, R: int) -> int:
-    """Cell on the 2R grid (R_ray = 2R) of the point at parameter t."""
-    return int(lib().or_cell2_t(float(t), float(o), float(d), float(lo), float(hi), R))
+    """2R-grid cell from the fused form (option)."""
+    return int(lib().or_cell2_at(t, o, d, lo, hi, R, 1))
+
+
+def cell2_at(t: float, o: float, d: float, lo: float, hi: float, R: int, form: int = 0) -> int:
+    """2R-grid cell: twice the Alg. 1 coordinate (form 0, default) or the
+    fused one (form 1), rounded down, clamped to [0, 2R-1]."""
+    return int(lib().or_cell2_at(t, o, d, lo, hi, R, form))
 
 
 # -------------------------------------------------------------- bounce rays --

@@ -12,8 +12,11 @@
 #include "oracle.h"
 
 #include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 /* ------------------------------------------------------------ helpers --- */
 
@@ -32,6 +35,67 @@ static int popcount_mask(const uint32_t* m, int W) {
 static int cell_bit(int R, int x, int y, int z) { return x + R * y + R * R * z; }
 static double dmin(double a, double b) { return a < b ? a : b; }
 static double dmax(double a, double b) { return a > b ? a : b; }
+
+/* ------------------------------------------------------------ threads --- */
+/* The build's independent pieces (subtrees of the BVH, the slots of one
+   depth level of the masks, the slots' LUT encodings) may run on several
+   threads.  Each piece is computed by the same code whatever the thread, so
+   the results do not depend on the thread count. */
+static int g_threads = 0; /* 0: every online core */
+static int64_t g_task_tris = 0; /* 0: automatic subtree task size */
+
+void or_set_threads(int threads, int64_t task_tris) {
+  g_threads = threads < 0 ? 0 : threads;
+  g_task_tris = task_tris < 0 ? 0 : task_tris;
+}
+
+static int num_threads(void) {
+  if (g_threads > 0) return g_threads;
+  long n = sysconf(_SC_NPROCESSORS_ONLN);
+  return n > 0 ? (int)(n > 256 ? 256 : n) : 1;
+}
+
+typedef struct {
+  void (*fn)(void* ctx, int64_t i);
+  void* ctx;
+  int64_t n, grain;
+  atomic_llong next;
+} Jobs;
+
+static void* jobs_worker(void* arg) {
+  Jobs* j = (Jobs*)arg;
+  for (;;) {
+    int64_t i0 = atomic_fetch_add(&j->next, j->grain);
+    if (i0 >= j->n) break;
+    int64_t i1 = i0 + j->grain < j->n ? i0 + j->grain : j->n;
+    for (int64_t i = i0; i < i1; ++i) j->fn(j->ctx, i);
+  }
+  return NULL;
+}
+
+/* fn(ctx, i) for every i in [0, n), on up to num_threads() threads. */
+static void run_jobs(void (*fn)(void*, int64_t), void* ctx, int64_t n, int64_t grain) {
+  Jobs j;
+  j.fn = fn;
+  j.ctx = ctx;
+  j.n = n;
+  j.grain = grain > 0 ? grain : 1;
+  atomic_init(&j.next, 0);
+  int t = num_threads();
+  if ((int64_t)t > (n + j.grain - 1) / j.grain) t = (int)((n + j.grain - 1) / j.grain);
+  if (t <= 1) {
+    jobs_worker(&j);
+    return;
+  }
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)t);
+  int started = 0;
+  for (int k = 0; k < t - 1; ++k)
+    if (pthread_create(&th[k], NULL, jobs_worker, &j) == 0) ++started;
+    else break;
+  jobs_worker(&j);
+  for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+  free(th);
+}
 
 /* ------------------------------------------- ray-mask LUT (Sec. 3.1.1) --- */
 /*
@@ -468,6 +532,7 @@ struct OrBvh {
   uint32_t* raylut;
   int ideal; /* 1: culling tests use the exact ray mask (ideal_ray_mask) */
   const uint32_t* raylut2r; /* R_ray = 2R table (caller-owned), or NULL */
+  int cellform; /* Alg. 1 cell form: 0 as written (default), 1 fused (or_cell_t) */
   /* 4-wide view (or_bvh_wide): per 4-wide node its child slots as (binary
      parent node, child index), and the 4-wide node of each inner child */
   int64_t nn4;
@@ -519,20 +584,17 @@ static int64_t new_node(OrBvh* b) {
   return b->nnodes++;
 }
 
-/* Builds the subtree for perm[begin, end) and returns its slot. */
-static void build_range(BuildCtx* x, int64_t begin, int64_t end, int depth,
-                        int32_t* s_child, int32_t* s_count, float* s_box) {
+/* The box of perm[begin, end) into s_box, and, for a range of more than
+   max_leaf triangles, its binned-SAH split: the range is partitioned in
+   place and the position of the split is returned; -1 for a leaf. */
+static int64_t split_range(BuildCtx* x, int64_t begin, int64_t end, int depth, float* s_box) {
   OrBvh* b = x->b;
   int64_t n = end - begin;
   box_empty(s_box);
   for (int64_t i = begin; i < end; ++i)
     box_grow(s_box, x->rec[b->perm[i]].lo, x->rec[b->perm[i]].hi);
   if (depth > b->max_depth) b->max_depth = depth;
-  if (n <= x->max_leaf) {
-    *s_child = (int32_t)begin;
-    *s_count = (int32_t)n;
-    return;
-  }
+  if (n <= x->max_leaf) return -1;
   double cmin[3] = {INFINITY, INFINITY, INFINITY};
   double cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t i = begin; i < end; ++i)
@@ -616,6 +678,19 @@ static void build_range(BuildCtx* x, int64_t begin, int64_t end, int depth,
   } else {
     mid = begin + n / 2;
   }
+  return mid;
+}
+
+/* Builds the subtree for perm[begin, end) and returns its slot. */
+static void build_range(BuildCtx* x, int64_t begin, int64_t end, int depth,
+                        int32_t* s_child, int32_t* s_count, float* s_box) {
+  OrBvh* b = x->b;
+  int64_t mid = split_range(x, begin, end, depth, s_box);
+  if (mid < 0) {
+    *s_child = (int32_t)begin;
+    *s_count = (int32_t)(end - begin);
+    return;
+  }
   int64_t node = new_node(b);
   b->ndepth[node] = depth;
   *s_child = (int32_t)node;
@@ -630,6 +705,191 @@ static void build_range(BuildCtx* x, int64_t begin, int64_t end, int depth,
   b->count[2 * node + 1] = n1;
   memcpy(b->box + 12 * node, b0, sizeof(b0));
   memcpy(b->box + 12 * node + 6, b1, sizeof(b1));
+}
+
+/* ---- the same build with independent subtrees on several threads.  The
+   top of the tree is split serially (build_top) down to ranges of at most
+   `task` triangles; each such range is a task that build_range turns into a
+   subtree in its own node arrays (its perm range is disjoint from every
+   other's); then every node gets the number the serial pre-order recursion
+   gives it: a top node before its left subtree, a task's nodes as one
+   block in their own pre-order. */
+typedef struct {
+  int64_t begin, end;
+  int depth;
+  int64_t parent; /* top node holding the slot, -1 for the root slot */
+  int c;
+  OrBvh sub;      /* the task's nodes (perm shared with the tree) */
+  int32_t child, count;
+  float box[6];
+  const TriRec* rec;
+  int max_leaf, bins;
+} Task;
+
+typedef struct {
+  Task* t;
+  int64_t n, cap;
+} TaskList;
+
+static void build_top(BuildCtx* x, TaskList* tl, int64_t task, int64_t begin, int64_t end,
+                      int depth, int64_t parent, int c, int32_t* s_child, int32_t* s_count,
+                      float* s_box) {
+  OrBvh* b = x->b;
+  int64_t n = end - begin;
+  if (n > x->max_leaf && n <= task) {
+    if (tl->n == tl->cap) {
+      tl->cap = tl->cap ? 2 * tl->cap : 64;
+      tl->t = (Task*)realloc(tl->t, sizeof(Task) * (size_t)tl->cap);
+    }
+    Task* t = &tl->t[tl->n];
+    memset(t, 0, sizeof(*t));
+    t->begin = begin;
+    t->end = end;
+    t->depth = depth;
+    t->parent = parent;
+    t->c = c;
+    *s_child = (int32_t)tl->n++;
+    *s_count = -1; /* filled in after the tasks ran */
+    return;
+  }
+  /* as build_range, with the recursion below going to build_top */
+  int64_t mid = split_range(x, begin, end, depth, s_box);
+  if (mid < 0) {
+    *s_child = (int32_t)begin;
+    *s_count = (int32_t)n;
+    return;
+  }
+  int64_t node = new_node(b);
+  b->ndepth[node] = depth;
+  *s_child = (int32_t)node;
+  *s_count = 0;
+  int32_t c0, n0, c1, n1;
+  float b0[6], b1[6];
+  build_top(x, tl, task, begin, mid, depth + 1, node, 0, &c0, &n0, b0);
+  build_top(x, tl, task, mid, end, depth + 1, node, 1, &c1, &n1, b1);
+  b->child[2 * node] = c0;
+  b->count[2 * node] = n0;
+  b->child[2 * node + 1] = c1;
+  b->count[2 * node + 1] = n1;
+  memcpy(b->box + 12 * node, b0, sizeof(b0));
+  memcpy(b->box + 12 * node + 6, b1, sizeof(b1));
+}
+
+static void task_job(void* ctx, int64_t i) {
+  Task* t = &((TaskList*)ctx)->t[i];
+  BuildCtx x = {&t->sub, t->rec, (int32_t*)malloc(sizeof(int32_t) * (size_t)(t->end - t->begin)),
+                t->max_leaf, t->bins};
+  build_range(&x, t->begin, t->end, t->depth, &t->child, &t->count, t->box);
+  free(x.tmp);
+}
+
+/* Pre-order numbers: map[top node] and base[task]. */
+static void number_top(const OrBvh* b, const TaskList* tl, int64_t node, int64_t* next,
+                       int64_t* map, int64_t* base) {
+  map[node] = (*next)++;
+  for (int c = 0; c < 2; ++c) {
+    int32_t ch = b->child[2 * node + c], cn = b->count[2 * node + c];
+    if (cn == -1) {
+      base[ch] = *next;
+      *next += tl->t[ch].sub.nnodes;
+    } else if (cn == 0) {
+      number_top(b, tl, ch, next, map, base);
+    }
+  }
+}
+
+static void build_threaded(BuildCtx* x, int64_t n, int64_t task) {
+  OrBvh* b = x->b;
+  TaskList tl = {NULL, 0, 0};
+  build_top(x, &tl, task, 0, n, 0, -1, 0, &b->root_child, &b->root_count, b->root_box);
+  for (int64_t k = 0; k < tl.n; ++k) {
+    Task* t = &tl.t[k];
+    t->sub.perm = b->perm;
+    t->rec = x->rec;
+    t->max_leaf = x->max_leaf;
+    t->bins = x->bins;
+  }
+  run_jobs(task_job, &tl, tl.n, 1);
+  int64_t ntop = b->nnodes, next = 0;
+  int64_t* map = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ntop > 0 ? ntop : 1));
+  int64_t* base = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tl.n > 0 ? tl.n : 1));
+  if (b->root_count == -1) {
+    base[b->root_child] = 0;
+    next = tl.t[b->root_child].sub.nnodes;
+  } else if (b->root_count == 0) {
+    number_top(b, &tl, b->root_child, &next, map, base);
+  }
+  OrBvh f;
+  memset(&f, 0, sizeof(f));
+  f.cap = next > 0 ? next : 1;
+  f.nnodes = next;
+  f.child = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)f.cap);
+  f.count = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)f.cap);
+  f.box = (float*)malloc(sizeof(float) * 12 * (size_t)f.cap);
+  f.ndepth = (int32_t*)malloc(sizeof(int32_t) * (size_t)f.cap);
+  int max_depth = b->max_depth;
+  /* a slot word (child, count) in the final numbering; a task's root is an
+     inner node (the task has more than max_leaf triangles) */
+  for (int64_t k = 0; k < tl.n; ++k) {
+    Task* t = &tl.t[k];
+    for (int64_t i = 0; i < t->sub.nnodes; ++i) {
+      int64_t d = base[k] + i;
+      for (int c = 0; c < 2; ++c) {
+        int32_t ch = t->sub.child[2 * i + c], cn = t->sub.count[2 * i + c];
+        f.child[2 * d + c] = cn > 0 ? ch : (int32_t)(base[k] + ch);
+        f.count[2 * d + c] = cn;
+      }
+      memcpy(f.box + 12 * d, t->sub.box + 12 * i, sizeof(float) * 12);
+      f.ndepth[d] = t->sub.ndepth[i];
+    }
+    if (t->sub.max_depth > max_depth) max_depth = t->sub.max_depth;
+    if (t->parent >= 0) {
+      memcpy(b->box + 12 * t->parent + 6 * t->c, t->box, sizeof(float) * 6);
+    } else {
+      memcpy(b->root_box, t->box, sizeof(float) * 6);
+    }
+  }
+  for (int64_t i = 0; i < ntop; ++i) {
+    int64_t d = map[i];
+    for (int c = 0; c < 2; ++c) {
+      int32_t ch = b->child[2 * i + c], cn = b->count[2 * i + c];
+      if (cn == -1) {
+        f.child[2 * d + c] = (int32_t)base[ch];
+        f.count[2 * d + c] = 0;
+      } else {
+        f.child[2 * d + c] = cn > 0 ? ch : (int32_t)map[ch];
+        f.count[2 * d + c] = cn;
+      }
+    }
+    memcpy(f.box + 12 * d, b->box + 12 * i, sizeof(float) * 12);
+    f.ndepth[d] = b->ndepth[i];
+  }
+  if (b->root_count == -1) {
+    b->root_child = 0;
+    b->root_count = 0;
+  } else if (b->root_count == 0) {
+    b->root_child = (int32_t)map[b->root_child];
+  }
+  free(b->child);
+  free(b->count);
+  free(b->box);
+  free(b->ndepth);
+  b->child = f.child;
+  b->count = f.count;
+  b->box = f.box;
+  b->ndepth = f.ndepth;
+  b->nnodes = f.nnodes;
+  b->cap = f.cap;
+  b->max_depth = max_depth;
+  for (int64_t k = 0; k < tl.n; ++k) {
+    free(tl.t[k].sub.child);
+    free(tl.t[k].sub.count);
+    free(tl.t[k].sub.box);
+    free(tl.t[k].sub.ndepth);
+  }
+  free(tl.t);
+  free(map);
+  free(base);
 }
 
 OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins) {
@@ -655,13 +915,21 @@ OrBvh* or_bvh_build(const float* tris, int64_t n, int max_leaf, int bins) {
   }
   BuildCtx x = {b, rec, (int32_t*)malloc(sizeof(int32_t) * (size_t)n),
                 max_leaf, bins};
-  build_range(&x, 0, n, 0, &b->root_child, &b->root_count, b->root_box);
+  int th = num_threads();
+  int64_t task = g_task_tris > 0 ? g_task_tris : n / (16 * (int64_t)th);
+  if (task < 4096) task = 4096;
+  if (th > 1 && n > task && max_leaf >= 1) {
+    build_threaded(&x, n, task);
+  } else {
+    build_range(&x, 0, n, 0, &b->root_child, &b->root_count, b->root_box);
+  }
   free(x.tmp);
   free(rec);
   return b;
 }
 
 void or_bvh_set_ideal(OrBvh* b, int ideal) { b->ideal = ideal; }
+void or_bvh_set_cellform(OrBvh* b, int form) { b->cellform = form == 1 ? 1 : 0; }
 
 /* Refit for moved triangles (dynamic scenes, which the paper leaves to
    future work): the tree's topology and triangle order stay; every child
@@ -835,22 +1103,68 @@ int or_bvh_masks(OrBvh* b, const float* tris, int R, int L, double eps) {
   return masks_fill_all(b, tris);
 }
 
+/* The two slot masks of node nidx. */
+static void node_masks(MaskCtx* x, int64_t nidx) {
+  OrBvh* b = x->b;
+  for (int c = 0; c < 2; ++c) {
+    uint32_t* out = b->masks + ((size_t)nidx * 2 + c) * b->W;
+    const float* gbox = b->box + 12 * nidx + 6 * c;
+    int32_t ch = b->child[2 * nidx + c], cn = b->count[2 * nidx + c];
+    memset(out, 0, sizeof(uint32_t) * b->W);
+    if (cn > 0) voxelize_leaf(x, ch, cn, gbox, out);
+    else collect(x, ch, 1, gbox, out);
+  }
+}
+
+typedef struct {
+  MaskCtx* x;
+  const int64_t* nodes;
+} LevelJob;
+
+static void level_job(void* ctx, int64_t i) {
+  LevelJob* j = (LevelJob*)ctx;
+  node_masks(j->x, j->nodes[i]);
+}
+
+/* A slot's mask reads only the masks of slots deeper than itself, so the
+   nodes are processed one depth level at a time, deepest first, and the
+   nodes of one level independently (on several threads). */
 static int masks_fill_all(OrBvh* b, const float* tris) {
   MaskCtx x = {b, tris};
-  for (int64_t nidx = b->nnodes - 1; nidx >= 0; --nidx)
-    for (int c = 0; c < 2; ++c) {
-      uint32_t* out = b->masks + ((size_t)nidx * 2 + c) * b->W;
-      const float* gbox = b->box + 12 * nidx + 6 * c;
-      int32_t ch = b->child[2 * nidx + c], cn = b->count[2 * nidx + c];
-      memset(out, 0, sizeof(uint32_t) * b->W);
-      if (cn > 0) voxelize_leaf(&x, ch, cn, gbox, out);
-      else collect(&x, ch, 1, gbox, out);
-    }
+  int64_t nn = b->nnodes;
+  if (nn == 0) return 0;
+  int D = 0;
+  for (int64_t i = 0; i < nn; ++i)
+    if (b->ndepth[i] > D) D = b->ndepth[i];
+  int64_t* start = (int64_t*)calloc((size_t)D + 2, sizeof(int64_t));
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)nn);
+  for (int64_t i = 0; i < nn; ++i) start[b->ndepth[i] + 1] += 1;
+  for (int d = 0; d <= D; ++d) start[d + 1] += start[d];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * ((size_t)D + 1));
+  for (int d = 0; d <= D; ++d) fill[d] = start[d];
+  for (int64_t i = 0; i < nn; ++i) order[fill[b->ndepth[i]]++] = i;
+  for (int d = D; d >= 0; --d) {
+    LevelJob j = {&x, order + start[d]};
+    run_jobs(level_job, &j, start[d + 1] - start[d], 64);
+  }
+  free(fill);
+  free(order);
+  free(start);
   return 0;
 }
 
 void or_bvh_get_masks(const OrBvh* b, uint32_t* masks) {
   memcpy(masks, b->masks, sizeof(uint32_t) * (size_t)b->nnodes * 2 * b->W);
+}
+
+typedef struct {
+  OrBvh* b;
+  const uint32_t* req;
+} EncodeJob;
+
+static void encode_job(void* ctx, int64_t s) {
+  EncodeJob* j = (EncodeJob*)ctx;
+  j->b->cidx[s] = (uint8_t)or_encode(j->b->masks + (size_t)s * j->b->W, j->req, j->b->R, j->b->bits);
 }
 
 int or_bvh_compress(OrBvh* b, int K, int bits) {
@@ -866,8 +1180,8 @@ int or_bvh_compress(OrBvh* b, int K, int bits) {
   int nchunk = (R * R * R + bits - 1) / bits;
   uint32_t* req = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nchunk * (1u << bits) * 8);
   or_req_luts(b->clut, b->K, R, bits, req);
-  for (int64_t s = 0; s < ns; ++s)
-    b->cidx[s] = (uint8_t)or_encode(b->masks + (size_t)s * W, req, R, bits);
+  EncodeJob j = {b, req};
+  run_jobs(encode_job, &j, ns, 4096);
   free(req);
   return b->K;
 }
@@ -976,16 +1290,21 @@ int or_ray_tri(const float* ray8, const float* tri9, float tcur, float* t,
   return mt_test(&r, tri9, tcur, t, u, v);
 }
 
-/* Culling test of one child (Sec. 3.1.2 and the red part of Alg. 4): the
-   clipped segment's ends at tn and tf are turned into cells (Alg. 1, see
-   or_cell_t), the ray mask is looked up, and the child survives iff the AND
-   with its object mask is non-zero. */
-/* Cell of the point at parameter t on axis k.  Alg. 1 maps p = o + t d to
-   floor(R/extent * (p - lower)); the traversal evaluates the same quantity
-   in the ray parameter, q(t) = s (o - lower) + t (s d) with s = R / extent,
-   as one fused multiply-add (one rounding): fmaf(t, s*d, s*(o - lower)).
-   Clamped to [0, R-1] like or_cell.  The eps dilation of the object masks
-   absorbs the difference in rounding. */
+/* Cell of the point at parameter t on one axis, Alg. 1 as written: the
+   point p = o + t d (a product, then a sum: two roundings, no fused
+   multiply-add), then floor(R/extent * (p - lower)) by or_cell, clamped to
+   [0, R-1].  This is the traversal's default. */
+int or_cell_at(float t, float o, float d, float lo, float hi, int R) {
+  float p = o + t * d;
+  return or_cell(p, lo, hi, R);
+}
+
+/* The same cell evaluated in the ray parameter instead (an option of the
+   traversal, not the paper's order): q(t) = s (o - lower) + t (s d) with
+   s = R / extent, as one fused multiply-add, fmaf(t, s*d, s*(o - lower)).
+   It can differ from Alg. 1 only where q lies within rounding of a cell
+   border; the eps dilation of the object masks keeps culling conservative
+   either way.  Clamped to [0, R-1] like or_cell. */
 int or_cell_t(float t, float o, float d, float lo, float hi, int R) {
   float ext = hi - lo;
   float s = (float)R / fmaxf(ext, 1e-30f);
@@ -1050,18 +1369,40 @@ static void ideal_ray_mask(const ORay* r, const float* bx, float tn, float tf, i
       }
 }
 
-/* Cell of the point at parameter t on the 2R grid (R_ray = 2R): twice the
-   R-grid coordinate q of or_cell_t (doubling is exact), clamped to
-   [0, 2R-1]. */
-int or_cell2_t(float t, float o, float d, float lo, float hi, int R) {
+/* Cell of the point at parameter t on the 2R grid (R_ray = 2R, Sec. 4.2):
+   twice the R-grid coordinate q, rounded down and clamped to [0, 2R-1].
+   Doubling is exact, so the enclosing R cell is the Alg. 1 cell.  form 0
+   (default): q = R/extent * (p - lower) with p = o + t d as in or_cell_at;
+   form 1: q by the fused multiply-add of or_cell_t. */
+int or_cell2_at(float t, float o, float d, float lo, float hi, int R, int form) {
   float ext = hi - lo;
   float s = (float)R / fmaxf(ext, 1e-30f);
-  float q = 2.0f * fmaf(t, d * s, (o - lo) * s);
+  float q;
+  if (form == 1) {
+    q = fmaf(t, d * s, (o - lo) * s);
+  } else {
+    float p = o + t * d;
+    q = (p - lo) * s;
+  }
+  q = 2.0f * q;
   q = fminf(fmaxf(q, -1.0f), (float)(2 * R));
   int i = (int)floorf(q);
   if (i < 0) i = 0;
   if (i > 2 * R - 1) i = 2 * R - 1;
   return i;
+}
+
+int or_cell2_t(float t, float o, float d, float lo, float hi, int R) {
+  return or_cell2_at(t, o, d, lo, hi, R, 1);
+}
+
+/* Culling test of one child (Sec. 3.1.2 and the red part of Alg. 4): the
+   ends of the clipped segment, at tn and tf, are turned into cells (Alg. 1:
+   or_cell_at, or or_cell_t when the BVH's cell form is 1), the ray mask of
+   the (begin, end) pair is looked up, and the child survives iff its AND
+   with the object mask is non-zero. */
+static int cell_of(const OrBvh* b, float t, float o, float d, float lo, float hi) {
+  return b->cellform == 1 ? or_cell_t(t, o, d, lo, hi, b->R) : or_cell_at(t, o, d, lo, hi, b->R);
 }
 
 static int cull_pass(const OrBvh* b, const ORay* r, const float* bx, float tn,
@@ -1078,8 +1419,8 @@ static int cull_pass(const OrBvh* b, const ORay* r, const float* bx, float tn,
     const int R2 = 2 * R, R23 = R2 * R2 * R2;
     int b2[3], e2[3];
     for (int k = 0; k < 3; ++k) {
-      b2[k] = or_cell2_t(tn, r->o[k], r->d[k], bx[k], bx[3 + k], R);
-      e2[k] = or_cell2_t(tf, r->o[k], r->d[k], bx[k], bx[3 + k], R);
+      b2[k] = or_cell2_at(tn, r->o[k], r->d[k], bx[k], bx[3 + k], R, b->cellform);
+      e2[k] = or_cell2_at(tf, r->o[k], r->d[k], bx[k], bx[3 + k], R, b->cellform);
     }
     const int beg = b2[0] + R2 * b2[1] + R2 * R2 * b2[2];
     const int end = e2[0] + R2 * e2[1] + R2 * R2 * e2[2];
@@ -1090,8 +1431,8 @@ static int cull_pass(const OrBvh* b, const ORay* r, const float* bx, float tn,
   }
   int cb[3], ce[3];
   for (int k = 0; k < 3; ++k) {
-    cb[k] = or_cell_t(tn, r->o[k], r->d[k], bx[k], bx[3 + k], R);
-    ce[k] = or_cell_t(tf, r->o[k], r->d[k], bx[k], bx[3 + k], R);
+    cb[k] = cell_of(b, tn, r->o[k], r->d[k], bx[k], bx[3 + k]);
+    ce[k] = cell_of(b, tf, r->o[k], r->d[k], bx[k], bx[3 + k]);
   }
   int beg = cell_bit(R, cb[0], cb[1], cb[2]);
   int end = cell_bit(R, ce[0], ce[1], ce[2]);

@@ -36,6 +36,7 @@ void or_raylut(int R, uint32_t* lut /* [R^3 * R^3][W] */);
 /* R_ray = 2R table (Sec. 4.2): rows [row_begin, row_end) of [(2R)^6][W]. */
 void or_raylut2r_rows(int R, int64_t row_begin, int64_t row_end, uint32_t* lut);
 int or_cell2_t(float t, float o, float d, float lo, float hi, int R);
+int or_cell2_at(float t, float o, float d, float lo, float hi, int R, int form);
 
 /* Conservative voxelization (Sec. 3.1.1): triangle-box overlap by the
    separating axis theorem, in double. */
@@ -64,6 +65,15 @@ void or_bvh_free(OrBvh* b);
    cells the clipped segment meets, found in double) instead of the
    lookup table -- the paper's "ideal culling" reference of Sec. 4.1. */
 void or_bvh_set_ideal(OrBvh* b, int ideal);
+/* Threads of the build (the tree's independent subtrees, the masks of one
+   depth level, the LUT encodings): 0 = every online core; task_tris = the
+   largest range built as one subtree task (0: automatic).  The results do
+   not depend on either. */
+void or_set_threads(int threads, int64_t task_tris);
+/* Alg. 1 cell form of the culling tests: 0 = as written, p = o + t d then
+   floor(R/extent * (p - lower)) (default); 1 = the fused form of
+   or_cell_t, an option of the GPU traversal mirrored here. */
+void or_bvh_set_cellform(OrBvh* b, int form);
 /* Refit: slot boxes from moved triangles, topology kept (masks: or_bvh_masks). */
 int or_bvh_refit(OrBvh* b, const float* tris);
 /* Alg. 3 for every slot against the existing compression LUT. */
@@ -145,6 +155,7 @@ int or_slab(const float* ray8, const float* box6, float tcur, float* tn,
             float* tf);
 int or_cell(float p, float lo, float hi, int R);
 int or_cell_t(float t, float o, float d, float lo, float hi, int R);
+int or_cell_at(float t, float o, float d, float lo, float hi, int R);
 
 #ifdef __cplusplus
 }

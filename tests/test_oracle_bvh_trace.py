@@ -101,17 +101,33 @@ def test_slab_closed_form():
     assert ok and tn == 0.0 and tf == 0.5
 
 
-def test_cell_in_ray_parameter_matches_alg1():
-    """or_cell_t (the traversal's form) evaluates Alg. 1 at p = o + t d; it
-    may differ from the literal form only where p is within rounding of a
-    cell border."""
+@pytest.mark.parametrize("R", [4, 6, 8])
+def test_traversal_cell_is_alg1_exactly(R):
+    """The culling test's cell (or_cell_at, the traversal's default) is Alg. 1
+    applied to the point p = o + t d formed in float32 (a product, then a
+    sum): it equals or_cell of that point on every sample, with no
+    tolerance.  numpy's float32 scalar arithmetic forms p independently."""
+    rng = np.random.default_rng(3 + R)
+    for _ in range(20000):
+        lo, hi = np.sort(rng.uniform(-2, 2, 2)).astype(np.float32)
+        if rng.random() < 0.05:
+            hi = lo  # flat box: the extent floor of 1e-30
+        o, d = np.float32(rng.uniform(-3, 3)), np.float32(rng.normal())
+        t = np.float32(rng.uniform(0, 4))
+        p = np.float32(o + np.float32(t * d))
+        assert oracle.cell_at(t, o, d, lo, hi, R) == oracle.cell(p, lo, hi, R)
+
+
+def test_fused_cell_option_differs_only_at_cell_borders():
+    """The fused form (an option of the traversal, or_cell_t) evaluates the
+    same coordinate with one rounding; it may differ from Alg. 1 only where
+    the exact coordinate lies within rounding of a cell border."""
     rng = np.random.default_rng(3)
     diff = 0
     for _ in range(20000):
         lo, hi = np.sort(rng.uniform(-2, 2, 2)).astype(np.float32)
         o, d, t = np.float32(rng.uniform(-3, 3)), np.float32(rng.normal()), np.float32(rng.uniform(0, 4))
-        p = np.float32(o + t * d)
-        a, b = oracle.cell(p, lo, hi, 6), oracle.cell_t(t, o, d, lo, hi, 6)
+        a, b = oracle.cell_at(t, o, d, lo, hi, 6), oracle.cell_t(t, o, d, lo, hi, 6)
         if a != b:
             q = (float(o) + float(t) * float(d) - float(lo)) * 6 / (float(hi) - float(lo))
             assert abs(q - round(q)) < 1e-4
@@ -228,10 +244,12 @@ def test_edge_cases():
     assert np.array_equal(o["t"], bt)
 
 
-def test_ray_mask_covers_sampled_segment():
+@pytest.mark.parametrize("form", [0, 1])
+def test_ray_mask_covers_sampled_segment(form):
     """C9: for random boxes and rays, every densely sampled point of the true
     clipped segment lies within a small distance of a cell set in the ray
-    mask looked up from the float segment ends (Alg. 1)."""
+    mask looked up from the float segment ends (Alg. 1 as written, form 0,
+    and the fused option, form 1)."""
     R = 6
     lut = oracle.raylut(R)
     bits = np.unpackbits(lut.view(np.uint8), axis=1, bitorder="little")[:, : R ** 3].astype(bool)
@@ -248,8 +266,9 @@ def test_ray_mask_covers_sampled_segment():
         ok, tn, tf = oracle.slab(ray, np.concatenate([lo, hi]))
         if not ok:
             continue
-        cb = [oracle.cell_t(tn, ray[k], ray[4 + k], lo[k], hi[k], R) for k in range(3)]
-        ce = [oracle.cell_t(tf, ray[k], ray[4 + k], lo[k], hi[k], R) for k in range(3)]
+        cell = oracle.cell_t if form else oracle.cell_at
+        cb = [cell(tn, ray[k], ray[4 + k], lo[k], hi[k], R) for k in range(3)]
+        ce = [cell(tf, ray[k], ray[4 + k], lo[k], hi[k], R) for k in range(3)]
         row = (cb[0] + R * cb[1] + R * R * cb[2]) * R ** 3 + (ce[0] + R * ce[1] + R * R * ce[2])
         m = bits[row].reshape(R, R, R)  # [z, y, x]
         od, dd = ray[:3].astype(np.float64), ray[4:7].astype(np.float64)

@@ -104,9 +104,12 @@ def test_cell2_encloses_in_the_R_cell_and_rounds_down(R):
         hi = lo + float(rng.choice([1e-3, 0.5, 3.0]))
         o, d = float(rng.uniform(-4, 4)), float(rng.normal())
         t = float(rng.uniform(-1, 3))
-        c1 = oracle.cell_t(t, o, d, lo, hi, R)
-        c2 = oracle.cell2_t(t, o, d, lo, hi, R)
+        c1 = oracle.cell_at(t, o, d, lo, hi, R)
+        c2 = oracle.cell2_at(t, o, d, lo, hi, R)
         assert 0 <= c2 < 2 * R and c2 // 2 == c1
+        f1 = oracle.cell_t(t, o, d, lo, hi, R)
+        f2 = oracle.cell2_t(t, o, d, lo, hi, R)
+        assert 0 <= f2 < 2 * R and f2 // 2 == f1
         u = 2 * R * ((o + t * d) - lo) / (hi - lo)
         if abs(u - round(u)) > 1e-3:
             assert c2 == int(np.clip(np.floor(u), 0, 2 * R - 1))
