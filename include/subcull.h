@@ -292,7 +292,32 @@ typedef struct {
                         out records SC_ERR_TIMEOUT, which sc_waves_poll
                         returns, and the kernel returns; the context stays
                         usable.                                           */
+  int variant;       /* kernel options, a bit field of SC_VARIANT_* (0 =
+                        the defaults).  Built for R = 6 images (uncompressed
+                        with the full table, compressed with the bit
+                        table) and the plain traversal, in sc_trace and,
+                        with block 128 / stack 64, sc_trace_waves; other
+                        combinations give SC_ERR_UNSUPPORTED.             */
 } sc_trace_opts;
+
+/* Kernel options of sc_trace_opts.variant.  Only SC_VARIANT_FUSED_CELLS
+   changes results: it evaluates the Alg. 1 cell coordinate in the ray
+   parameter as one fused multiply-add, s (o - lower) + t (s d) with
+   s = R / extent, instead of the paper's order (p = o + t d, then
+   s (p - lower)); cells can then differ where the coordinate lies within
+   rounding of a cell border (the object masks' dilation keeps culling
+   conservative).  The others change only the timing of loads, where the
+   top stack entry lives and the order in which bounce rays are traced; hits
+   and per-ray counts are unchanged. */
+enum {
+  SC_VARIANT_FUSED_CELLS = 1,  /* fused Alg. 1 coordinate (see above)        */
+  SC_VARIANT_PAIR = 2,         /* both children's lookups in flight together */
+  SC_VARIANT_SPEC = 4,         /* the nearer child's record requested before
+                                  the culling results arrive                */
+  SC_VARIANT_TOS = 8,          /* top stack entry held in registers          */
+  SC_VARIANT_SORT = 16         /* waves: bounce queues sorted by direction
+                                  octant and origin cell before tracing     */
+};
 
 /* Workspace bytes sc_trace needs (ray counter and device status word). */
 size_t sc_trace_workspace_bytes(void);
@@ -336,10 +361,12 @@ sc_status sc_trace_host(const sc_dbvh* d, const float* h_rays, int64_t n,
  * Arguments as for sc_trace, without the workspace: the caller still passes
  * the image, rays, hits and (optional) counts.  The call clears the scratch,
  * launches the trace on `stream`, waits for it and returns the device
- * status (SC_ERR_STACK / SC_ERR_STATE as sc_status_poll would).  The first
- * call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream
- * capture.  All calls share the one array, which keeps the last call's
+ * status (SC_ERR_STACK / SC_ERR_STATE as sc_status_poll would); every call
+ * blocks until its trace has finished.  The first call on a device looks up
+ * the array's device address (once per device, with that device current)
+ * and keeps it for the life of the process, so the library must not be used
+ * across a cudaDeviceReset; make that first call before any stream capture
+ * begins.  All calls share the one array, which keeps the last call's
  * contents: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialized by the caller.  Returns
  * SC_ERR_UNSUPPORTED if the trace ever needed more scratch than the array
@@ -367,8 +394,9 @@ typedef struct {
 } sc_wave_out;
 
 /* Workspace bytes sc_trace_waves needs for n0 primary rays with opts'
-   wave_chunk (NULL = one chunk): two ray queues of one chunk, their path
-   ids and the control words. */
+   wave_chunk (NULL = one chunk): two ray queues of one chunk and their path
+   ids, a third queue and a 32,768-entry histogram for the bounce-queue sort
+   (SC_VARIANT_SORT), and the control words. */
 size_t sc_trace_waves_workspace_bytes(int64_t n0, const sc_trace_opts* opts);
 
 /* d_rays: device float[n0][8] primary rays; outs: host array of bounces+1

@@ -30,6 +30,9 @@ WaveKernelFn get_waves_w4_r8(int cull, int lutv, int block);
 SeededKernelFn get_seeded_r4(int cull, int lutv, int scales);
 SeededKernelFn get_seeded_r6(int cull, int lutv, int scales);
 SeededKernelFn get_seeded_r8(int cull, int lutv, int scales);
+bool var_supported(int opt);
+KernelFn get_kernel_var(int R, int cull, int mode, int lutv, int opt);
+WaveKernelFn get_waves_var(int R, int cull, int lutv, int opt);
 }  // namespace sct
 
 using namespace sc;
@@ -109,6 +112,31 @@ sct::KernelFn pick_kernel(const sc_dbvh* d, int mode, int cull, int lutv) {
   fail(SC_ERR_UNSUPPORTED, "no kernel for R = %d", d->lay.R);
 }
 
+// Kernels with non-default options (sc_trace_opts.variant): R = 6 images
+// with the full table (uncompressed) or the bit table (compressed), scales
+// stored, and the plain traversal.
+void check_variant(const sc_dbvh* d, int cull, int lutv, int variant) {
+  if (!sct::var_supported(variant))
+    fail(SC_ERR_UNSUPPORTED, "kernel variant %d is not built", variant);
+  if (d->lay.width != 2) fail(SC_ERR_UNSUPPORTED, "kernel variants need a binary image");
+  if (cull) {
+    const bool ok = d->lay.R == 6 && d->lay.scales &&
+                    ((!d->lay.compress && lutv == 0) || (d->lay.compress && lutv == 2));
+    if (!ok)
+      fail(SC_ERR_UNSUPPORTED,
+           "kernel variants are built for R = 6 images with stored scales (full table "
+           "uncompressed, bit table compressed)");
+  }
+}
+
+sct::KernelFn pick_kernel_var(const sc_dbvh* d, int mode, int cull, int lutv, int variant) {
+  check_variant(d, cull, lutv, variant);
+  sct::KernelFn k = cull ? sct::get_kernel_var(6, d->lay.compress ? 2 : 1, mode, lutv, variant)
+                         : sct::get_kernel_var(0, 0, mode, 0, variant);
+  if (!k) fail(SC_ERR_UNSUPPORTED, "kernel variant %d is not built for this image", variant);
+  return k;
+}
+
 void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hits,
                   uint32_t* d_counts, int mode, int cull, const sc_trace_opts* opts,
                   void* d_work, size_t work_bytes, cudaStream_t st) {
@@ -125,13 +153,15 @@ void launch_trace(const sc_dbvh* d, const float* d_rays, int64_t n, sc_hit* d_hi
   if (d->stack_need > sct::kStack)
     fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
          sct::kStack);
-  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
+  sc_trace_opts o{};
+  o.lut_mode = SC_LUT_AUTO;
   if (opts) o = *opts;
   if (o.block != 0 && o.block != kBlock) fail(SC_ERR_UNSUPPORTED, "block must be 0 or 128");
   if (o.stack != 0 && o.stack != sct::kStack) fail(SC_ERR_UNSUPPORTED, "stack must be 0 or 64");
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   const int lutv = lut_variant(d, o.lut_mode);
-  sct::KernelFn k = pick_kernel(d, mode, cull ? 1 : 0, lutv);
+  sct::KernelFn k = o.variant ? pick_kernel_var(d, mode, cull ? 1 : 0, lutv, o.variant)
+                              : pick_kernel(d, mode, cull ? 1 : 0, lutv);
   CUDA_OK(cudaMemsetAsync(d_work, 0, kWorkBytes, st));
   if (n == 0) return;
   DevInfo di = device_info();
@@ -182,8 +212,8 @@ size_t waves_ctrl_bytes(int64_t n0, int64_t chunk) {
 
 size_t waves_ws_bytes(int64_t n0, int64_t chunk) {
   const size_t q = (size_t)(chunk > 0 ? chunk : 1);
-  return waves_ctrl_bytes(n0, chunk) + 2 * ((q * 32 + 255) / 256 * 256) +
-         2 * ((q * 4 + 255) / 256 * 256);
+  return waves_ctrl_bytes(n0, chunk) + 3 * ((q * 32 + 255) / 256 * 256) +
+         3 * ((q * 4 + 255) / 256 * 256) + (size_t)sct::kSortBins * 4;
 }
 
 void fill_params(const sc_dbvh* d, sct::Params& p) {
@@ -248,7 +278,8 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   }
   if (n0 > 0 && !d_rays) fail(SC_ERR_ARG, "sc_trace_waves: NULL rays");
   if (reinterpret_cast<uintptr_t>(d_rays) & 15) fail(SC_ERR_ARG, "rays must be 16-byte aligned");
-  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
+  sc_trace_opts o{};
+  o.lut_mode = SC_LUT_AUTO;
   if (opts) o = *opts;
   const int64_t chunk = wave_chunk_of(n0, &o);
   if (o.wave_chunk < 0) fail(SC_ERR_ARG, "wave_chunk must be >= 0");
@@ -266,7 +297,17 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   int lutv = lut_variant(d, o.lut_mode);
   if (lutv == 1 && d->lay.R != 4) lutv = 0;  // factored tables: single-batch kernel only
-  sct::WaveKernelFn k = pick_waves(d, cull, lutv, block, stack);
+  sct::WaveKernelFn k = nullptr;
+  if (o.variant) {
+    check_variant(d, cull, lutv, o.variant);
+    if (block != kBlock || stack != sct::kStack)
+      fail(SC_ERR_UNSUPPORTED, "kernel variants of the waves are built for block %d, stack %d",
+           kBlock, sct::kStack);
+    k = cull ? sct::get_waves_var(6, d->lay.compress ? 2 : 1, lutv, o.variant)
+             : sct::get_waves_var(0, 0, 0, o.variant);
+  } else {
+    k = pick_waves(d, cull, lutv, block, stack);
+  }
   if (!k) fail(SC_ERR_UNSUPPORTED, "no wave kernel for this block / stack / lookup combination");
   const size_t ctrl = waves_ctrl_bytes(n0, chunk);
   CUDA_OK(cudaMemsetAsync(d_ws, 0, ctrl, st));
@@ -288,6 +329,16 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
   for (int i = 0; i < 2; ++i) {
     wp.qpath[i] = reinterpret_cast<int*>(ws + off);
     off += (q * 4 + 255) / 256 * 256;
+  }
+  wp.srays = reinterpret_cast<float4*>(ws + off);
+  off += (q * 32 + 255) / 256 * 256;
+  wp.spath = reinterpret_cast<int*>(ws + off);
+  off += (q * 4 + 255) / 256 * 256;
+  wp.hist = reinterpret_cast<unsigned*>(ws + off);
+  for (int k = 0; k < 3; ++k) {
+    const float ext = d->root_box[3 + k] - d->root_box[k];
+    wp.box_lo[k] = d->root_box[k];
+    wp.box_scale[k] = ext > 0.0f ? (float)(1 << sct::kSortCellBits) / ext : 0.0f;
   }
   wp.rays0 = reinterpret_cast<const float4*>(d_rays);
   wp.n0 = n0;
@@ -397,6 +448,7 @@ sc_status sc_bvh_upload(const sc_bvh* h, int layout, void* d_buf, size_t nbytes,
   d->root_slot = root_slot_word(b);  // the root node is record 0 at either width
   d->has_root = b.ntri > 0 ? 1 : 0;
   d->stack_need = L.stack_need;
+  for (int k = 0; k < 6; ++k) d->root_box[k] = b.root_box[k];
   *out = d;
   return SC_OK;
   SC_CATCH
@@ -436,10 +488,12 @@ sc_status sc_trace_seeded(const sc_dbvh* d, const float* d_rays, int64_t n, cons
   if (d->stack_need > sct::kStack)
     fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
          sct::kStack);
-  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
+  sc_trace_opts o{};
+  o.lut_mode = SC_LUT_AUTO;
   if (opts) o = *opts;
   if ((o.block && o.block != kBlock) || (o.stack && o.stack != sct::kStack))
     fail(SC_ERR_UNSUPPORTED, "sc_trace_seeded: default block and stack only");
+  if (o.variant) fail(SC_ERR_UNSUPPORTED, "sc_trace_seeded: kernel variants are not built");
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   int lutv = lut_variant(d, o.lut_mode);
   if (lutv == 1 || lutv == 3) lutv = 0;
@@ -581,9 +635,10 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
   SC_TRY
   if (!d || !best || n0 <= 0 || reps < 1) fail(SC_ERR_ARG, "sc_autotune_waves: bad argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  sc_trace_opts o{0, 0, SC_LUT_AUTO, 0, 0, 0};
+  sc_trace_opts o{};
+  o.lut_mode = SC_LUT_AUTO;
   if (base) o = *base;
-  const bool all_blocks = (!cull) || d->lay.R == 6;
+  const bool all_blocks = ((!cull) || d->lay.R == 6) && o.variant == 0;
   std::vector<int> blocks = all_blocks ? std::vector<int>{64, 128, 256} : std::vector<int>{128};
   std::vector<int> stacks;
   if (all_blocks && d->stack_need <= 32) stacks.push_back(32);

@@ -82,13 +82,44 @@ struct MaskTraits {
   static constexpr int kWords = (R * R * R + 31) / 32;
 };
 
-// Alg. 1 on one axis, evaluated in the ray parameter: the cell coordinate
-// of o + t d is q = s (o - lo) + t (s d), s = R / max(extent, 1e-30), one
-// fused multiply-add.  The saturating float-to-unsigned conversion (cvt.rmi,
-// negatives and NaN to 0) and a min give floor(q) clamped to [0, R-1].
+// Kernel options (template bit field OPT).  None changes which nodes are
+// visited; OPT_FUSED changes the rounding of the Alg. 1 cell coordinate and
+// has its own oracle mode.
+enum : int {
+  OPT_FUSED = 1,  // Alg. 1 coordinate by one fused multiply-add in t (not the paper's order)
+  OPT_PAIR = 2,   // the lookups of both children are in flight before either is used
+  OPT_SPEC = 4,   // the nearer slab-passing child's record is fetched before the
+                  // culling results arrive (and every next record at the end of a step)
+  OPT_TOS = 8,    // the top stack entry is kept in registers
+  OPT_SORT = 16,  // waves: each bounce queue is sorted by direction octant and
+                  // origin cell before its wave is traced
+};
+
+// floor(q) clamped to [0, R-1]: the saturating float-to-unsigned conversion
+// (cvt.rmi, negatives and NaN to 0) and a min.
 template <int R>
 __device__ __forceinline__ int cell_of_q(float q) {
   return (int)min(__float2uint_rd(q), (unsigned)(R - 1));
+}
+
+// Alg. 1 cell coordinates (before the floor) of the segment ends at tn and
+// tf on one axis of a box with lower bound lo and scale s = R / extent.  As
+// written: p = o + t d (product, then sum), then (p - lo) * s.  OPT_FUSED:
+// s (o - lo) + t (s d) as one fused multiply-add.
+template <int OPT>
+__device__ __forceinline__ void cell_coords(float o, float d, float lo, float s, float tn,
+                                            float tf, float& q0, float& q1) {
+  if constexpr ((OPT & OPT_FUSED) != 0) {
+    const float a = __fmul_rn(__fsub_rn(o, lo), s);
+    const float b = __fmul_rn(d, s);
+    q0 = __fmaf_rn(tn, b, a);
+    q1 = __fmaf_rn(tf, b, a);
+  } else {
+    const float p0 = __fadd_rn(o, __fmul_rn(tn, d));
+    const float p1 = __fadd_rn(o, __fmul_rn(tf, d));
+    q0 = __fmul_rn(__fsub_rn(p0, lo), s);
+    q1 = __fmul_rn(__fsub_rn(p1, lo), s);
+  }
 }
 
 template <int R>
@@ -266,6 +297,25 @@ __device__ __forceinline__ void stage_tables(SharedTables<R, LUTV>& sh, const Pa
   }
 }
 
+// Record of one inner node as loaded: boxes, slots and meta words, and with
+// stored scales the two float4 after them.
+struct Rec {
+  float4 f0, f1, f2, f3, f4, f5;
+};
+
+template <bool SCALED>
+__device__ __forceinline__ void load_rec(const Params& p, uint32_t node, Rec& r) {
+  const float4* nd = p.nodes + (long long)node * p.node_f4;
+  r.f0 = __ldg(nd);
+  r.f1 = __ldg(nd + 1);
+  r.f2 = __ldg(nd + 2);
+  r.f3 = __ldg(nd + 3);
+  if constexpr (SCALED) {
+    r.f4 = __ldg(nd + 4);
+    r.f5 = __ldg(nd + 5);
+  }
+}
+
 struct RayState {
   float ox, oy, oz, dx, dy, dz, ix, iy, iz, tmin, tcur;
   float ht, hu, hv;
@@ -275,6 +325,9 @@ struct RayState {
   int sp;
   uint32_t cur;
   bool have;  // `cur` is the next slot to visit (else pop)
+  bool pre;   // OPT_SPEC: nx holds the record of `cur` (loaded or in flight)
+  Rec nx;     // OPT_SPEC: prefetched record (its first four float4)
+  uint2 top;  // OPT_TOS: the top stack entry (the array holds the ones below)
 };
 
 __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const float4 rb,
@@ -294,12 +347,13 @@ __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const flo
   s.sp = 0;
   s.cur = p.root_slot;
   s.have = p.has_root != 0;
+  s.pre = false;
 }
 
 // Culling test of one child from its record data: Alg. 1 cells of the
 // segment [tn, tf] in the child's grid (lo, scales), the ray-mask lookup and
 // the AND with the object mask `obj` (uncompressed) or LUT entry `meta`.
-template <int R, int CULL, int LUTV>
+template <int R, int CULL, int LUTV, int OPT = 0>
 __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R, LUTV>& sh,
                                           const uint8_t* obj, unsigned meta, const float* lo,
                                           const float* sk, const float* o, const float* d,
@@ -313,10 +367,10 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
     constexpr int R2 = 2 * R;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
-      const float b = __fmul_rn(d[k], sk[k]);
-      cb[k] = cell_of_q<R2>(__fmul_rn(2.0f, __fmaf_rn(tn, b, a)));
-      ce[k] = cell_of_q<R2>(__fmul_rn(2.0f, __fmaf_rn(tf, b, a)));
+      float q0, q1;
+      cell_coords<OPT>(o[k], d[k], lo[k], sk[k], tn, tf, q0, q1);
+      cb[k] = cell_of_q<R2>(__fmul_rn(2.0f, q0));
+      ce[k] = cell_of_q<R2>(__fmul_rn(2.0f, q1));
     }
     const int beg2 = cb[0] + R2 * cb[1] + R2 * R2 * cb[2];
     const int end2 = ce[0] + R2 * ce[1] + R2 * R2 * ce[2];
@@ -326,10 +380,10 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float a = __fmul_rn(__fsub_rn(o[k], lo[k]), sk[k]);
-    const float b = __fmul_rn(d[k], sk[k]);
-    cb[k] = cell_of_q<R>(__fmaf_rn(tn, b, a));
-    ce[k] = cell_of_q<R>(__fmaf_rn(tf, b, a));
+    float q0, q1;
+    cell_coords<OPT>(o[k], d[k], lo[k], sk[k], tn, tf, q0, q1);
+    cb[k] = cell_of_q<R>(q0);
+    ce[k] = cell_of_q<R>(q1);
   }
   const int beg = cb[0] + R * cb[1] + R * R * cb[2];
   const int end = ce[0] + R * ce[1] + R * R * ce[2];
@@ -357,14 +411,122 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
   }
 }
 
+// Stack push / pop.  OPT_TOS keeps the top entry in a register and the
+// entries below it in the array, so a pop takes the register and refills it
+// with a load whose latency hides behind the next node's work.
+template <int STACK, int OPT>
+__device__ __forceinline__ bool stack_push(RayState& s, uint2* stack, uint2 e) {
+  if (s.sp >= STACK) return false;
+  if constexpr ((OPT & OPT_TOS) != 0) {
+    if (s.sp > 0) stack[s.sp - 1] = s.top;
+    s.top = e;
+  } else {
+    stack[s.sp] = e;
+  }
+  ++s.sp;
+  return true;
+}
+
+template <int OPT>
+__device__ __forceinline__ uint2 stack_pop(RayState& s, uint2* stack) {
+  uint2 e;
+  --s.sp;
+  if constexpr ((OPT & OPT_TOS) != 0) {
+    e = s.top;
+    if (s.sp > 0) s.top = stack[s.sp - 1];
+  } else {
+    e = stack[s.sp];
+  }
+  return e;
+}
+
+// Begin and end cells (x + R y + R^2 z) of the clipped segment (Alg. 1).
+template <int R, int OPT>
+__device__ __forceinline__ int2 cell_pair(const float* o, const float* d, const float* lo,
+                                          const float* sk, float tn, float tf) {
+  int cb[3], ce[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float q0, q1;
+    cell_coords<OPT>(o[k], d[k], lo[k], sk[k], tn, tf, q0, q1);
+    cb[k] = cell_of_q<R>(q0);
+    ce[k] = cell_of_q<R>(q1);
+  }
+  return make_int2(cb[0] + R * cb[1] + R * R * cb[2], ce[0] + R * ce[1] + R * R * ce[2]);
+}
+
+// A culling test split in two, so that the loads of several tests can be in
+// flight together: lookup_issue computes the cells and issues the loads of
+// the ray-mask row (or bit-table word) and object mask; lookup_result ANDs
+// them.  Full table in global memory (LUTV 0, R <= 6) and bit table (LUTV 2).
+template <int R, int CULL, int LUTV>
+struct Lookup {
+  static constexpr int kQ = MaskTraits<R>::kQuads;
+  uint4 row[kQ > 0 ? kQ : 1], obj[kQ > 0 ? kQ : 1];
+  uint2 row2, obj2;  // R = 4
+  uint32_t word;     // bit table
+  unsigned bit;
+};
+
+template <int R, int CULL, int LUTV, int OPT>
+__device__ __forceinline__ void lookup_issue(const Params& p, Lookup<R, CULL, LUTV>& L,
+                                             const uint8_t* obj, unsigned meta, const float* lo,
+                                             const float* sk, const float* o, const float* d,
+                                             float tn, float tf) {
+  constexpr int R3 = R * R * R;
+  constexpr int MB = MaskTraits<R>::kStrideBytes;
+  const int2 be = cell_pair<R, OPT>(o, d, lo, sk, tn, tf);
+  const size_t row = (size_t)(be.x * R3 + be.y);
+  if constexpr (LUTV == 2) {
+    const unsigned j = meta & 0xFFu;
+    L.word = __ldg(p.bits + row * 8 + (j >> 5));
+    L.bit = j & 31u;
+  } else {
+    if constexpr (CULL == 2) obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
+    const uint8_t* rm = reinterpret_cast<const uint8_t*>(p.lut) + row * MB;
+    if constexpr (R == 4) {
+      L.row2 = __ldg(reinterpret_cast<const uint2*>(rm));
+      L.obj2 = __ldg(reinterpret_cast<const uint2*>(obj));
+    } else {
+#pragma unroll
+      for (int q = 0; q < Lookup<R, CULL, LUTV>::kQ; ++q) {
+        L.row[q] = __ldg(reinterpret_cast<const uint4*>(rm) + q);
+        L.obj[q] = __ldg(reinterpret_cast<const uint4*>(obj) + q);
+      }
+    }
+  }
+}
+
+template <int R, int CULL, int LUTV>
+__device__ __forceinline__ bool lookup_result(const Lookup<R, CULL, LUTV>& L) {
+  if constexpr (LUTV == 2) {
+    return (L.word >> L.bit) & 1u;
+  } else if constexpr (R == 4) {
+    return ((L.row2.x & L.obj2.x) | (L.row2.y & L.obj2.y)) != 0u;
+  } else {
+    unsigned acc = 0;
+#pragma unroll
+    for (int q = 0; q < Lookup<R, CULL, LUTV>::kQ; ++q)
+      acc |= (L.row[q].x & L.obj[q].x) | (L.row[q].y & L.obj[q].y) |
+             (L.row[q].z & L.obj[q].z) | (L.row[q].w & L.obj[q].w);
+    return acc != 0u;
+  }
+}
+
 // One traversal step of one ray: either the triangles of one leaf or one
 // inner node, then a pop if nothing is left to visit.  Returns true when the
-// ray has finished (or was stopped by a recorded device error).
-template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack>
+// ray has finished (or was stopped by a recorded device error).  The OPT
+// bits change only when loads are issued and where the top stack entry
+// lives, never which nodes are visited.
+template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack, int OPT = 0>
 __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* stack,
                                            const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
   constexpr int RR = (R > 0 ? R : 4);
   constexpr int MB = MaskTraits<RR>::kStrideBytes;
+  constexpr bool kScaled = CULL != 0 && SCALES != 0;
+  constexpr bool kSpec = (OPT & OPT_SPEC) != 0;
+  constexpr bool kSplit = CULL != 0 && (LUTV == 2 || (LUTV == 0 && RR <= 6)) &&
+                          (OPT & (OPT_PAIR | OPT_SPEC)) != 0;
   bool done = false;
   if (s.have) {
     if (s.cur & kLeaf) {
@@ -399,8 +561,23 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
       }
     } else {
       const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
-      const float4 f0 = __ldg(nd), f1 = __ldg(nd + 1), f2 = __ldg(nd + 2);
-      const uint4 f3 = __ldg(reinterpret_cast<const uint4*>(nd + 3));
+      Rec rc;
+      if constexpr (kSpec) {
+        // the prefetch holds the first 64 bytes; the scales follow in the
+        // same lines and are requested here, used after the slab tests
+        if (!s.pre) load_rec<false>(p, s.cur, s.nx);
+        rc = s.nx;
+        if constexpr (kScaled) {
+          rc.f4 = __ldg(nd + 4);
+          rc.f5 = __ldg(nd + 5);
+        }
+        s.pre = false;
+      } else {
+        load_rec<kScaled>(p, s.cur, rc);
+      }
+      const float4 f0 = rc.f0, f1 = rc.f1, f2 = rc.f2;
+      const uint4 f3 = make_uint4(__float_as_uint(rc.f3.x), __float_as_uint(rc.f3.y),
+                                  __float_as_uint(rc.f3.z), __float_as_uint(rc.f3.w));
       s.ntest += 2;
       const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
       const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
@@ -423,44 +600,58 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
                       fminf(fmaxf(a0[2], a1[2]), s.tcur));
         hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
       }
+      const uint32_t s0 = f3.x, s1 = f3.y;
+      uint32_t spec_slot = kLeaf;  // a leaf word: nothing fetched
       if constexpr (CULL != 0) {
         const float d[3] = {s.dx, s.dy, s.dz};
         float sc[2][3];
         if constexpr (SCALES) {
-          const float4 f4 = __ldg(nd + 4), f5 = __ldg(nd + 5);
-          sc[0][0] = f4.x; sc[0][1] = f4.y; sc[0][2] = f4.z;
-          sc[1][0] = f4.w; sc[1][1] = f5.x; sc[1][2] = f5.y;
+          sc[0][0] = rc.f4.x; sc[0][1] = rc.f4.y; sc[0][2] = rc.f4.z;
+          sc[1][0] = rc.f4.w; sc[1][1] = rc.f5.x; sc[1][2] = rc.f5.y;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+              sc[c][k] = scale_of<RR>(c ? lo1[k] : lo0[k], c ? hi1[k] : hi0[k]);
         }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const unsigned meta = c ? f3.w : f3.z;
-          if (!hit[c] || (meta & kMetaFull)) continue;
-          const float* lo = c ? lo1 : lo0;
-          const float* hi = c ? hi1 : hi0;
-          float sk[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            if constexpr (SCALES) {
-              sk[k] = sc[c][k];
-            } else {
-              sk[k] = scale_of<RR>(lo[k], hi[k]);
+        const bool need0 = hit[0] && !(f3.z & kMetaFull);
+        const bool need1 = hit[1] && !(f3.w & kMetaFull);
+        const uint8_t* objs = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4);
+        if constexpr (kSplit) {
+          Lookup<RR, CULL, LUTV> L0, L1;
+          if (need0) lookup_issue<RR, CULL, LUTV, OPT>(p, L0, objs, f3.z, lo0, sc[0], o, d, tn[0], tf[0]);
+          if (need1)
+            lookup_issue<RR, CULL, LUTV, OPT>(p, L1, objs + MB, f3.w, lo1, sc[1], o, d, tn[1], tf[1]);
+          if constexpr (kSpec) {
+            // the child visited next if both survive their tests
+            if (hit[0] || hit[1]) {
+              const int c = (hit[0] && hit[1]) ? (tn[1] < tn[0] ? 1 : 0) : (hit[0] ? 0 : 1);
+              const uint32_t sl = c ? s1 : s0;
+              if (!(sl & kLeaf) && slot_ok(sl, (long long)s.cur, p)) {
+                spec_slot = sl;
+                load_rec<false>(p, sl, s.nx);
+              }
             }
           }
-          hit[c] = cull_test<RR, CULL, LUTV>(
-              p, sh, reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4) + c * MB, meta, lo, sk,
-              o, d, tn[c], tf[c]);
+          if (need0) hit[0] = lookup_result(L0);
+          if (need1) hit[1] = lookup_result(L1);
+        } else {
+          if (need0)
+            hit[0] = cull_test<RR, CULL, LUTV, OPT>(p, sh, objs, f3.z, lo0, sc[0], o, d, tn[0], tf[0]);
+          if (need1)
+            hit[1] =
+                cull_test<RR, CULL, LUTV, OPT>(p, sh, objs + MB, f3.w, lo1, sc[1], o, d, tn[1], tf[1]);
         }
       }
-      const uint32_t s0 = f3.x, s1 = f3.y;
       if ((hit[0] && !slot_ok(s0, (long long)s.cur, p)) ||
           (hit[1] && !slot_ok(s1, (long long)s.cur, p))) {
         atomicOr(p.status, (unsigned)ST_BAD_NODE);
         done = true;
       } else if (hit[0] && hit[1]) {
         const int nr = tn[1] < tn[0] ? 1 : 0;
-        if (s.sp < STACK) {
-          stack[s.sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
-          ++s.sp;
+        if (stack_push<STACK, OPT>(s, stack,
+                                   make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1])))) {
           s.cur = nr ? s1 : s0;
         } else {
           atomicOr(p.status, (unsigned)ST_STACK);
@@ -473,19 +664,27 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
       } else {
         s.have = false;
       }
+      if constexpr (kSpec) s.pre = !(spec_slot & kLeaf) && s.have && s.cur == spec_slot;
     }
   }
   if (!done && !s.have) {
     while (s.sp > 0) {
-      --s.sp;
+      const uint2 e = stack_pop<OPT>(s, stack);
       // same widened bound as the slab test: a child is kept or dropped
       // alike whether it is reached directly or through the stack
-      if (__uint_as_float(stack[s.sp].y) > __fmul_rn(s.tcur, kRobust)) continue;
-      s.cur = stack[s.sp].x;
+      if (__uint_as_float(e.y) > __fmul_rn(s.tcur, kRobust)) continue;
+      s.cur = e.x;
       s.have = true;
       break;
     }
     if (!s.have) done = true;
+  }
+  if constexpr (kSpec) {
+    // the next inner record is requested now, before the loop's bookkeeping
+    if (!done && s.have && !s.pre && !(s.cur & kLeaf) && (long long)s.cur < p.num_nodes) {
+      load_rec<false>(p, s.cur, s.nx);
+      s.pre = true;
+    }
   }
   return done;
 }
@@ -497,9 +696,10 @@ constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 // their culling tests, then the slab-passing children ordered by entry
 // distance (ties by position); the nearest is visited next, the others
 // pushed farthest first.  Counts: node_tests += the node's children.
-template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack>
+template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack, int OPT = 0>
 __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2* stack,
                                             const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
+  static_assert((OPT & (OPT_PAIR | OPT_SPEC | OPT_TOS)) == 0, "binary-step options only");
   constexpr int RR = (R > 0 ? R : 4);
   constexpr int MB = MaskTraits<RR>::kStrideBytes;
   bool done = false;
@@ -585,7 +785,7 @@ __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2*
             const float tnc = c == 0 ? tn[0] : c == 1 ? tn[1] : c == 2 ? tn[2] : tn[3];
             const float tfc = c == 0 ? tf[0] : c == 1 ? tf[1] : c == 2 ? tf[2] : tf[3];
             const unsigned mc = c == 0 ? meta[0] : c == 1 ? meta[1] : c == 2 ? meta[2] : meta[3];
-            if (!cull_test<RR, CULL, LUTV>(p, sh, objs + c * MB, mc, l3, s3, o, d, tnc, tfc)) {
+            if (!cull_test<RR, CULL, LUTV, OPT>(p, sh, objs + c * MB, mc, l3, s3, o, d, tnc, tfc)) {
               if (c == 0) hit[0] = false;
               else if (c == 1) hit[1] = false;
               else if (c == 2) hit[2] = false;
@@ -641,13 +841,13 @@ __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2*
 }
 
 // The step of a trace or wave kernel of the given node width.
-template <int WIDTH, int R, int CULL, int MODE, int LUTV, int SCALES, int STACK>
+template <int WIDTH, int R, int CULL, int MODE, int LUTV, int SCALES, int STACK, int OPT = 0>
 __device__ __forceinline__ bool step_w(const Params& p, RayState& s, uint2* stack,
                                        const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
   if constexpr (WIDTH == 4) {
-    return trace_step4<R, CULL, MODE, LUTV, SCALES, STACK>(p, s, stack, sh);
+    return trace_step4<R, CULL, MODE, LUTV, SCALES, STACK, OPT>(p, s, stack, sh);
   } else {
-    return trace_step<R, CULL, MODE, LUTV, SCALES, STACK>(p, s, stack, sh);
+    return trace_step<R, CULL, MODE, LUTV, SCALES, STACK, OPT>(p, s, stack, sh);
   }
 }
 
@@ -678,7 +878,7 @@ __device__ __forceinline__ long long warp_fetch(bool active, unsigned* counter, 
 // (uncompressed, R = 4 or 6) the R_ray = 2R table in global memory.
 // SCALES: 1 = the per-child Alg. 1 scales R/extent are precomputed in the
 // node record, 0 = divided.
-template <int R, int CULL, int MODE, int LUTV, int SCALES, int WIDTH = 2>
+template <int R, int CULL, int MODE, int LUTV, int SCALES, int WIDTH = 2, int OPT = 0>
 __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
@@ -700,7 +900,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
     }
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
-    if (step_w<WIDTH, R, CULL, MODE, LUTV, SCALES, kStack>(p, s, stack, sh)) {
+    if (step_w<WIDTH, R, CULL, MODE, LUTV, SCALES, kStack, OPT>(p, s, stack, sh)) {
       p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
@@ -727,6 +927,11 @@ enum {
 };
 enum { ST_TIMEOUT = 4 };
 
+// Bounce-queue sort (OPT_SORT): key = direction octant (3 bits) above the
+// Morton code of the origin's cell in a 16^3 grid over the scene box.
+constexpr int kSortCellBits = 4;
+constexpr int kSortBins = 8 << (3 * kSortCellBits);
+
 struct WaveParams {
   Params p;                    // image, status word (p.work = control words), refill
   const float4* rays0;         // primary rays
@@ -734,6 +939,11 @@ struct WaveParams {
   long long chunk;             // primary rays per chunk (the wave size)
   float4* qrays[2];            // bounce-ray queues (scratch), `chunk` rays each
   int* qpath[2];               // path id of each queued ray
+  float4* srays;               // OPT_SORT: sorted queue (scratch), `chunk` rays
+  int* spath;                  //   its path ids
+  unsigned* hist;              //   kSortBins counters / offsets
+  float box_lo[3];             //   scene box lower corner
+  float box_scale[3];          //   2^kSortCellBits / extent per axis
   float4* hits[kMaxWaves];     // per wave: {t, id, u, v}
   int* path[kMaxWaves];        // per wave: path id (primary ray index)
   uint2* counts[kMaxWaves];    // per wave, optional
@@ -780,6 +990,75 @@ __device__ __forceinline__ bool grid_barrier(unsigned* w, unsigned long long tim
   }
   __syncthreads();
   return ok != 0;
+}
+
+__device__ __forceinline__ unsigned sort_key(const float4 a, const float4 b, const WaveParams& wp) {
+  const unsigned oct = (b.x < 0.0f ? 1u : 0u) | (b.y < 0.0f ? 2u : 0u) | (b.z < 0.0f ? 4u : 0u);
+  constexpr int kMax = (1 << kSortCellBits) - 1;
+  const float o[3] = {a.x, a.y, a.z};
+  unsigned c[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int v = __float2int_rz((o[k] - wp.box_lo[k]) * wp.box_scale[k]);
+    c[k] = (unsigned)min(max(v, 0), kMax);
+  }
+  unsigned m = 0;
+#pragma unroll
+  for (int bit = 0; bit < kSortCellBits; ++bit)
+    m |= (((c[0] >> bit) & 1u) << (3 * bit)) | (((c[1] >> bit) & 1u) << (3 * bit + 1)) |
+         (((c[2] >> bit) & 1u) << (3 * bit + 2));
+  return (oct << (3 * kSortCellBits)) | m;
+}
+
+// Counting sort of queue (q, qp) of n rays into (wp.srays, wp.spath) by
+// sort_key, across the whole cooperative grid; wp.hist must be zero on
+// entry.  Three bounded grid barriers; false if one timed out.
+template <int BLOCK>
+__device__ bool sort_queue(const WaveParams& wp, const float4* q, const int* qp, long long n) {
+  const long long tid = (long long)blockIdx.x * BLOCK + threadIdx.x;
+  const long long nth = (long long)gridDim.x * BLOCK;
+  for (long long i = tid; i < n; i += nth)
+    atomicAdd(&wp.hist[sort_key(__ldcg(&q[2 * i]), __ldcg(&q[2 * i + 1]), wp)], 1u);
+  __threadfence();
+  if (!grid_barrier(wp.p.work, wp.timeout_ns)) return false;
+  if (blockIdx.x == 0) {
+    // exclusive scan in place: each thread a contiguous run of bins
+    constexpr int kPer = kSortBins / BLOCK;
+    __shared__ unsigned part[BLOCK];
+    unsigned sum = 0;
+    for (int j = 0; j < kPer; ++j) sum += __ldcg(&wp.hist[threadIdx.x * kPer + j]);
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned acc = 0;
+      for (int t = 0; t < BLOCK; ++t) {
+        const unsigned v = part[t];
+        part[t] = acc;
+        acc += v;
+      }
+    }
+    __syncthreads();
+    unsigned acc = part[threadIdx.x];
+    for (int j = 0; j < kPer; ++j) {
+      unsigned* h = &wp.hist[threadIdx.x * kPer + j];
+      const unsigned v = __ldcg(h);
+      __stcg(h, acc);
+      acc += v;
+    }
+  }
+  __threadfence();
+  if (!grid_barrier(wp.p.work, wp.timeout_ns)) return false;
+  for (long long i = tid; i < n; i += nth) {
+    const float4 a = __ldcg(&q[2 * i]), b = __ldcg(&q[2 * i + 1]);
+    const unsigned pos = atomicAdd(&wp.hist[sort_key(a, b, wp)], 1u);
+    if ((long long)pos < n) {  // always: the offsets of a full count
+      wp.srays[2 * (long long)pos] = a;
+      wp.srays[2 * (long long)pos + 1] = b;
+      wp.spath[pos] = __ldcg(&qp[i]);
+    }
+  }
+  __threadfence();
+  return grid_barrier(wp.p.work, wp.timeout_ns);
 }
 
 // Diffuse bounce ray from a hit (same canonical op sequence as the CPU
@@ -852,7 +1131,7 @@ static __device__ __noinline__ bool make_bounce(float ox, float oy, float oz, fl
 // separates the waves.  Outputs: wave 0 by primary index; wave w >= 1 after
 // the entries of the previous chunks.
 template <int R, int CULL, int LUTV, int SCALES, int BLOCK = kBlock, int STACK = kStack,
-          int WIDTH = 2>
+          int WIDTH = 2, int OPT = 0>
 __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_kernel(WaveParams wp) {
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
@@ -879,6 +1158,20 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
       }
       const float4* rays = (w == 0) ? wp.rays0 + 2 * c0 : wp.qrays[w & 1];
       const int* qpath = (w == 0) ? nullptr : wp.qpath[w & 1];
+      if constexpr ((OPT & OPT_SORT) != 0) {
+        if (w > 0) {
+          if (!sort_queue<BLOCK>(wp, rays, qpath, n)) return;
+          rays = wp.srays;
+          qpath = wp.spath;
+        }
+        if (w < wp.bounces) {
+          // zero the counters for the sort before the next wave (the barrier
+          // at the end of this wave orders it before the count)
+          for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < kSortBins;
+               i += (long long)gridDim.x * BLOCK)
+            wp.hist[i] = 0u;
+        }
+      }
       RayState s;
       s.have = false;
       long long rid = -1;
@@ -894,7 +1187,7 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
         }
         if (!__any_sync(0xffffffffu, active)) break;
         const bool done =
-            active && step_w<WIDTH, R, CULL, 0, LUTV, SCALES, STACK>(p, s, stack, sh);
+            active && step_w<WIDTH, R, CULL, 0, LUTV, SCALES, STACK, OPT>(p, s, stack, sh);
         if (!__any_sync(0xffffffffu, done)) continue;
         bool spawn = false;
         float4 b0, b1;
@@ -970,7 +1263,7 @@ __device__ __forceinline__ bool box_hit(const RayState& s, const float4 b0, cons
 // distant triangle met earlier in traversal order replaces it, and t_max
 // drops to t_s when phase 2 reaches the seed slot: the result is the
 // plain traversal's closest hit.  Counts sum both phases.
-template <int R, int CULL, int LUTV, int SCALES>
+template <int R, int CULL, int LUTV, int SCALES, int OPT = 0>
 __global__ void __launch_bounds__(kBlock) seeded_kernel(Params p, const int* cls,
                                                         const float4* frontier, int nfront) {
   constexpr int RR = (R > 0 ? R : 4);
@@ -1022,7 +1315,7 @@ __global__ void __launch_bounds__(kBlock) seeded_kernel(Params p, const int* cls
       if (s.hid >= 0 && s.hpos == seed_pos) s.tcur = s.ht;  // the seed counts as found here
       s.have = false;
     }
-    if (trace_step<R, CULL, 0, LUTV, SCALES>(p, s, stack, sh)) {
+    if (trace_step<R, CULL, 0, LUTV, SCALES, kStack, OPT>(p, s, stack, sh)) {
       if (phase == 1) {
         phase = 2;
         s.sp = 0;

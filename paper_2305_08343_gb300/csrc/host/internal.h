@@ -132,6 +132,7 @@ struct sc_dbvh {
   uint32_t root_slot = 0;
   int has_root = 0;
   int stack_need = 0;  // max_depth + 1
+  float root_box[6] = {0, 0, 0, 0, 0, 0};  // scene box (lo.xyz, hi.xyz)
 };
 
 struct sc_bvh {

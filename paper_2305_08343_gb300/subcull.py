@@ -70,7 +70,14 @@ SC_MAX_BOUNCES = 4
 class sc_trace_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("lut_mode", C.c_int),
                 ("refill", C.c_int), ("stack", C.c_int), ("wave_chunk", C.c_int64),
-                ("wait_timeout_ns", C.c_int64)]
+                ("wait_timeout_ns", C.c_int64), ("variant", C.c_int)]
+
+
+SC_VARIANT_FUSED_CELLS = 1
+SC_VARIANT_PAIR = 2
+SC_VARIANT_SPEC = 4
+SC_VARIANT_TOS = 8
+SC_VARIANT_SORT = 16
 
 
 class sc_tune_result(C.Structure):
@@ -277,7 +284,14 @@ def sc_l2_probe_blocks() -> int:
 
 def sc_l2_read(buf, reps: int, sink, stream=None):
     """Reads the device tensor `buf` reps times through L2 (see the header);
-    sink: device int64 tensor of >= sc_l2_probe_blocks() entries."""
+    sink: contiguous device int64 / uint64 tensor of >= sc_l2_probe_blocks()
+    entries (each block writes one)."""
+    import torch
+    if (not sink.is_cuda or not sink.is_contiguous()
+            or sink.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64))
+            or sink.numel() < sc_l2_probe_blocks()):
+        raise ValueError("sink must be a contiguous CUDA int64 tensor of at least "
+                         f"{sc_l2_probe_blocks()} entries")
     _check(lib().sc_l2_read(C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(), reps,
                             C.c_void_p(sink.data_ptr()), _stream_ptr(stream)))
 
@@ -355,9 +369,9 @@ def sc_bvh_upload(bvh: Bvh, layout: int, stream=None) -> DeviceBVH:
 
 
 def _opts(block=0, blocks_per_sm=0, lut_mode=SC_LUT_AUTO, refill=0, stack=0, wave_chunk=0,
-          wait_timeout_ns=0):
+          wait_timeout_ns=0, variant=0):
     return sc_trace_opts(block, blocks_per_sm, lut_mode, refill, stack, wave_chunk,
-                         wait_timeout_ns)
+                         wait_timeout_ns, variant)
 
 
 def sc_trace(dbvh: DeviceBVH, rays, hits, counts, mode: int, cull: int, work,
