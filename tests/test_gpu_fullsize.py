@@ -11,7 +11,6 @@ refill and wave chunk).
   - 12.1M hair and the 4M soup: brute force over every triangle: hit t
     bit-identical, hit id identical unless another triangle ties exactly.
 """
-import os
 
 import numpy as np
 import pytest
@@ -171,32 +170,45 @@ def test_soup4m_full_size_closest_and_any_hit():
             assert ok and _bits(np.float32([tt]))[0] == _bits(h[i:i + 1, 0])[0]
 
 
-@pytest.mark.skipif(os.environ.get("SUBCULL_FULL_ORACLE") != "1",
-                    reason="builds the oracle's own 12.1M BVH, masks and LUT (many minutes); "
-                           "set SUBCULL_FULL_ORACLE=1")
 def test_hair12m_full_size_oracle_counts():
-    """12.1M hair with compressed masks, in the bench's wave configuration:
-    sampled primary and first-bounce rays against the oracle's own BVH,
-    masks and compression LUT -- hit id, t and per-ray counts bit-exact."""
+    """12.1M hair with compressed masks, built as the bench builds it (tree
+    and masks on the GPU), in the bench's wave configuration (primary rays
+    and two bounce waves, autotuned): sampled primary, first- and
+    second-bounce rays against the oracle's own BVH, masks and compression
+    LUT (its threaded build) -- bounce rays, hit id, t, u, v and per-ray
+    counts bit-exact."""
     _need_gpu()
     tris = sg.hair(378125, 16, False, seed=4)
     rays = sg.pinhole(1920, 1080)
-    bvh = sc.sc_bvh_build(tris, 6, 1)
-    culled, plain = _tuned_waves(bvh, sc.SC_LAYOUT_MASKED, rays, 1)
+    bvh = sc.sc_bvh_build(tris, 6, 1, gpu_bvh=1, gpu_masks=1)
+    culled, plain = _tuned_waves(bvh, sc.SC_LAYOUT_MASKED, rays, 2)
     _check_culled_equals_plain(culled, plain)
+    del plain
     ob = oracle.OracleBVH(tris).build_masks(6, 3).compress(256, 8)
+
+    def check(w, idx, r):
+        o = ob.trace(r, 0, 2)
+        assert np.array_equal(_bits(w["hits"][idx, 1]), o["id"])
+        assert np.array_equal(_bits(w["hits"][idx, 0]), _bits(o["t"]))
+        assert np.array_equal(_bits(w["hits"][idx, 2:]), _bits(o["uv"]))
+        assert np.array_equal(w["counts"][idx], o["counts"])
+
     w0 = culled[0]
     idx = np.linspace(0, len(rays) - 1, 600).astype(np.int64)
-    o = ob.trace(rays[idx], 0, 2)
-    assert np.array_equal(_bits(w0["hits"][idx, 1]), o["id"])
-    assert np.array_equal(_bits(w0["hits"][idx, 0]), _bits(o["t"]))
-    assert np.array_equal(w0["counts"][idx], o["counts"])
-    w1 = culled[1]
-    pos = np.linspace(0, len(w1["path"]) - 1, 300).astype(np.int64)
-    pid = w1["path"][pos]
-    brays = np.stack([oracle.bounce(rays[p], float(w0["hits"][p, 0]), tris[_bits(w0["hits"][p, 1])],
-                                    SEED, int(p), 1) for p in pid])
-    assert np.array_equal(_bits(brays), _bits(w1["rays"][pos]))
-    ob_ = ob.trace(brays, 0, 2)
-    assert np.array_equal(_bits(w1["hits"][pos, 1]), ob_["id"])
-    assert np.array_equal(w1["counts"][pos], ob_["counts"])
+    check(w0, idx, rays[idx])
+    by_path = [None] + [{int(p): k for k, p in enumerate(culled[w]["path"])} for w in (1, 2)]
+    prev = w0
+    for wave in (1, 2):
+        w = culled[wave]
+        assert len(w["path"]) > 100000
+        pos = np.linspace(0, len(w["path"]) - 1, 300).astype(np.int64)
+        pid = w["path"][pos]
+        # the ray of the previous wave on each sampled path, and its hit
+        k = pid if wave == 1 else np.array([by_path[1][int(p)] for p in pid])
+        src = rays[pid] if wave == 1 else prev["rays"][k]
+        ht, hid = prev["hits"][k, 0], _bits(prev["hits"][k, 1])
+        brays = np.stack([oracle.bounce(src[q], float(ht[q]), tris[hid[q]], SEED, int(pid[q]),
+                                        wave) for q in range(len(pid))])
+        assert np.array_equal(_bits(brays), _bits(w["rays"][pos]))
+        check(w, pos, brays)
+        prev = w

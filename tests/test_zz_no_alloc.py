@@ -6,7 +6,8 @@ device array inside the library instead of a caller workspace.
 Checked through the C-ABI against sc_trace with a caller workspace on the
 same inputs, on two calls in a row (the shared scratch must be cleared by
 each call): hit ids and per-ray test counts exact, t within the 1e-6
-relative tolerance of the other GPU tests.  This file is collected last so
+relative tolerance of the other GPU tests; and the device's free memory does
+not drop over the second call.  This file is collected last so
 that a run stopping at the first failure has run every other test.
 """
 import numpy as np
@@ -37,10 +38,17 @@ def test_noalloc_matches_workspace_trace_twice(cull):
     ref_hits, ref_counts = sc.trace(d, r, sc.SC_CLOSEST, cull)
     torch.cuda.synchronize()
     rt, ri, rc = _split(ref_hits, ref_counts)
+    bufs = [(torch.full((n, 4), -7.0, dtype=torch.float32, device="cuda"),
+             torch.full((n, 2), -7, dtype=torch.int32, device="cuda")) for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):
-        hits = torch.full((n, 4), -7.0, dtype=torch.float32, device="cuda")
-        counts = torch.full((n, 2), -7, dtype=torch.int32, device="cuda")
+        hits, counts = bufs[call]
+        free0 = torch.cuda.mem_get_info()[0]
         sc.sc_trace_noalloc(d, r, hits, counts, sc.SC_CLOSEST, cull)
+        if call == 1:
+            # the first call may load the module and look up the array;
+            # after it, a call takes no device memory at all
+            assert torch.cuda.mem_get_info()[0] >= free0, "the second call allocated"
         t, i, c = _split(hits, counts)
         assert np.array_equal(i, ri), f"call {call}: hit ids differ"
         assert np.array_equal(c, rc), f"call {call}: per-ray counts differ"
