@@ -216,36 +216,48 @@ def measure_l2_peak(dev):
     return best, best_mb
 
 
-def oracle_rays_per_s(ob, tris, rays, cull, threads, budget_s, skip_bits=None, stride=1,
-                      leaf_min=0, width=2):
-    """Times the oracle's traversal (threads split the rays statically) on a
-    sample of rays sized to roughly budget_s seconds of CPU time."""
-    import oracle  # noqa: F401  (the oracle package; CPU baseline only)
+def oracle_waves_per_s(ob, tris, rays, bounces, cull, threads, budget_s, seed, skip_bits=None,
+                       stride=1, leaf_min=0, width=2):
+    """Times the oracle on the GPU arm's work, bounded: an evenly spaced
+    sample of the primary rays and the bounce waves their hits spawn (the
+    oracle's own bounce generator, keyed by path id like the GPU's), sized
+    to roughly budget_s seconds.  Threads split each wave statically; the
+    time covers tracing and bounce generation.  Returns (rays/s, rays traced,
+    primary sample, seconds, per-wave sizes)."""
+    import oracle
     n = rays.shape[0]
-    # calibrate on a small sample
     m = min(n, 512)
     t0 = time.perf_counter()
     ob.trace(rays[:m], 0, cull, skip_bits=skip_bits, stride=stride, leaf_min=leaf_min,
              width=width)
     per_ray = (time.perf_counter() - t0) / m
-    sample = int(min(n, max(threads * 256, budget_s * threads / max(per_ray, 1e-9))))
+    sample = int(min(n, max(threads * 64,
+                            budget_s * threads / max(per_ray * (1 + 0.9 * bounces), 1e-9))))
     idx = np.linspace(0, n - 1, sample).astype(np.int64)
-    sub = np.ascontiguousarray(rays[idx])
-    out = dict(t=np.zeros(sample, np.float32), id=np.zeros(sample, np.int32),
-               uv=np.zeros((sample, 2), np.float32), counts=np.zeros((sample, 2), np.uint32),
-               mask_tests=np.zeros(sample, np.uint32))
-    bounds = np.linspace(0, sample, threads + 1).astype(np.int64)
-    ts = [threading.Thread(target=ob.trace, args=(sub, 0, cull, int(bounds[i]),
-                                                   int(bounds[i + 1]), out, skip_bits, stride,
-                                                   leaf_min, width))
-          for i in range(threads)]
+    cur, path = np.ascontiguousarray(rays[idx]), idx
+    total, sizes = 0, []
     t0 = time.perf_counter()
-    for t in ts:
-        t.start()
-    for t in ts:
-        t.join()
+    for w in range(bounces + 1):
+        k = cur.shape[0]
+        out = dict(t=np.zeros(k, np.float32), id=np.zeros(k, np.int32),
+                   uv=np.zeros((k, 2), np.float32), counts=np.zeros((k, 2), np.uint32),
+                   mask_tests=np.zeros(k, np.uint32))
+        bounds = np.linspace(0, k, threads + 1).astype(np.int64)
+        ts = [threading.Thread(target=ob.trace, args=(cur, 0, cull, int(bounds[i]),
+                                                       int(bounds[i + 1]), out, skip_bits,
+                                                       stride, leaf_min, width))
+              for i in range(threads)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        total += k
+        sizes.append(k)
+        if w < bounces:
+            cur, path = oracle.bounce_wave(cur, out["t"], out["id"], tris, seed, w + 1, path)
+            cur = np.ascontiguousarray(cur, dtype=np.float32)
     dt = time.perf_counter() - t0
-    return sample / dt, sample, dt, out
+    return total / dt, total, sample, dt, sizes
 
 
 def make_inputs(name):
@@ -268,31 +280,38 @@ def run_reference(args):
         return 0
     import oracle
     desc, tris, rays, R, comp = make_inputs(args.workload)
+    bounces = args.bounces if args.bounces >= 0 else WORKLOAD_BOUNCES.get(args.workload, 1)
     threads = cpu_count()
+    t0 = time.perf_counter()
     ob = oracle.OracleBVH(tris).build_masks(R, 3)
     cull = 1
     if comp:
         ob.compress(256, 8)
         cull = 2
+    build_s = time.perf_counter() - t0
     budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_rays_per_s(ob, tris, rays, cull, threads, budget / 4)
-    vals, samples, secs = [], [], []
+        oracle_waves_per_s(ob, tris, rays, bounces, cull, threads, budget / 4, SEED)
+    traced, secs, samples, sizes = [], [], [], None
     for _ in range(args.steps):
-        v, s, dt, _ = oracle_rays_per_s(ob, tris, rays, cull, threads, budget)
-        vals.append(v)
-        samples.append(s)
+        _, tot, samp, dt, sizes = oracle_waves_per_s(ob, tris, rays, bounces, cull, threads,
+                                                     budget, SEED)
+        traced.append(tot)
         secs.append(dt)
-    mrays = float(np.sum(samples) / np.sum(secs) / 1e6)
+        samples.append(samp)
+    mrays = float(np.sum(traced) / np.sum(secs) / 1e6)
+    sample_desc = (f"{int(np.mean(samples))} primary rays per step (evenly spaced over the "
+                   f"{rays.shape[0]}) and the {bounces} bounce wave(s) their hits spawn "
+                   f"(last step's wave sizes {sizes}), culled closest hit; the oracle's own "
+                   f"threaded build ({build_s:.0f} s, untimed)")
     line = {
         "impl": "reference", "metric": METRIC, "value": mrays, "unit": "Mrays/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": float(np.mean(secs) * 1e3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc},
+        "config": {"workload": args.workload, "description": desc, "bounces": bounces},
         "cpu_baseline": {"value": mrays, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{int(np.mean(samples))} primary rays per step (evenly "
-                                   f"spaced over the {rays.shape[0]}), culled closest hit"},
+                         "sample": sample_desc},
         "e2e": {"value": mrays, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -301,6 +320,12 @@ def run_reference(args):
 
 
 METRIC = "Mrays/s closest-hit, culled vs plain, 1 GB300, identical hits; node+tri tests/ray"
+SEED = 2305  # bounce-ray seed of every arm
+
+# Kernel options (sc_trace_opts.variant) of the timed culled and plain wave
+# kernels; neither changes a hit or a count.
+DEFAULT_VARIANT = 0
+DEFAULT_PLAIN_VARIANT = 0
 
 
 # ------------------------------------------------------------------ gb300 --
@@ -323,24 +348,65 @@ def _sorted_waves(bufs, sizes):
 NET_FLOPS_PER_RAY = 2 * (6 * 64 + 64 * 64 + 64 * 256)
 
 
-def run_learned(args, bvh, d_masked, dev, flush, W, H):
-    """Learned proposal against plain culled traversal on held-out rays:
-    train on the GPU (training pairs from the plain traversal of jittered
-    primary rays and their bounce waves), then time [network top-1 + seeded
-    traversal] and [culled traversal] on 2^22 held-out jittered primary
-    rays (other jitter seeds), identical hits asserted."""
+def seeding_upper_bound(lp, d_masked, rays, bounces, dev):
+    """What seeding can gain at best, per wave: node + triangle tests per ray
+    of the culled traversal, and of the seeded traversal given every ray's
+    true class (the frontier subtree of its closest hit; misses unseeded),
+    over one batch of rays and the bounce waves its hits spawn."""
+    import torch
+    from paper_2305_08343_gb300 import subcull as sc
+    n = rays.shape[0]
+    bufs = sc.WaveBuffers(n, bounces, with_counts=True, device=dev, with_rays=True)
+    _, sizes = sc.trace_waves(d_masked, rays, bounces, SEED, 1, bufs)
+    out = {}
+    for w in range(bounces + 1):
+        m = int(sizes[w])
+        if m == 0:
+            continue
+        r = bufs.rays[w][:m].contiguous()
+        hid = bufs.hits[w][:m, 1].contiguous().view(torch.int32)
+        lab = torch.where(hid >= 0, lp.class_of_tri[hid.clamp(min=0).long()].int(),
+                          torch.full_like(hid, -1))
+        cnt = torch.empty((m, 2), dtype=torch.int32, device=dev)
+        hits = lp.trace(d_masked, r, lab, counts=cnt)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(hits.view(torch.int32),
+                                bufs.hits[w][:m].contiguous().view(torch.int32)))
+        culled = bufs.counts[w][:m].double().sum(1).mean().item()
+        seeded = cnt.double().sum(1).mean().item()
+        out[f"wave{w}"] = {"rays": m, "culled_node_plus_tri": culled,
+                           "true_label_node_plus_tri": seeded,
+                           "change": seeded / culled - 1.0, "identical_hits": same}
+    return out
+
+
+def run_learned(args, bvh, d_masked, dev, flush, W, H, bounces):
+    """Learned proposal against culled traversal on held-out rays: first the
+    true-label upper bound per wave (what any seeding could gain); then
+    training on the GPU (pairs from the plain traversal of jittered primary
+    rays, or random rays for the soup, and their bounce waves), then [network
+    top-1 + seeded traversal] and [culled traversal] timed on 2^22 held-out
+    rays (other seeds), identical hits asserted."""
     import torch
 
     from paper_2305_08343_gb300 import learned
+    from paper_2305_08343_gb300 import scenegen as sg
     from paper_2305_08343_gb300 import subcull as sc
+
+    def batch_of_rays(seed):
+        # camera workloads: jittered primary rays; the soup: random rays
+        if H > 0:
+            return learned.primary_rays(W, H, seed, device=dev)
+        return torch.from_numpy(sg.random_rays(W, seed=seed)).to(dev)
 
     t0 = time.perf_counter()
     lp = learned.LearnedProposal(bvh, depth=8, seed=0, device=dev)
+    bounds = seeding_upper_bound(lp, d_masked, batch_of_rays(4242), bounces, dev)
     target = args.learned_pairs
     pairs_r, pairs_l, total, s = [], [], 0, 1
     while total < target and s <= 64:
-        rays = learned.primary_rays(W, H, 1000 + s, device=dev)
-        r, l = lp.collect(d_masked, [rays], bounces=2, seed=77 + s)
+        rays = batch_of_rays(1000 + s)
+        r, l = lp.collect(d_masked, [rays], bounces=bounces, seed=77 + s)
         pairs_r.append(r.clone())
         pairs_l.append(l.clone())
         total += r.shape[0]
@@ -354,8 +420,9 @@ def run_learned(args, bvh, d_masked, dev, flush, W, H):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     n_held = 1 << 22
-    held = torch.cat([learned.primary_rays(W, H, 5 + k, device=dev)
-                      for k in range((n_held + W * H - 1) // (W * H))])[:n_held].contiguous()
+    per = W * max(H, 1)
+    held = torch.cat([batch_of_rays(5 + k)
+                      for k in range((n_held + per - 1) // per)])[:n_held].contiguous()
     n = held.shape[0]
     cls = torch.empty(n, dtype=torch.int32, device=dev)
     hits_s = torch.empty((n, 4), dtype=torch.float32, device=dev)
@@ -365,7 +432,8 @@ def run_learned(args, bvh, d_masked, dev, flush, W, H):
     work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
     out = {"training_pairs": int(tr_r.shape[0]), "train_steps": args.learned_steps,
            "batch": 4096, "final_loss": loss, "collect_s": collect_s, "train_s": train_s,
-           "held_out_rays": n, "frontier": lp.n_frontier}
+           "held_out_rays": n, "frontier": lp.n_frontier,
+           "true_label_upper_bound": bounds}
     stream = torch.cuda.current_stream()
     for min_prob in (0.0, 0.8):
         key = "top1" if min_prob == 0.0 else f"top1_p{min_prob}"
@@ -439,10 +507,10 @@ def run_gpu(args):
         R = args.R
     bounces = args.bounces if args.bounces >= 0 else WORKLOAD_BOUNCES.get(args.workload, 1)
     t0 = time.perf_counter()
+    gpu_build = 0 if args.host_build else 1
     bvh = sc.sc_bvh_build(tris, R, comp, skip_bits=args.skip_bits, L=args.L,
                           test_stride=args.stride, leaf_min_tris=args.leaf_min,
-                          max_leaf=args.max_leaf, gpu_masks=int(args.gpu_masks),
-                          gpu_bvh=int(args.gpu_bvh))
+                          max_leaf=args.max_leaf, gpu_masks=gpu_build, gpu_bvh=gpu_build)
     build_s = time.perf_counter() - t0
     info = bvh.info()
     wide = args.width == 4
@@ -450,8 +518,12 @@ def run_gpu(args):
     d_plain = sc.DeviceBVH(bvh, sc.SC_LAYOUT_PLAIN4 if wide else sc.SC_LAYOUT_PLAIN)
     n = rays_np.shape[0]
     rays = torch.from_numpy(rays_np).to(dev)
-    opts = sc._opts(lut_mode=args.lut, refill=args.refill)
-    seed = 2305
+    opts = sc._opts(lut_mode=args.lut, refill=args.refill,
+                    variant=max(args.variant, 0) if args.variant >= 0 else DEFAULT_VARIANT)
+    opts_plain = sc._opts(lut_mode=args.lut, refill=args.refill,
+                          variant=args.plain_variant if args.plain_variant >= 0
+                          else DEFAULT_PLAIN_VARIANT)
+    seed = SEED
     if args.primary_only:
         # a few single-batch traces (culled, then plain) and nothing else:
         # the command used for ncu captures of trace_kernel
@@ -459,7 +531,7 @@ def run_gpu(args):
         work = torch.empty(sc.sc_trace_workspace_bytes(), dtype=torch.uint8, device=dev)
         for dbvh, cull in ((d_masked, 1), (d_plain, 0)):
             for _ in range(max(1, args.steps)):
-                sc.sc_trace(dbvh, rays, hits, None, 0, cull, work, opts)
+                sc.sc_trace(dbvh, rays, hits, None, 0, cull, work, opts if cull else opts_plain)
         sc.sc_status_poll(work)
         torch.cuda.synchronize()
         print(json.dumps({"primary_only": True, "workload": args.workload, "rays": n}))
@@ -470,7 +542,8 @@ def run_gpu(args):
         # waves_kernel
         for dbvh, cull in ((d_masked, 1), (d_plain, 0)):
             b = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
-            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, b.outs(), b.ws, opts)
+            sc.sc_trace_waves(dbvh, rays, bounces, seed, cull, b.outs(), b.ws,
+                              opts if cull else opts_plain)
             sizes = sc.sc_waves_poll(b.ws, bounces)
             del b
         print(json.dumps({"waves_once": True, "workload": args.workload, "rays": n,
@@ -483,7 +556,7 @@ def run_gpu(args):
     ref_c = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
     ref_p = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
     _, sizes = sc.trace_waves(d_masked, rays, bounces, seed, 1, ref_c, opts)
-    _, sizes_p = sc.trace_waves(d_plain, rays, bounces, seed, 0, ref_p, opts)
+    _, sizes_p = sc.trace_waves(d_plain, rays, bounces, seed, 0, ref_p, opts_plain)
     wc, wpl = _sorted_waves(ref_c, sizes), _sorted_waves(ref_p, sizes_p)
     same = bool(np.array_equal(sizes, sizes_p)) and all(
         torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(wc, wpl))
@@ -511,12 +584,12 @@ def run_gpu(args):
 
     # autotuner: block size, stack depth, refill batch and wave chunk, per variant
     tuned = {}
-    opts_c, opts_p = opts, opts
+    opts_c, opts_p = opts, opts_plain
     if not args.no_autotune:
         t0 = time.perf_counter()
         opts_c, rows_c = sc.sc_autotune_waves(d_masked, rays, bounces, seed, 1, bufs_c, opts, 3,
                                               flush)
-        opts_p, rows_p = sc.sc_autotune_waves(d_plain, rays, bounces, seed, 0, bufs_p, opts, 3,
+        opts_p, rows_p = sc.sc_autotune_waves(d_plain, rays, bounces, seed, 0, bufs_p, opts_plain, 3,
                                               flush)
         pick = lambda o: {"block": o.block, "stack": o.stack, "refill": o.refill,
                           "wave_chunk": int(o.wave_chunk)}
@@ -586,23 +659,25 @@ def run_gpu(args):
     prim = {}
     for name, dbvh, cull in (("culled", d_masked, 1), ("plain", d_plain, 0),
                              ("plain_kernel_on_masked_image", d_masked, 0)):
+        o1 = opts if cull else (opts_plain if dbvh is d_plain else sc._opts(lut_mode=args.lut))
         for _ in range(2):
-            sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, opts)
+            sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, o1)
         flush.zero_()
         ev[0].record(stream)
         for _ in range(3):
-            sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, opts)
+            sc.sc_trace(dbvh, rays, hits1, None, 0, cull, work, o1)
         ev[1].record(stream)
         torch.cuda.synchronize()
         prim[name] = 3 * n / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e6
     anyhit = {}
     if bounces == 0:
         for name, dbvh, cull in (("culled", d_masked, 1), ("plain", d_plain, 0)):
-            sc.sc_trace(dbvh, rays, hits1, None, 1, cull, work, opts)
+            o1 = opts if cull else opts_plain
+            sc.sc_trace(dbvh, rays, hits1, None, 1, cull, work, o1)
             flush.zero_()
             ev[2].record(stream)
             for _ in range(3):
-                sc.sc_trace(dbvh, rays, hits1, None, 1, cull, work, opts)
+                sc.sc_trace(dbvh, rays, hits1, None, 1, cull, work, o1)
             ev[3].record(stream)
             torch.cuda.synchronize()
             anyhit[name] = 3 * n / (ev[2].elapsed_time(ev[3]) * 1e-3) / 1e6
@@ -653,67 +728,97 @@ def run_gpu(args):
            "overlap": "double-buffered: upload i+1 and download i-1 overlap traversal i"}
     sc.sc_waves_poll(bufs2[1].ws, bounces)
 
-    # roofline of the wave kernel: algorithmic bytes per ray (ray 32 + hit 16
-    # + path 4 + node records + 48-B triangles; spawned rays add 32 + 4)
+    # roofline of the wave kernel.  Algorithmic bytes per ray (the method's
+    # own fetches, from the exact per-ray counters): 32 (ray) + 16 (hit) +
+    # node visits x B_node + triangle tests x 48, plus 32 per spawned bounce
+    # ray.  B_node is the method's record: a 64-byte child pair, plus the two
+    # R^3-bit masks when uncompressed (80 / 128 / 192 bytes at R = 4 / 6 / 8);
+    # the image's own records (stored scales, 4-wide layouts) are reported
+    # beside it as record_bytes_per_ray.
     mstride = {4: 8, 6: 32, 8: 64}[R]
+    b_node = 64 + (0 if comp else 2 * mstride)
     if wide:
         # a 4-wide node is made from every binary node at even depth and
         # holds 2 + its inner children: node tests / mean children = visits
-        node_bytes = 176 + (0 if comp else 4 * mstride)
+        rec_bytes = 176 + (0 if comp else 4 * mstride)
         visits = cnt_c[0] / mean_wide_children(bvh)
+        b_node_w = 2 * b_node
     else:
-        node_bytes = (96 if args.layout in (1, 5) else 64) + (0 if comp else 2 * mstride)
+        rec_bytes = (96 if args.layout in (1, 5) else 64) + (0 if comp else 2 * mstride)
         visits = cnt_c[0] / 2.0
+        b_node_w = b_node
     spawned = float(np.sum(sizes[1:])) / rays_per_step
-    b_ray = (32 + 16 + 4 + visits * node_bytes + cnt_c[1] * 48 + spawned * (32 + 4))
+    b_ray = 32 + 16 + visits * b_node_w + cnt_c[1] * 48 + spawned * 32
+    b_ray_rec = 32 + 16 + 4 + visits * rec_bytes + cnt_c[1] * 48 + spawned * (32 + 4)
     per_launch_bytes = b_ray * rays_per_step
     avg_ms = float(np.mean(ms_cull))
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peaks = load_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic, traffic_src = measured_traffic(args.workload)
     if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
             or args.leaf_min or args.L != 3 or args.max_leaf != 4 or wide
-            or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)):
+            or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
+            or opts.variant != DEFAULT_VARIANT):
         traffic, traffic_src = None, None  # measured for the default configuration only
     l2_peak, l2_mb = measure_l2_peak(dev)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
-                "peak_source": "measured" if peaks else "fallback",
-                "bytes_per_ray": b_ray, "kernel": "waves_kernel (culled)",
-                # the scene's BVH may stay in L2: the same bytes against the
-                # measured L2 read bandwidth
+    # The bound: DRAM traffic far below the algorithmic bytes means the
+    # fetched bytes come from L2 (the working set of one frame stays there),
+    # so the L2 read bandwidth is the roofline; HBM otherwise.
+    on_chip = traffic is not None and traffic < 0.25 * per_launch_bytes
+    if traffic is None:
+        bound_basis = ("no DRAM capture of this kernel source: bound taken as HBM; the "
+                       "fraction against L2 is given beside it")
+    elif on_chip:
+        bound_basis = (f"DRAM traffic {traffic / 1e9:.2f} GB per launch is "
+                       f"{100 * traffic / per_launch_bytes:.1f}% of the algorithmic bytes")
+    else:
+        bound_basis = "DRAM traffic is a large part of the algorithmic bytes"
+    bound_l2 = on_chip and bool(l2_peak)
+    peak = l2_peak if bound_l2 else hbm_peak
+    roofline = {"bound": "l2" if bound_l2 else "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": traffic_src, "bound_basis": bound_basis,
+                "peak_source": ("measured (sc_l2_read probe, this run)" if bound_l2 else
+                                ("measured" if peaks else "fallback")),
+                "bytes_per_ray": b_ray, "b_node": b_node, "node_visits_per_ray": visits,
+                "record_bytes_per_ray": b_ray_rec, "record_bytes": rec_bytes,
+                "kernel": "waves_kernel (culled)",
+                "hbm_peak": hbm_peak, "frac_hbm": achieved / hbm_peak,
                 "l2_peak": l2_peak, "frac_l2": achieved / l2_peak if l2_peak else None,
                 "l2_peak_source": f"sc_l2_read probe, best over 16-64 MB resident buffers "
                                   f"({l2_mb} MB), measured in this run"}
 
     learned_out = None
-    if args.learned:
+    if not args.no_learned:
         W, H = WORKLOADS[args.workload][2]
-        if H == 0:
-            learned_out = {"skipped": "the learned proposal is trained on camera rays"}
-        else:
-            d_learn = sc.DeviceBVH(bvh, args.layout) if wide else d_masked  # binary frontier
-            learned_out = run_learned(args, bvh, d_learn, dev, flush, W, H)
+        d_learn = sc.DeviceBVH(bvh, args.layout) if wide else d_masked  # binary frontier
+        learned_out = run_learned(args, bvh, d_learn, dev, flush, W, H, bounces)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
+        t0 = time.perf_counter()
         ob = oracle.OracleBVH(tris).build_masks(R, args.L)
         cull_mode = 1
         if comp:
             ob.compress(256, 8)
             cull_mode = 2
+        ob_s = time.perf_counter() - t0
         thr = cpu_count()
-        v, sample, dt, _ = oracle_rays_per_s(ob, tris, rays_np, cull_mode, thr, 15.0,
-                                             args.skip_bits or R ** 3, args.stride,
-                                             args.leaf_min, args.width)
-        vp, sample_p, dt_p, _ = oracle_rays_per_s(ob, tris, rays_np, 0, thr, 6.0)
+        v, tot, sample, dt, wsz = oracle_waves_per_s(ob, tris, rays_np, bounces, cull_mode, thr,
+                                                     15.0, SEED, args.skip_bits or R ** 3,
+                                                     args.stride, args.leaf_min, args.width)
+        vp, tot_p, sample_p, dt_p, _ = oracle_waves_per_s(ob, tris, rays_np, bounces, 0, thr,
+                                                          6.0, SEED)
         cpu = {"value": v / 1e6, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
-               "sample": f"{sample} primary rays evenly spaced over the {n}, culled closest hit, "
-                         f"{dt:.1f} s on {thr} threads (oracle's own BVH and masks)",
+               "sample": f"{sample} primary rays evenly spaced over the {n} and the bounce "
+                         f"waves they spawn ({wsz} rays), culled closest hit, {dt:.1f} s on "
+                         f"{thr} threads (the oracle's own BVH, masks and LUT, built in "
+                         f"{ob_s:.0f} s untimed)",
                "plain_value": vp / 1e6,
-               "plain_sample": f"{sample_p} primary rays, plain closest hit, {dt_p:.1f} s"}
+               "plain_sample": f"{tot_p} rays ({sample_p} primary + bounces), plain closest "
+                               f"hit, {dt_p:.1f} s"}
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world,
@@ -728,7 +833,8 @@ def run_gpu(args):
                    "skip_bits": args.skip_bits or R ** 3, "test_stride": args.stride,
                    "leaf_min_tris": args.leaf_min, "max_leaf": args.max_leaf,
                    "node_width": args.width,
-                   "gpu_masks": bool(args.gpu_masks), "gpu_bvh": bool(args.gpu_bvh),
+                   "gpu_masks": bool(gpu_build), "gpu_bvh": bool(gpu_build),
+                   "variant": opts.variant, "plain_variant": opts_plain.variant,
                    "cuda_graph": graphs is not None,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -766,7 +872,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="hair1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="hair12m", choices=sorted(WORKLOADS))
     ap.add_argument("--lut", type=int, default=0,
                     help="0 auto, 1 global table, 2 shared, 3 bit table, 4 the R_ray = 2R table")
     ap.add_argument("--layout", type=int, default=1,
@@ -787,17 +893,21 @@ def main():
     ap.add_argument("--max-leaf", type=int, default=4, help="triangles per BVH leaf (1..8)")
     ap.add_argument("--width", type=int, default=2, choices=[2, 4],
                     help="children per node record: 2 (binary) or 4 (4-wide layouts)")
-    ap.add_argument("--gpu-masks", action="store_true",
-                    help="build the object masks on the GPU (same bits as the host build)")
-    ap.add_argument("--gpu-bvh", action="store_true",
-                    help="build the SAH tree on the GPU (the same tree as the host build)")
+    ap.add_argument("--host-build", action="store_true",
+                    help="build the tree and the masks on the host cores instead of the GPU "
+                         "(the same tree and bits)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="kernel options of the culled traversal (SC_VARIANT_* bits; "
+                         "-1: the library's default)")
+    ap.add_argument("--plain-variant", type=int, default=-1,
+                    help="kernel options of the plain traversal (-1: the library's default)")
     ap.add_argument("--leaf-min", type=int, default=0,
                     help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,
                     help="keep children with >= this many mask bits untested (0: R^3)")
-    ap.add_argument("--learned", action="store_true",
-                    help="also train the learned proposal and time it against plain culled "
-                         "traversal on held-out rays")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned proposal (trained on the GPU, then timed against "
+                         "culled traversal on held-out rays)")
     ap.add_argument("--learned-pairs", type=int, default=1 << 24)
     ap.add_argument("--learned-steps", type=int, default=4000)
     args = ap.parse_args()

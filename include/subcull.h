@@ -315,8 +315,15 @@ enum {
   SC_VARIANT_SPEC = 4,         /* the nearer child's record requested before
                                   the culling results arrive                */
   SC_VARIANT_TOS = 8,          /* top stack entry held in registers          */
-  SC_VARIANT_SORT = 16         /* waves: bounce queues sorted by direction
+  SC_VARIANT_SORT = 16,        /* waves: bounce queues sorted by direction
                                   octant and origin cell before tracing     */
+  SC_VARIANT_LAZY = 64,        /* the per-child Alg. 1 scales are fetched only
+                                  for nodes with a child to test            */
+  SC_VARIANT_DEFER = 32        /* compressed masks with the bit table: each
+                                  child's bit-table lookup is issued when the
+                                  child is visited, beside its own fetch
+                                  (its cells still come from the parent's
+                                  slab test); other images ignore the bit    */
 };
 
 /* Workspace bytes sc_trace needs (ray counter and device status word). */
@@ -522,6 +529,17 @@ sc_status sc_mlp_grad(const void* d_wb, const float* d_rays, const int32_t* d_la
 sc_status sc_mlp_adam(float* d_w, void* d_wb, float* d_grad, float* d_m, float* d_v,
                       int step, float lr, float beta1, float beta2, float eps,
                       void* stream);
+/* Minibatch gather for training, shuffled on the device: d_out_rays[i] /
+   d_out_labels[i] <- row perm(start + i) of d_rays (device float[n][8],
+   16-byte aligned) / d_labels (device int32[n]) for i < batch, where perm is
+   a pseudo-random permutation of [0, n) chosen by `key` (a 4-round Feistel
+   network on the smallest domain of an even number of bits holding n, with
+   cycle walking into [0, n)).  Batches start, start + batch, ... of one key
+   cover an epoch without repeats.  SC_ERR_ARG unless 0 <= start and
+   start + batch <= n < 2^31. */
+sc_status sc_mlp_gather(const float* d_rays, const int32_t* d_labels, int64_t n,
+                        uint64_t key, int64_t start, int64_t batch, float* d_out_rays,
+                        int32_t* d_out_labels, void* stream);
 /* Training pairs: appends (ray, class_of_tri[hit id]) of every ray that hit
    to d_out_rays / d_out_labels at position atomicAdd(d_count); at most cap. */
 sc_status sc_mlp_labels(const float* d_rays, const void* d_hits, int64_t n,

@@ -93,7 +93,13 @@ enum : int {
   OPT_TOS = 8,    // the top stack entry is kept in registers
   OPT_SORT = 16,  // waves: each bounce queue is sorted by direction octant and
                   // origin cell before its wave is traced
+  OPT_LAZY = 64,  // the per-child scales are loaded only when a child needs a test
+  OPT_DEFER = 32, // compressed, bit table: a child's culling lookup is issued
+                  // when the child is visited, beside its own fetch (the
+                  // cells still come from the parent's slab test)
 };
+
+constexpr uint32_t kNoTest = 0xFFFFFFFFu;
 
 // floor(q) clamped to [0, R-1]: the saturating float-to-unsigned conversion
 // (cvt.rmi, negatives and NaN to 0) and a min.
@@ -328,6 +334,7 @@ struct RayState {
   bool pre;   // OPT_SPEC: nx holds the record of `cur` (loaded or in flight)
   Rec nx;     // OPT_SPEC: prefetched record (its first four float4)
   uint2 top;  // OPT_TOS: the top stack entry (the array holds the ones below)
+  uint32_t ctest;  // OPT_DEFER: pending test of `cur`: bit-table word index << 5 | bit, or kNoTest
 };
 
 __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const float4 rb,
@@ -348,6 +355,7 @@ __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const flo
   s.cur = p.root_slot;
   s.have = p.has_root != 0;
   s.pre = false;
+  s.ctest = kNoTest;
 }
 
 // Culling test of one child from its record data: Alg. 1 cells of the
@@ -513,6 +521,99 @@ __device__ __forceinline__ bool lookup_result(const Lookup<R, CULL, LUTV>& L) {
   }
 }
 
+// Pops the next entry that would still pass the widened slab test
+// (tn <= tcur * kRobust: a child is kept or dropped alike whether it is
+// reached directly or through the stack).  True when the stack is empty.
+template <int OPT>
+__device__ __forceinline__ bool pop_next(RayState& s, uint2* stack, uint32_t* tstack) {
+  while (s.sp > 0) {
+    const uint2 e = stack_pop<OPT>(s, stack);
+    if (__uint_as_float(e.y) > __fmul_rn(s.tcur, kRobust)) continue;
+    s.cur = e.x;
+    if constexpr ((OPT & OPT_DEFER) != 0) s.ctest = tstack[s.sp];
+    s.have = true;
+    return false;
+  }
+  return true;
+}
+
+// The inner-node visit of the deferred variant (compressed masks, bit
+// table, stored scales): the two slab tests, and for each slab-passing
+// child that needs a culling test its bit-table word index and bit (from
+// Alg. 1 cells of its clipped segment, computed now), carried with the
+// child to its visit; then the near-first order of trace_step.  Node tests
+// are counted here, so a child culled at its visit is counted as never
+// visited.  Returns true when the ray has finished.
+template <int R, int STACK>
+__device__ __forceinline__ bool trace_inner_deferred(const Params& p, RayState& s, uint2* stack,
+                                                     uint32_t* tstack, const float4* nd,
+                                                     const Rec& rc) {
+  constexpr int R3 = R * R * R;
+  const float4 f0 = rc.f0, f1 = rc.f1, f2 = rc.f2;
+  const uint32_t s0 = __float_as_uint(rc.f3.x), s1 = __float_as_uint(rc.f3.y);
+  const uint32_t m0 = __float_as_uint(rc.f3.z), m1 = __float_as_uint(rc.f3.w);
+  s.ntest += 2;
+  const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
+  const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
+  const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+  const float d[3] = {s.dx, s.dy, s.dz};
+  const float sc0[3] = {rc.f4.x, rc.f4.y, rc.f4.z}, sc1[3] = {rc.f4.w, rc.f5.x, rc.f5.y};
+  float tn[2], tf[2];
+  bool hit[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float* lo = c ? lo1 : lo0;
+    const float* hi = c ? hi1 : hi0;
+    float a0[3], a1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
+      a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
+    }
+    tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
+                  fmaxf(fminf(a0[2], a1[2]), s.tmin));
+    tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
+                  fminf(fmaxf(a0[2], a1[2]), s.tcur));
+    hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
+  }
+  uint32_t code[2] = {kNoTest, kNoTest};
+  if (hit[0] && !(m0 & kMetaFull)) {
+    const int2 be = cell_pair<R, 0>(o, d, lo0, sc0, tn[0], tf[0]);
+    const uint32_t j = m0 & 0xFFu;
+    code[0] = ((uint32_t)(be.x * R3 + be.y) * 8u + (j >> 5)) << 5 | (j & 31u);
+  }
+  if (hit[1] && !(m1 & kMetaFull)) {
+    const int2 be = cell_pair<R, 0>(o, d, lo1, sc1, tn[1], tf[1]);
+    const uint32_t j = m1 & 0xFFu;
+    code[1] = ((uint32_t)(be.x * R3 + be.y) * 8u + (j >> 5)) << 5 | (j & 31u);
+  }
+  if ((hit[0] && !slot_ok(s0, (long long)s.cur, p)) ||
+      (hit[1] && !slot_ok(s1, (long long)s.cur, p))) {
+    atomicOr(p.status, (unsigned)ST_BAD_NODE);
+    return true;
+  }
+  if (hit[0] && hit[1]) {
+    const int nr = tn[1] < tn[0] ? 1 : 0;
+    if (s.sp >= STACK) {
+      atomicOr(p.status, (unsigned)ST_STACK);
+      return true;
+    }
+    stack[s.sp] = make_uint2(nr ? s0 : s1, __float_as_uint(nr ? tn[0] : tn[1]));
+    tstack[s.sp] = nr ? code[0] : code[1];
+    ++s.sp;
+    s.cur = nr ? s1 : s0;
+    s.ctest = nr ? code[1] : code[0];
+    return false;
+  }
+  if (hit[0] || hit[1]) {
+    s.cur = hit[0] ? s0 : s1;
+    s.ctest = hit[0] ? code[0] : code[1];
+    return false;
+  }
+  s.have = false;
+  return pop_next<OPT_DEFER>(s, stack, tstack);
+}
+
 // One traversal step of one ray: either the triangles of one leaf or one
 // inner node, then a pop if nothing is left to visit.  Returns true when the
 // ray has finished (or was stopped by a recorded device error).  The OPT
@@ -520,14 +621,64 @@ __device__ __forceinline__ bool lookup_result(const Lookup<R, CULL, LUTV>& L) {
 // lives, never which nodes are visited.
 template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack, int OPT = 0>
 __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* stack,
-                                           const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
+                                           const SharedTables<(R > 0 ? R : 4), LUTV>& sh,
+                                           uint32_t* tstack = nullptr) {
   constexpr int RR = (R > 0 ? R : 4);
   constexpr int MB = MaskTraits<RR>::kStrideBytes;
   constexpr bool kScaled = CULL != 0 && SCALES != 0;
   constexpr bool kSpec = (OPT & OPT_SPEC) != 0;
   constexpr bool kSplit = CULL != 0 && (LUTV == 2 || (LUTV == 0 && RR <= 6)) &&
                           (OPT & (OPT_PAIR | OPT_SPEC)) != 0;
+  constexpr bool kDefer = (OPT & OPT_DEFER) != 0;
+  static_assert(!kDefer || (CULL == 2 && LUTV == 2 && kTrisPerStep == 1 &&
+                            (OPT & (OPT_PAIR | OPT_SPEC | OPT_TOS)) == 0),
+                "the deferred test is built for the compressed bit table alone");
   bool done = false;
+  if constexpr (kDefer) {
+    // the pending culling test of the slot about to be visited: its
+    // bit-table word is requested beside the slot's own fetch; a culled
+    // slot is left without a test count, as if its parent had culled it
+    if (s.have && s.ctest != kNoTest) {
+      const uint32_t code = s.ctest;
+      s.ctest = kNoTest;
+      const uint32_t word = __ldg(p.bits + (code >> 5));
+      if (s.cur & kLeaf) {
+        const float4* tp = p.tris + 3 * (long long)(s.cur & 0x0FFFFFFFu);
+        const float4 A = __ldg(tp), E1 = __ldg(tp + 1), E2 = __ldg(tp + 2);
+        if (!((word >> (code & 31u)) & 1u)) {
+          s.have = false;
+        } else {
+          const int first = (int)(s.cur & 0x0FFFFFFFu);
+          const int left = (int)((s.cur >> 28) & 7u) + 1;
+          ++s.ttest;
+          float t, u, v;
+          if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
+            s.ht = t;
+            s.hu = u;
+            s.hv = v;
+            s.hid = __float_as_int(A.w);
+            s.hpos = first;
+            if (MODE == 1) return true;
+            s.tcur = t;
+          }
+          if (left > 1) {
+            s.cur = kLeaf | ((uint32_t)(left - 2) << 28) | (uint32_t)(first + 1);
+            return false;
+          }
+          s.have = false;
+        }
+      } else {
+        const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
+        Rec rc;
+        load_rec<true>(p, s.cur, rc);
+        if (!((word >> (code & 31u)) & 1u)) {
+          s.have = false;
+        } else {
+          return trace_inner_deferred<RR, STACK>(p, s, stack, tstack, nd, rc);
+        }
+      }
+    }
+  }
   if (s.have) {
     if (s.cur & kLeaf) {
       const int first = (int)(s.cur & 0x0FFFFFFFu);
@@ -559,6 +710,11 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
       } else {
         s.have = false;
       }
+    } else if constexpr (kDefer) {
+      const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
+      Rec rc;
+      load_rec<true>(p, s.cur, rc);
+      return trace_inner_deferred<RR, STACK>(p, s, stack, tstack, nd, rc);
     } else {
       const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
       Rec rc;
@@ -573,7 +729,7 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
         }
         s.pre = false;
       } else {
-        load_rec<kScaled>(p, s.cur, rc);
+        load_rec<kScaled && (OPT & OPT_LAZY) == 0>(p, s.cur, rc);
       }
       const float4 f0 = rc.f0, f1 = rc.f1, f2 = rc.f2;
       const uint4 f3 = make_uint4(__float_as_uint(rc.f3.x), __float_as_uint(rc.f3.y),
@@ -604,6 +760,14 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
       uint32_t spec_slot = kLeaf;  // a leaf word: nothing fetched
       if constexpr (CULL != 0) {
         const float d[3] = {s.dx, s.dy, s.dz};
+        const bool need0 = hit[0] && !(f3.z & kMetaFull);
+        const bool need1 = hit[1] && !(f3.w & kMetaFull);
+        if constexpr (kScaled && !kSpec && (OPT & OPT_LAZY) != 0) {
+          if (need0 || need1) {
+            rc.f4 = __ldg(nd + 4);
+            rc.f5 = __ldg(nd + 5);
+          }
+        }
         float sc[2][3];
         if constexpr (SCALES) {
           sc[0][0] = rc.f4.x; sc[0][1] = rc.f4.y; sc[0][2] = rc.f4.z;
@@ -615,8 +779,6 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
             for (int k = 0; k < 3; ++k)
               sc[c][k] = scale_of<RR>(c ? lo1[k] : lo0[k], c ? hi1[k] : hi0[k]);
         }
-        const bool need0 = hit[0] && !(f3.z & kMetaFull);
-        const bool need1 = hit[1] && !(f3.w & kMetaFull);
         const uint8_t* objs = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4);
         if constexpr (kSplit) {
           Lookup<RR, CULL, LUTV> L0, L1;
@@ -667,18 +829,7 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
       if constexpr (kSpec) s.pre = !(spec_slot & kLeaf) && s.have && s.cur == spec_slot;
     }
   }
-  if (!done && !s.have) {
-    while (s.sp > 0) {
-      const uint2 e = stack_pop<OPT>(s, stack);
-      // same widened bound as the slab test: a child is kept or dropped
-      // alike whether it is reached directly or through the stack
-      if (__uint_as_float(e.y) > __fmul_rn(s.tcur, kRobust)) continue;
-      s.cur = e.x;
-      s.have = true;
-      break;
-    }
-    if (!s.have) done = true;
-  }
+  if (!done && !s.have) done = pop_next<OPT>(s, stack, tstack);
   if constexpr (kSpec) {
     // the next inner record is requested now, before the loop's bookkeeping
     if (!done && s.have && !s.pre && !(s.cur & kLeaf) && (long long)s.cur < p.num_nodes) {
@@ -843,11 +994,12 @@ __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2*
 // The step of a trace or wave kernel of the given node width.
 template <int WIDTH, int R, int CULL, int MODE, int LUTV, int SCALES, int STACK, int OPT = 0>
 __device__ __forceinline__ bool step_w(const Params& p, RayState& s, uint2* stack,
-                                       const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
+                                       const SharedTables<(R > 0 ? R : 4), LUTV>& sh,
+                                       uint32_t* tstack) {
   if constexpr (WIDTH == 4) {
     return trace_step4<R, CULL, MODE, LUTV, SCALES, STACK, OPT>(p, s, stack, sh);
   } else {
-    return trace_step<R, CULL, MODE, LUTV, SCALES, STACK, OPT>(p, s, stack, sh);
+    return trace_step<R, CULL, MODE, LUTV, SCALES, STACK, OPT>(p, s, stack, sh, tstack);
   }
 }
 
@@ -887,6 +1039,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
     __syncthreads();
   }
   uint2 stack[kStack];
+  uint32_t tstack[(OPT & OPT_DEFER) ? kStack : 1];
   RayState s;
   s.have = false;
   long long rid = -1;
@@ -900,7 +1053,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
     }
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
-    if (step_w<WIDTH, R, CULL, MODE, LUTV, SCALES, kStack, OPT>(p, s, stack, sh)) {
+    if (step_w<WIDTH, R, CULL, MODE, LUTV, SCALES, kStack, OPT>(p, s, stack, sh, tstack)) {
       p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
@@ -1144,6 +1297,7 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
   if (blockIdx.x == 0 && threadIdx.x == 0)
     p.work[WW_NCHUNKS] = (unsigned)((wp.n0 + wp.chunk - 1) / wp.chunk);
   uint2 stack[STACK];
+  uint32_t tstack[(OPT & OPT_DEFER) ? STACK : 1];
   long long ci = 0;
   for (long long c0 = 0; c0 < wp.n0; c0 += wp.chunk, ++ci) {
     unsigned* cw = p.work + WW_HEAD + WW_CHUNK_WORDS * ci;
@@ -1187,7 +1341,7 @@ __global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_
         }
         if (!__any_sync(0xffffffffu, active)) break;
         const bool done =
-            active && step_w<WIDTH, R, CULL, 0, LUTV, SCALES, STACK, OPT>(p, s, stack, sh);
+            active && step_w<WIDTH, R, CULL, 0, LUTV, SCALES, STACK, OPT>(p, s, stack, sh, tstack);
         if (!__any_sync(0xffffffffu, done)) continue;
         bool spawn = false;
         float4 b0, b1;

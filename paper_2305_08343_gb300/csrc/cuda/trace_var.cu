@@ -22,7 +22,8 @@ WaveKernelFn waves_of() {
 // The option sets built here.
 #define SCT_OPTS(X)                                                                   \
   X(OPT_FUSED) X(OPT_PAIR) X(OPT_SPEC) X(OPT_TOS) X(OPT_SPEC | OPT_TOS) X(OPT_SORT) \
-  X(OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_FUSED | OPT_SPEC | OPT_TOS | OPT_SORT)
+  X(OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_FUSED | OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_DEFER) \
+  X(OPT_LAZY)
 
 }  // namespace
 
@@ -38,8 +39,8 @@ bool var_supported(int opt) {
 KernelFn get_kernel_var(int R, int cull, int mode, int lutv, int opt) {
 #define SCT_CASE(O)                                                        \
   if (opt == (O)) {                                                        \
-    if (R == 0) return kernel_of<0, 0, 0, 0, (O)>(mode);                   \
-    if (cull == 1 && lutv == 0) return kernel_of<6, 1, 0, 1, (O)>(mode);   \
+    if (R == 0) return kernel_of<0, 0, 0, 0, (O) & ~OPT_DEFER>(mode);      \
+    if (cull == 1 && lutv == 0) return kernel_of<6, 1, 0, 1, (O) & ~OPT_DEFER>(mode); \
     if (cull == 2 && lutv == 2) return kernel_of<6, 2, 2, 1, (O)>(mode);   \
     return nullptr;                                                        \
   }
@@ -51,8 +52,8 @@ KernelFn get_kernel_var(int R, int cull, int mode, int lutv, int opt) {
 WaveKernelFn get_waves_var(int R, int cull, int lutv, int opt) {
 #define SCT_CASE(O)                                                   \
   if (opt == (O)) {                                                   \
-    if (R == 0) return waves_of<0, 0, 0, 0, (O)>();                   \
-    if (cull == 1 && lutv == 0) return waves_of<6, 1, 0, 1, (O)>();   \
+    if (R == 0) return waves_of<0, 0, 0, 0, (O) & ~OPT_DEFER>();      \
+    if (cull == 1 && lutv == 0) return waves_of<6, 1, 0, 1, (O) & ~OPT_DEFER>(); \
     if (cull == 2 && lutv == 2) return waves_of<6, 2, 2, 1, (O)>();   \
     return nullptr;                                                   \
   }

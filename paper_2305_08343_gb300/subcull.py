@@ -78,6 +78,8 @@ SC_VARIANT_PAIR = 2
 SC_VARIANT_SPEC = 4
 SC_VARIANT_TOS = 8
 SC_VARIANT_SORT = 16
+SC_VARIANT_DEFER = 32
+SC_VARIANT_LAZY = 64
 
 
 class sc_tune_result(C.Structure):
@@ -148,6 +150,7 @@ def lib():
             "sc_mlp_adam": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float,
                                       C.c_float, C.c_float, vp]),
             "sc_mlp_labels": (C.c_int, [vp, vp, i64, vp, vp, vp, vp, i64, vp]),
+            "sc_mlp_gather": (C.c_int, [vp, vp, i64, C.c_uint64, i64, i64, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -612,6 +615,16 @@ def sc_mlp_adam(w, wb, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999,
                              C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
                              C.c_void_p(v.data_ptr()), step, lr, beta1, beta2, eps,
                              _stream_ptr(stream)))
+
+
+def sc_mlp_gather(rays, labels, key: int, start: int, batch: int, out_rays, out_labels,
+                  stream=None):
+    """Rows perm(start .. start+batch-1) of (rays, labels) under the
+    permutation of [0, n) chosen by key (see the header)."""
+    _check(lib().sc_mlp_gather(C.c_void_p(rays.data_ptr()), C.c_void_p(labels.data_ptr()),
+                               rays.shape[0], int(key) & 0xFFFFFFFFFFFFFFFF, start, batch,
+                               C.c_void_p(out_rays.data_ptr()), C.c_void_p(out_labels.data_ptr()),
+                               _stream_ptr(stream)))
 
 
 def sc_mlp_labels(rays, hits, class_of_tri, out_rays, out_labels, count, stream=None):

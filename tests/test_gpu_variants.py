@@ -18,9 +18,9 @@ from paper_2305_08343_gb300 import subcull as sc
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-F, P, S, T, O = (sc.SC_VARIANT_FUSED_CELLS, sc.SC_VARIANT_PAIR, sc.SC_VARIANT_SPEC,
-                 sc.SC_VARIANT_TOS, sc.SC_VARIANT_SORT)
-VARIANTS = [F, P, S, T, S | T, O, S | T | O, F | S | T | O]
+F, P, S, T, O, D = (sc.SC_VARIANT_FUSED_CELLS, sc.SC_VARIANT_PAIR, sc.SC_VARIANT_SPEC,
+                    sc.SC_VARIANT_TOS, sc.SC_VARIANT_SORT, sc.SC_VARIANT_DEFER)
+VARIANTS = [F, P, S, T, S | T, O, S | T | O, F | S | T | O, D, sc.SC_VARIANT_LAZY]
 # (cull mode of the oracle, compressed, lookup)
 CONFIGS = [(2, 1, sc.SC_LUT_BITTABLE), (1, 0, sc.SC_LUT_GLOBAL), (0, 0, sc.SC_LUT_AUTO)]
 
