@@ -323,6 +323,45 @@ __global__ void labels_kernel(const float4* rays, const float4* hits, long long 
   }
 }
 
+// Minibatch gather through a pseudo-random permutation of [0, n) (device
+// shuffling for training): a 4-round Feistel network on the smallest
+// domain of 2h bits that holds n, with cycle walking (Black & Rogaway,
+// "Ciphers with arbitrary finite domains", 2002): a value outside [0, n)
+// is permuted again until it falls inside, which ends because the walk
+// follows the cycle of the start value.
+__device__ __forceinline__ uint32_t feistel_round(uint32_t x, uint32_t k) {
+  uint32_t v = (x ^ k) * 0x9E3779B1u;
+  v ^= v >> 15;
+  v *= 0x85EBCA77u;
+  v ^= v >> 13;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int h, const uint32_t* key) {
+  const uint32_t mask = (h >= 32) ? 0xFFFFFFFFu : ((1u << h) - 1u);
+  uint32_t L = x >> h, R = x & mask;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint32_t t = R;
+    R = (L ^ feistel_round(R, key[r])) & mask;
+    L = t;
+  }
+  return (L << h) | R;
+}
+
+__global__ void gather_kernel(const float4* rays, const int* labels, long long n, int h,
+                              uint4 key, long long start, long long batch, float4* out_rays,
+                              int* out_labels) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  const uint32_t k[4] = {key.x, key.y, key.z, key.w};
+  uint32_t y = feistel((uint32_t)(start + i), h, k);
+  while ((long long)y >= n) y = feistel(y, h, k);
+  out_rays[2 * i] = rays[2 * (long long)y];
+  out_rays[2 * i + 1] = rays[2 * (long long)y + 1];
+  out_labels[i] = labels[y];
+}
+
 // ------------------------------------------------ tensor-core inference --
 // Layers 2 and 3 of the forward pass on the 5th-generation tensor cores:
 // per tile of 128 rays, tcgen05.mma (kind::f16, BF16 operands from shared
@@ -739,6 +778,39 @@ sc_status sc_mlp_adam(float* d_w, void* d_wb, float* d_grad, float* d_m, float* 
   mlpk::adam_kernel<<<(mlpk::P + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       d_w, reinterpret_cast<__nv_bfloat16*>(d_wb), d_grad, d_m, d_v, lr, beta1, beta2, eps, bc1,
       bc2);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_gather(const float* d_rays, const int32_t* d_labels, int64_t n, uint64_t key,
+                        int64_t start, int64_t batch, float* d_out_rays, int32_t* d_out_labels,
+                        void* stream) {
+  SC_TRY
+  if (n < 1 || n > (int64_t)0x7FFFFFFF || start < 0 || batch < 0 || start + batch > n)
+    fail(SC_ERR_ARG, "sc_mlp_gather: need 0 <= start, start + batch <= n < 2^31");
+  if (batch > 0 && (!d_rays || !d_labels || !d_out_rays || !d_out_labels))
+    fail(SC_ERR_ARG, "sc_mlp_gather: NULL buffer");
+  if ((reinterpret_cast<uintptr_t>(d_rays) & 15) || (reinterpret_cast<uintptr_t>(d_out_rays) & 15))
+    fail(SC_ERR_ARG, "sc_mlp_gather: rays must be 16-byte aligned");
+  if (batch == 0) return SC_OK;
+  int bits = 1;
+  while (bits < 31 && (int64_t(1) << bits) < n) ++bits;
+  const int h = (bits + 1) / 2;
+  // four round keys from the 64-bit key (SplitMix64 steps)
+  uint64_t z = key;
+  uint32_t k[4];
+  for (int r = 0; r < 4; ++r) {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    k[r] = (uint32_t)(x ^ (x >> 31));
+  }
+  mlpk::gather_kernel<<<(unsigned)((batch + 255) / 256), 256, 0,
+                        reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float4*>(d_rays), d_labels, n, h, make_uint4(k[0], k[1], k[2], k[3]),
+      start, batch, reinterpret_cast<float4*>(d_out_rays), d_out_labels);
   CUDA_OK(cudaGetLastError());
   return SC_OK;
   SC_CATCH

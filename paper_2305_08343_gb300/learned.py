@@ -3,15 +3,17 @@ subtree most likely to hold its closest hit (not in the paper).
 
 Everything that computes runs in this package's CUDA kernels behind the
 C-ABI (``sc_mlp_*``, ``sc_trace_waves``, ``sc_trace_seeded``); torch only
-owns the device buffers and numpy only shuffles and initialises on the host.
+owns the device buffers, and numpy only draws the initial weights and the
+per-epoch shuffle keys on the host.
 
 Pipeline:
   1. ``collect``: jittered primary rays and their diffuse bounce waves are
      traced by the plain (exact) traversal; every ray that hits becomes a
      training pair (ray, frontier index of the hit triangle's subtree).
      Misses are left out.
-  2. ``fit``: Adam on the mean cross-entropy over shuffled minibatches
-     (FP32 master weights, BF16 copy for the kernels).
+  2. ``fit``: Adam on the mean cross-entropy over minibatches gathered on
+     the device through a per-epoch permutation (FP32 master weights, BF16
+     copy for the kernels).
   3. ``predict`` / ``trace``: top-1 subtree per ray, then the seeded
      traversal, whose hits are bit-identical to the plain traversal's.
 """
@@ -99,9 +101,10 @@ class LearnedProposal:
     # -------------------------------------------------------- training --
     def fit(self, rays, labels, steps: int, batch: int = 4096, lr: float = 2e-3,
             seed: int = 0, log_every: int = 0):
-        """`steps` Adam steps over minibatches of a host-shuffled copy of the
-        pairs (reshuffled every epoch); warm-up then cosine learning rate.
-        Returns the mean loss of the last min(steps, 50) steps."""
+        """`steps` Adam steps over minibatches drawn on the device through a
+        new pseudo-random permutation of the pairs every epoch
+        (sc_mlp_gather); warm-up then cosine learning rate.  Returns the mean
+        loss of the last min(steps, 50) steps."""
         import torch
         n = int(rays.shape[0])
         if n == 0:
@@ -110,18 +113,19 @@ class LearnedProposal:
         ws = torch.empty(sc.sc_mlp_train_workspace_bytes(batch), dtype=torch.uint8,
                          device=self.device)
         rng = np.random.default_rng(seed)
-        h_r, h_l = rays.cpu().numpy(), labels.cpu().numpy()
+        rays = rays.contiguous()
+        labels = labels.contiguous()
+        br = torch.empty((batch, 8), dtype=torch.float32, device=self.device)
+        bl = torch.empty(batch, dtype=torch.int32, device=self.device)
         losses = torch.zeros(steps, dtype=torch.float32, device=self.device)
-        d_r = d_l = None
+        key = 0
         pos = n
         warm = max(1, steps // 20)
         for it in range(steps):
             if pos + batch > n:
-                perm = rng.permutation(n)
-                d_r = torch.from_numpy(h_r[perm]).to(self.device)
-                d_l = torch.from_numpy(h_l[perm]).to(self.device)
+                key = int(rng.integers(0, 2 ** 63))
                 pos = 0
-            br, bl = d_r[pos:pos + batch], d_l[pos:pos + batch]
+            sc.sc_mlp_gather(rays, labels, key, pos, batch, br, bl)
             pos += batch
             sc.sc_mlp_grad(self.wb, br, bl, self.box, self.grad, self.loss, ws)
             losses[it:it + 1].copy_(self.loss)
