@@ -577,6 +577,7 @@ def run_gpu(args):
 
     pct_c, pct_p = pct(cat_c), pct(cat_p)
     rays_per_step = int(np.sum(sizes))
+    hit_ref_c = [x[1].clone() for x in wc]
     del ref_c, ref_p, wc, wpl, cat_c, cat_p
 
     bufs_c = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
@@ -789,6 +790,46 @@ def run_gpu(args):
                 "l2_peak_source": f"sc_l2_read probe, best over 16-64 MB resident buffers "
                                   f"({l2_mb} MB), measured in this run"}
 
+    # Test selection (an option beside the paper's method, which tests
+    # every child): children whose decoded mask has at least skip_bits bits
+    # set are kept untested.  Same hits; counts between the fully tested
+    # culled traversal's and plain's (the oracle applies the same rule).
+    tuned_policy = None
+    if not args.no_policy and not wide and args.skip_bits == 0:
+        kbits = max(1, (R ** 3 * 5) // 9)  # 120 of 216 bits at R = 6
+        bvh_t = sc.sc_bvh_build(tris, R, comp, skip_bits=kbits, L=args.L, max_leaf=args.max_leaf,
+                                gpu_masks=gpu_build, gpu_bvh=gpu_build)
+        d_t = sc.DeviceBVH(bvh_t, args.layout)
+        ref_t = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
+        _, sizes_t = sc.trace_waves(d_t, rays, bounces, seed, 1, ref_t, opts)
+        wt = _sorted_waves(ref_t, sizes_t)
+        same_t = bool(np.array_equal(sizes_t, sizes))
+        cnt_t = torch.cat([x[2] for x in wt]).double().mean(0).tolist()
+        del ref_t
+        bufs_t = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
+        opts_t, _ = sc.sc_autotune_waves(d_t, rays, bounces, seed, 1, bufs_t, opts, 3, flush)
+        ms_t = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sc.sc_trace_waves(d_t, rays, bounces, seed, 1, bufs_t.outs(), bufs_t.ws, opts_t)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                ms_t.append(e0.elapsed_time(e1))
+        sc.sc_waves_poll(bufs_t.ws, bounces)
+        hits_t = [x[1] for x in wt]
+        same_t = same_t and all(torch.equal(a, b) for a, b in zip(hits_t, hit_ref_c))
+        v_t = rays_per_step * len(ms_t) / (float(np.sum(ms_t)) * 1e-3) / 1e6
+        tuned_policy = {"skip_bits": kbits, "mrays_s": v_t, "speedup_vs_plain": v_t / plain_value,
+                        "identical_hits": same_t,
+                        "tests_per_ray": {"node": cnt_t[0], "tri": cnt_t[1],
+                                          "node_plus_tri": cnt_t[0] + cnt_t[1]},
+                        "note": "children whose decoded mask has >= skip_bits of R^3 bits set "
+                                "are kept untested (not the paper's policy)"}
+        del d_t, bvh_t, bufs_t, wt
+
     learned_out = None
     if not args.no_learned:
         W, H = WORKLOADS[args.workload][2]
@@ -851,7 +892,7 @@ def run_gpu(args):
                                     **{k: {a: float(b) for a, b in v.items()}
                                        for k, v in pct_p.items()}}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "learned_proposal": learned_out,
+        "learned_proposal": learned_out, "culled_dense_masks_untested": tuned_policy,
         "gpu_launches": args.steps,
         "build_s": build_s, "bvh": {"nodes": info.num_nodes, "max_depth": info.max_depth,
                                     "ms_bvh": info.ms_bvh, "ms_masks": info.ms_masks,
@@ -905,6 +946,8 @@ def main():
                     help="keep leaf children with fewer triangles untested (0: test all)")
     ap.add_argument("--skip-bits", type=int, default=0,
                     help="keep children with >= this many mask bits untested (0: R^3)")
+    ap.add_argument("--no-policy", action="store_true",
+                    help="skip the culled run with dense masks kept untested")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned proposal (trained on the GPU, then timed against "
                          "culled traversal on held-out rays)")
