@@ -524,6 +524,20 @@ size_t sc_mlp_train_workspace_bytes(int64_t batch);
 sc_status sc_mlp_grad(const void* d_wb, const float* d_rays, const int32_t* d_labels,
                       int64_t batch, const float* d_box, float* d_grad, float* d_loss,
                       void* d_ws, size_t ws_bytes, void* stream);
+/* The same gradient and loss with the contractions on the tensor cores
+   (tcgen05, BF16 operands, FP32 accumulation in tensor memory): the
+   forward's layers 2 and 3 (hidden activations rounded to BF16, as in
+   sc_mlp_forward_tc), the weight gradients dW += dA^T H over split-K batch
+   slices (with a column of ones for the bias gradient), and the hidden
+   backward (dA W) * gelu'(A).  Every operand of a product is rounded to BF16
+   (dZ, dA, the activations and features); softmax, GELU and its derivative
+   run in FP32.  d_status: device uint32 that the caller zeroes; a call ORs
+   a non-zero value into it if a wait for the tensor cores ran out (the
+   kernels then stop early), so one check after many steps covers them all.
+   Same workspace as sc_mlp_grad. */
+sc_status sc_mlp_grad_tc(const void* d_wb, const float* d_rays, const int32_t* d_labels,
+                         int64_t batch, const float* d_box, float* d_grad, float* d_loss,
+                         void* d_ws, size_t ws_bytes, void* d_status, void* stream);
 /* Adam step `step` (1-based) on the FP32 master d_w with d_grad (then
    zeroed), moments d_m, d_v; refreshes d_wb. */
 sc_status sc_mlp_adam(float* d_w, void* d_wb, float* d_grad, float* d_m, float* d_v,

@@ -121,3 +121,39 @@ def logits_bf16_activations(flat_bf16, X) -> np.ndarray:
 
 def top1(flat_bf16, X) -> np.ndarray:
     return forward(unpack(flat_bf16), X)[-1].argmax(1)
+
+
+def _bf(x) -> np.ndarray:
+    return bf16_round(np.asarray(x, np.float64).astype(np.float32)).astype(np.float64)
+
+
+def loss_and_grad_bf16_operands(flat_bf16, X, y):
+    """Mean cross-entropy and its gradient when every operand of a product
+    is rounded to BF16 (round to nearest even) and everything else is exact
+    -- the tensor-core form of the training step: the hidden activations
+    entering layers 2 and 3, dZ, dA2 and dA1 entering the weight-gradient and
+    hidden-backward products, and the input features entering dW1.  Bias
+    gradients are sums of the rounded dZ / dA (a column of ones in the
+    product)."""
+    p = unpack(flat_bf16)
+    B = X.shape[0]
+    a1 = X @ p["W1"].T + p["b1"]
+    h1 = _bf(gelu(a1))
+    a2 = h1 @ p["W2"].T + p["b2"]
+    h2 = _bf(gelu(a2))
+    z = h2 @ p["W3"].T + p["b3"]
+    m = z.max(1, keepdims=True)
+    e = np.exp(z - m)
+    s = e.sum(1, keepdims=True)
+    loss = float(np.mean(np.log(s[:, 0]) + m[:, 0] - z[np.arange(B), y]))
+    dz = e / s
+    dz[np.arange(B), y] -= 1.0
+    dz = _bf(dz / B)
+    g = {"W3": dz.T @ h2, "b3": dz.sum(0)}
+    da2 = _bf((dz @ p["W3"]) * gelu_grad(a2))
+    g["W2"] = da2.T @ h1
+    g["b2"] = da2.sum(0)
+    da1 = _bf((da2 @ p["W2"]) * gelu_grad(a1))
+    g["W1"] = da1.T @ _bf(X)
+    g["b1"] = da1.sum(0)
+    return loss, pack(g)

@@ -606,6 +606,399 @@ __global__ void __launch_bounds__(tc::M) infer_tc_kernel(const __nv_bfloat16* wb
                  "r"(tc::kTmemCols));
 }
 
+// ------------------------------------------------ tensor-core training --
+// The training step's contractions on the tensor cores, with BF16 operands
+// and FP32 accumulation, in the K-major no-swizzle layout of the inference
+// kernel generalised to any K (a multiple of 16): element (r, k) of an
+// operand with K columns sits at byte
+// ((r / 8) * (K / 8) + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2, so core
+// matrices adjacent along K are 128 bytes apart and 8-row groups K * 16
+// bytes apart.  Three kernels: the forward pass that keeps A1, A2 and dZ
+// (layers 2 and 3 as products, as in inference); the weight gradients
+// dW += dA^T H over a batch slice (a column of ones in H gives the bias
+// gradient in the same product); and the hidden backward
+// dA_prev = (dA W) * gelu'(A_prev).
+namespace tc {
+
+__device__ __forceinline__ uint32_t core_off_k(int r, int k, int K) {
+  return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void put_bf16(unsigned char* base, uint32_t off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// Sequence point between threads' shared-memory writes and the tensor
+// cores' reads (or their TMEM writes and the threads' reads).
+__device__ __forceinline__ void sync_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(cols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+}
+
+__device__ __forceinline__ void mbar_init(void* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+}  // namespace tc
+
+// Training forward on the tensor cores: A1 and A2 (pre-activations, FP32),
+// dZ = (softmax(z) - onehot(y)) / B and the mean loss, for a batch.  The
+// hidden activations enter the products rounded to BF16, as in inference.
+__global__ void __launch_bounds__(tc::M) train_fwd_tc_kernel(
+    const __nv_bfloat16* wb, const float4* rays, const int* labels, long long B, const float* box,
+    float* A1, float* A2, float* dZ, float* loss, unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw_tc[];
+  tc::Smem& sm = *reinterpret_cast<tc::Smem*>(smem_raw_tc);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < 64 * tc::K; i += blockDim.x) {
+    const int r = i / tc::K, k = i % tc::K;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.w2) +
+                                      tc::core_off(r, k)) = wb[OFF_W2 + i];
+  }
+  for (int i = tid; i < 256 * tc::K; i += blockDim.x) {
+    const int r = i / tc::K, k = i % tc::K;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.w3) +
+                                      tc::core_off(r, k)) = wb[OFF_W3 + i];
+  }
+  for (int i = tid; i < 64 * IN; i += blockDim.x) sm.w1[i] = __bfloat162float(wb[OFF_W1 + i]);
+  for (int i = tid; i < 64; i += blockDim.x) {
+    sm.b1[i] = __bfloat162float(wb[OFF_B1 + i]);
+    sm.b2[i] = __bfloat162float(wb[OFF_B2 + i]);
+  }
+  for (int i = tid; i < 256; i += blockDim.x) sm.b3[i] = __bfloat162float(wb[OFF_B3 + i]);
+  if (tid == 0) {
+    sm.err = 0;
+    tc::mbar_init(&sm.mbar);
+  }
+  if (warp == 0) tc::tmem_alloc(&sm.tmem_slot, tc::kTmemCols);
+  tc::sync_async();
+  const uint32_t tmem = sm.tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t a_addr = tc::smem_u32(sm.a), w2_addr = tc::smem_u32(sm.w2),
+                 w3_addr = tc::smem_u32(sm.w3);
+  float bx[6];
+  for (int k = 0; k < 6; ++k) bx[k] = box[k];
+  const float invB = 1.0f / (float)B;
+  float lsum = 0.0f;
+  uint32_t phase = 0;
+  unsigned char* abytes = reinterpret_cast<unsigned char*>(sm.a);
+  for (long long t0 = (long long)blockIdx.x * tc::M; t0 < B; t0 += (long long)gridDim.x * tc::M) {
+    const long long r = t0 + tid;
+    const bool live = r < B;
+    float x[IN];
+    if (live) {
+      features(__ldg(&rays[2 * r]), __ldg(&rays[2 * r + 1]), bx, x);
+    } else {
+      for (int i = 0; i < IN; ++i) x[i] = 0.0f;
+    }
+#pragma unroll 8
+    for (int o = 0; o < 64; ++o) {
+      float acc = sm.b1[o];
+#pragma unroll
+      for (int i = 0; i < IN; ++i) acc += sm.w1[o * IN + i] * x[i];
+      if (live) A1[r * H + o] = acc;
+      tc::put_bf16(abytes, tc::core_off(tid, o), gelu(acc));
+    }
+    tc::sync_async();
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < tc::K / 16; ++s)
+        tc::mma(tmem, tc::desc(a_addr + s * 256, 128, 1024), tc::desc(w2_addr + s * 256, 128, 1024),
+                tc::idesc(tc::M, 64), s > 0);
+      tc::commit(&sm.mbar);
+    }
+    if (!tc::wait_parity(&sm.mbar, phase)) {
+      if (tid == 0) atomicOr(status, kMlpTimeout);
+      sm.err = 1;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sm.err) break;
+#pragma unroll
+    for (int c = 0; c < 64; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float a2 = v[j] + sm.b2[c + j];
+        if (live) A2[r * H + c + j] = a2;
+        tc::put_bf16(abytes, tc::core_off(tid, c + j), gelu(a2));
+      }
+    }
+    tc::sync_async();
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < tc::K / 16; ++s)
+        tc::mma(tmem, tc::desc(a_addr + s * 256, 128, 1024), tc::desc(w3_addr + s * 256, 128, 1024),
+                tc::idesc(tc::M, 256), s > 0);
+      tc::commit(&sm.mbar);
+    }
+    if (!tc::wait_parity(&sm.mbar, phase)) {
+      if (tid == 0) atomicOr(status, kMlpTimeout);
+      sm.err = 1;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sm.err) break;
+    // softmax over the 256 logits of this thread's row: max, then the sum
+    // of exponentials, then dZ; the label's logit is picked on the way
+    const int y = live ? labels[r] : 0;
+    float m = -INFINITY, zy = 0.0f;
+    for (int c = 0; c < 256; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float z = v[j] + sm.b3[c + j];
+        m = fmaxf(m, z);
+        if (c + j == y) zy = z;
+      }
+    }
+    float se = 0.0f;
+    for (int c = 0; c < 256; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) se += expf(v[j] + sm.b3[c + j] - m);
+    }
+    const float inv = 1.0f / se;
+    for (int c = 0; c < 256; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          dZ[r * OUT + c + j] =
+              (expf(v[j] + sm.b3[c + j] - m) * inv - (c + j == y ? 1.0f : 0.0f)) * invB;
+      }
+    }
+    if (live) lsum += (logf(se) + m) - zy;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __shared__ float red[tc::M];
+  red[tid] = lsum;
+  __syncthreads();
+  for (int st = tc::M / 2; st > 0; st >>= 1) {
+    if (tid < st) red[tid] += red[tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) atomicAdd(loss, red[0] * invB);
+  if (warp == 0) tc::tmem_free(tmem, tc::kTmemCols);
+}
+
+// Weight gradients over a batch slice: dW[o][i] += sum_b dA[b][o] Hin[b][i]
+// and db[o] += sum_b dA[b][o], as one product per 64-ray chunk: A = dA^T
+// (128 outputs of this CTA's tile x 64 rays), B = [Hin | 1 | 0]^T (NP x 64,
+// NP = I + 1 rounded up to 16), both BF16; Hin = gelu(Asrc) (act 1), Asrc
+// (act 0) or the ray features (act 2, Asrc = rays).  The FP32 accumulator
+// stays in TMEM over the slice and is added to dW / db at the end.
+constexpr int kGradChunk = 64;
+
+template <int NP>
+struct GradSmem {
+  __nv_bfloat16 a[tc::M * kGradChunk];
+  __nv_bfloat16 b[NP * kGradChunk];
+  unsigned long long mbar;
+  uint32_t tmem_slot;
+  int err;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(tc::M) grad_tc_kernel(const float* dA, int O, const float* Asrc,
+                                                        int I, int act, const float* box,
+                                                        long long B, long long slice, float* dW,
+                                                        float* db, unsigned* status) {
+  constexpr uint32_t kCols = NP <= 32 ? 32 : (NP <= 64 ? 64 : (NP <= 128 ? 128 : 256));
+  __shared__ __align__(1024) GradSmem<NP> sm;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int o0 = blockIdx.y * tc::M;
+  const long long b_begin = (long long)blockIdx.x * slice;
+  const long long b_end = b_begin + slice < B ? b_begin + slice : B;
+  if (tid == 0) {
+    sm.err = 0;
+    tc::mbar_init(&sm.mbar);
+  }
+  if (warp == 0) tc::tmem_alloc(&sm.tmem_slot, kCols);
+  tc::sync_async();
+  const uint32_t tmem = sm.tmem_slot;
+  float bx[6] = {0, 0, 0, 1, 1, 1};
+  if (act == 2)
+    for (int k = 0; k < 6; ++k) bx[k] = box[k];
+  unsigned char* ab = reinterpret_cast<unsigned char*>(sm.a);
+  unsigned char* bb = reinterpret_cast<unsigned char*>(sm.b);
+  const uint32_t a_addr = tc::smem_u32(sm.a), b_addr = tc::smem_u32(sm.b);
+  uint32_t phase = 0;
+  bool first = true;
+  for (long long c0 = b_begin; c0 < b_end; c0 += kGradChunk) {
+    // A: element (o, k) = dA[c0 + k][o0 + o]; consecutive threads take
+    // consecutive outputs of one ray (coalesced reads)
+    for (int e = tid; e < tc::M * kGradChunk; e += tc::M) {
+      const int o = e % tc::M, k = e / tc::M;
+      const long long b = c0 + k;
+      const float v = (b < b_end && o0 + o < O) ? dA[b * O + o0 + o] : 0.0f;
+      tc::put_bf16(ab, tc::core_off_k(o, k, kGradChunk), v);
+    }
+    // B: element (i, k) = Hin[c0 + k][i] for i < I, 1 at i = I (a ray in
+    // the slice), 0 beyond
+    for (int e = tid; e < NP * kGradChunk; e += tc::M) {
+      const int i = e % NP, k = e / NP;
+      const long long b = c0 + k;
+      float v = 0.0f;
+      if (b < b_end) {
+        if (i < I) {
+          if (act == 2) {
+            const float4* rr = reinterpret_cast<const float4*>(Asrc) + 2 * b;
+            float x[IN];
+            features(rr[0], rr[1], bx, x);
+            v = x[i];
+          } else {
+            const float a = Asrc[b * I + i];
+            v = act ? gelu(a) : a;
+          }
+        } else if (i == I) {
+          v = 1.0f;
+        }
+      }
+      tc::put_bf16(bb, tc::core_off_k(i, k, kGradChunk), v);
+    }
+    tc::sync_async();
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < kGradChunk / 16; ++s)
+        tc::mma(tmem, tc::desc(a_addr + s * 256, 128, (kGradChunk / 8) * 128),
+                tc::desc(b_addr + s * 256, 128, (kGradChunk / 8) * 128), tc::idesc(tc::M, NP),
+                (first && s == 0) ? 0u : 1u);
+      tc::commit(&sm.mbar);
+    }
+    first = false;
+    if (!tc::wait_parity(&sm.mbar, phase)) {
+      if (tid == 0) atomicOr(status, kMlpTimeout);
+      sm.err = 1;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sm.err) break;
+  }
+  if (!sm.err && !first) {
+    // thread t holds output o0 + t (TMEM lane t)
+    const int o = o0 + tid;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int c = 0; c < NP; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+      if (o < O) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int i = c + j;
+          if (i < I) atomicAdd(&dW[o * I + i], v[j]);
+          else if (i == I) atomicAdd(&db[o], v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, kCols);
+}
+
+// Hidden backward on the tensor cores: dAprev[b][i] = (sum_o dA[b][o]
+// W[o][i]) * gelu'(Aprev[b][i]) per tile of 128 rays: A = dA (128 x O, BF16),
+// B = W^T (64 x O, from the BF16 weights), FP32 accumulation.
+template <int O>
+struct BackSmem {
+  __nv_bfloat16 a[tc::M * O];
+  __nv_bfloat16 w[64 * O];
+  unsigned long long mbar;
+  uint32_t tmem_slot;
+  int err;
+};
+
+template <int O>
+__global__ void __launch_bounds__(tc::M) back_tc_kernel(const float* dA,
+                                                        const __nv_bfloat16* wb, int off_w,
+                                                        const float* Aprev, long long B,
+                                                        float* dAprev, unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw_tc[];
+  BackSmem<O>& sm = *reinterpret_cast<BackSmem<O>*>(smem_raw_tc);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* ab = reinterpret_cast<unsigned char*>(sm.a);
+  unsigned char* wbytes = reinterpret_cast<unsigned char*>(sm.w);
+  // W^T: element (i, o) = W[o][i]
+  for (int e = tid; e < 64 * O; e += tc::M) {
+    const int o = e / 64, i = e % 64;
+    *reinterpret_cast<__nv_bfloat16*>(wbytes + tc::core_off_k(i, o, O)) = wb[off_w + o * 64 + i];
+  }
+  if (tid == 0) {
+    sm.err = 0;
+    tc::mbar_init(&sm.mbar);
+  }
+  if (warp == 0) tc::tmem_alloc(&sm.tmem_slot, 64);
+  tc::sync_async();
+  const uint32_t tmem = sm.tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t a_addr = tc::smem_u32(sm.a), w_addr = tc::smem_u32(sm.w);
+  uint32_t phase = 0;
+  for (long long t0 = (long long)blockIdx.x * tc::M; t0 < B; t0 += (long long)gridDim.x * tc::M) {
+    // A: element (b, o) = dA[t0 + b][o]; consecutive threads, consecutive o
+    for (int e = tid; e < tc::M * O; e += tc::M) {
+      const int b = e / O, o = e % O;
+      const long long r = t0 + b;
+      tc::put_bf16(ab, tc::core_off_k(b, o, O), r < B ? dA[r * O + o] : 0.0f);
+    }
+    tc::sync_async();
+    if (tid == 0) {
+#pragma unroll
+      for (int s = 0; s < O / 16; ++s)
+        tc::mma(tmem, tc::desc(a_addr + s * 256, 128, (O / 8) * 128),
+                tc::desc(w_addr + s * 256, 128, (O / 8) * 128), tc::idesc(tc::M, 64), s > 0);
+      tc::commit(&sm.mbar);
+    }
+    if (!tc::wait_parity(&sm.mbar, phase)) {
+      if (tid == 0) atomicOr(status, kMlpTimeout);
+      sm.err = 1;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (sm.err) break;
+    const long long r = t0 + tid;
+#pragma unroll
+    for (int c = 0; c < 64; c += 16) {
+      float v[16];
+      tc::ld16(tmem + lane_base + c, v);
+      if (r < B) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          dAprev[r * H + c + j] = v[j] * gelu_grad(Aprev[r * H + c + j]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_free(tmem, 64);
+}
+
 int num_sms() {
   static std::once_flag f;
   static int sms = 0;
@@ -764,6 +1157,64 @@ sc_status sc_mlp_grad(const void* d_wb, const float* d_rays, const int32_t* d_la
   // layer 1: dW1 = dA1^T x, db1
   grad_w_kernel<<<dim3(nsl, H / TG, 1), 256, 0, st>>>(A2, H, d_rays, IN, 2, d_box, batch, slice,
                                                        d_grad + OFF_W1, d_grad + OFF_B1);
+  CUDA_OK(cudaGetLastError());
+  return SC_OK;
+  SC_CATCH
+}
+
+sc_status sc_mlp_grad_tc(const void* d_wb, const float* d_rays, const int32_t* d_labels,
+                         int64_t batch, const float* d_box, float* d_grad, float* d_loss,
+                         void* d_ws, size_t ws_bytes, void* d_status, void* stream) {
+  SC_TRY
+  check_box(d_box);
+  if (batch <= 0 || !d_wb || !d_rays || !d_labels || !d_grad || !d_loss || !d_ws || !d_status)
+    fail(SC_ERR_ARG, "sc_mlp_grad_tc: bad arguments");
+  if (ws_bytes < sc_mlp_train_workspace_bytes(batch))
+    fail(SC_ERR_ARG, "sc_mlp_grad_tc: workspace too small");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  using namespace mlpk;
+  float* A1 = reinterpret_cast<float*>(d_ws);
+  float* A2 = A1 + batch * H;
+  float* dZ = A2 + batch * H;
+  float* dAh = dZ + batch * OUT;
+  unsigned* status = reinterpret_cast<unsigned*>(d_status);
+  const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(d_wb);
+  CUDA_OK(cudaMemsetAsync(d_loss, 0, sizeof(float), st));
+  // forward: A1, A2, dZ and the loss (two CTAs per SM share its TMEM)
+  const size_t fsm = sizeof(tc::Smem);
+  CUDA_OK(cudaFuncSetAttribute((const void*)train_fwd_tc_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  const long long tiles = (batch + tc::M - 1) / tc::M, cap = 2LL * num_sms();
+  train_fwd_tc_kernel<<<(unsigned)(tiles < cap ? tiles : cap), tc::M, fsm, st>>>(
+      wb, reinterpret_cast<const float4*>(d_rays), d_labels, batch, d_box, A1, A2, dZ, d_loss,
+      status);
+  CUDA_OK(cudaGetLastError());
+  const long long slice = 256;  // rays per split-K CTA of the weight gradients
+  const unsigned nsl = (unsigned)((batch + slice - 1) / slice);
+  // layer 3: dW3 = dZ^T gelu(A2), db3
+  grad_tc_kernel<80><<<dim3(nsl, OUT / tc::M), tc::M, 0, st>>>(
+      dZ, OUT, A2, H, 1, d_box, batch, slice, d_grad + OFF_W3, d_grad + OFF_B3, status);
+  CUDA_OK(cudaGetLastError());
+  // dA2 = (dZ W3) * gelu'(A2)
+  const size_t bs3 = sizeof(BackSmem<OUT>), bs2 = sizeof(BackSmem<H>);
+  CUDA_OK(cudaFuncSetAttribute((const void*)back_tc_kernel<OUT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs3));
+  CUDA_OK(cudaFuncSetAttribute((const void*)back_tc_kernel<H>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs2));
+  back_tc_kernel<OUT><<<(unsigned)(tiles < cap ? tiles : cap), tc::M, bs3, st>>>(
+      dZ, wb, OFF_W3, A2, batch, dAh, status);
+  CUDA_OK(cudaGetLastError());
+  // layer 2: dW2 = dA2^T gelu(A1), db2
+  grad_tc_kernel<80><<<dim3(nsl, 1), tc::M, 0, st>>>(dAh, H, A1, H, 1, d_box, batch, slice,
+                                                     d_grad + OFF_W2, d_grad + OFF_B2, status);
+  CUDA_OK(cudaGetLastError());
+  // dA1 = (dA2 W2) * gelu'(A1), into A2 (no longer needed)
+  back_tc_kernel<H><<<(unsigned)(tiles < cap ? tiles : cap), tc::M, bs2, st>>>(
+      dAh, wb, OFF_W2, A1, batch, A2, status);
+  CUDA_OK(cudaGetLastError());
+  // layer 1: dW1 = dA1^T x, db1
+  grad_tc_kernel<16><<<dim3(nsl, 1), tc::M, 0, st>>>(A2, H, d_rays, IN, 2, d_box, batch, slice,
+                                                     d_grad + OFF_W1, d_grad + OFF_B1, status);
   CUDA_OK(cudaGetLastError());
   return SC_OK;
   SC_CATCH

@@ -100,11 +100,13 @@ class LearnedProposal:
 
     # -------------------------------------------------------- training --
     def fit(self, rays, labels, steps: int, batch: int = 4096, lr: float = 2e-3,
-            seed: int = 0, log_every: int = 0):
+            seed: int = 0, log_every: int = 0, tensor_cores: bool = True):
         """`steps` Adam steps over minibatches drawn on the device through a
         new pseudo-random permutation of the pairs every epoch
-        (sc_mlp_gather); warm-up then cosine learning rate.  Returns the mean
-        loss of the last min(steps, 50) steps."""
+        (sc_mlp_gather); warm-up then cosine learning rate.  tensor_cores:
+        the gradient's contractions as tcgen05 products (sc_mlp_grad_tc,
+        BF16 operands), else FP32 CUDA cores (sc_mlp_grad).  Returns the
+        mean loss of the last min(steps, 50) steps."""
         import torch
         n = int(rays.shape[0])
         if n == 0:
@@ -121,13 +123,18 @@ class LearnedProposal:
         key = 0
         pos = n
         warm = max(1, steps // 20)
+        self._status.zero_()
         for it in range(steps):
             if pos + batch > n:
                 key = int(rng.integers(0, 2 ** 63))
                 pos = 0
             sc.sc_mlp_gather(rays, labels, key, pos, batch, br, bl)
             pos += batch
-            sc.sc_mlp_grad(self.wb, br, bl, self.box, self.grad, self.loss, ws)
+            if tensor_cores:
+                sc.sc_mlp_grad_tc(self.wb, br, bl, self.box, self.grad, self.loss, ws,
+                                  self._status)
+            else:
+                sc.sc_mlp_grad(self.wb, br, bl, self.box, self.grad, self.loss, ws)
             losses[it:it + 1].copy_(self.loss)
             frac = it / max(1, steps - 1)
             cur = lr * min(1.0, (it + 1) / warm) * (0.1 + 0.45 * (1.0 + math.cos(math.pi * frac)))
@@ -136,7 +143,10 @@ class LearnedProposal:
             if log_every and (it + 1) % log_every == 0:
                 print(f"step {it + 1}: loss {losses[it].item():.4f}")
         tail = losses[max(0, steps - 50):]
-        return float(tail.mean().item())
+        out = float(tail.mean().item())
+        if tensor_cores:
+            self.check()
+        return out
 
     # ------------------------------------------------------- inference --
     def predict(self, rays, cls=None, logits=None, min_prob: float = 0.0,
@@ -169,9 +179,9 @@ class LearnedProposal:
         sc.sc_mlp_to_bf16(self.w, self.wb)
 
     def check(self):
-        """Raises if a tensor-core wait ran out in a forward pass."""
+        """Raises if a tensor-core wait ran out in a forward or training pass."""
         if int(self._status.item()) != 0:
-            raise RuntimeError("tensor-core forward: a wait for the tensor cores ran out")
+            raise RuntimeError("tensor-core pass: a wait for the tensor cores ran out")
 
     def trace(self, dbvh: sc.DeviceBVH, rays, cls, hits=None, counts=None, cull: int = 1,
               work=None):

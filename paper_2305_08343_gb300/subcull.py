@@ -147,6 +147,7 @@ def lib():
             "sc_mlp_train_workspace_bytes": (C.c_size_t, [i64]),
             "sc_mlp_forward_tc": (C.c_int, [vp, vp, i64, vp, vp, vp, C.c_float, vp, vp]),
             "sc_mlp_grad": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_size_t, vp]),
+            "sc_mlp_grad_tc": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp, C.c_size_t, vp, vp]),
             "sc_mlp_adam": (C.c_int, [vp, vp, vp, vp, vp, C.c_int, C.c_float, C.c_float,
                                       C.c_float, C.c_float, vp]),
             "sc_mlp_labels": (C.c_int, [vp, vp, i64, vp, vp, vp, vp, i64, vp]),
@@ -607,6 +608,17 @@ def sc_mlp_grad(wb, rays, labels, box, grad, loss, ws, stream=None):
                              C.c_void_p(box.data_ptr()), C.c_void_p(grad.data_ptr()),
                              C.c_void_p(loss.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
                              _stream_ptr(stream)))
+
+
+def sc_mlp_grad_tc(wb, rays, labels, box, grad, loss, ws, status, stream=None):
+    """sc_mlp_grad with the contractions on the tensor cores; status: device
+    int32 tensor zeroed by the caller, ORed non-zero if a tensor-core wait
+    ran out."""
+    _check(lib().sc_mlp_grad_tc(C.c_void_p(wb.data_ptr()), C.c_void_p(rays.data_ptr()),
+                                C.c_void_p(labels.data_ptr()), rays.shape[0],
+                                C.c_void_p(box.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                C.c_void_p(loss.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                ws.numel(), C.c_void_p(status.data_ptr()), _stream_ptr(stream)))
 
 
 def sc_mlp_adam(w, wb, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8,

@@ -199,6 +199,48 @@ def test_mlp_gradient_vs_oracle(batch):
     assert np.linalg.norm(g2 - 2 * g) <= 1e-5 * np.linalg.norm(g2)
 
 
+@pytest.mark.parametrize("batch", [1, 130, 4096])
+def test_mlp_gradient_tensor_cores_vs_oracle(batch):
+    """sc_mlp_grad_tc against the fp64 reference with the kernel's BF16
+    operand roundings (oracle/mlp.py): the mean loss, and every gradient
+    tensor within 1e-3 relative in L2 norm (FP32 accumulation order, and
+    the odd operand whose FP32 and FP64 values round to neighbouring BF16
+    values); ragged batches (a partial 128-ray tile, a partial split-K
+    slice); gradients accumulate over calls."""
+    _need_gpu()
+    w = _params(7)
+    dw, wb = _upload_weights(w)
+    rng = np.random.default_rng(batch + 11)
+    rays = sg.random_rays(batch, seed=batch + 11)
+    labels = rng.integers(0, 256, batch).astype(np.int32)
+    r = torch.from_numpy(rays).cuda()
+    lab = torch.from_numpy(labels).cuda()
+    box = torch.from_numpy(BOX).cuda()
+    grad = torch.zeros(omlp.P, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(sc.sc_mlp_train_workspace_bytes(batch), dtype=torch.uint8, device="cuda")
+    sc.sc_mlp_grad_tc(wb, r, lab, box, grad, loss, ws, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref_loss, ref_g = omlp.loss_and_grad_bf16_operands(
+        omlp.bf16_round(w).astype(np.float64), omlp.features(rays, BOX), labels)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * abs(ref_loss)
+    g = grad.cpu().numpy().astype(np.float64)
+    gd, rd = omlp.unpack(g), omlp.unpack(ref_g)
+    for name, _ in omlp.SHAPES:
+        err = np.linalg.norm(gd[name] - rd[name]) / np.linalg.norm(rd[name])
+        assert err <= 1e-3, (name, err)
+    # the same step in exact arithmetic differs by the BF16 roundings only
+    _, exact = omlp.loss_and_grad(omlp.bf16_round(w).astype(np.float64),
+                                  omlp.features(rays, BOX), labels)
+    assert np.linalg.norm(g - exact) <= 3e-2 * np.linalg.norm(exact)
+    sc.sc_mlp_grad_tc(wb, r, lab, box, grad, loss, ws, status)
+    torch.cuda.synchronize()
+    g2 = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g2 - 2 * g) <= 1e-5 * np.linalg.norm(g2)
+
+
 def test_mlp_adam_step():
     _need_gpu()
     w = _params(3)

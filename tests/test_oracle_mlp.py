@@ -79,3 +79,27 @@ def test_features_map_box_to_unit_cube():
     box = np.array([1, 2, 3, 1, 2, 3], np.float64)
     X = mlp.features(rays, box)
     assert np.array_equal(X, [[-1, -1, -1, 1, 0, 0], [1, 1, 1, 0, 0, 1]])
+
+
+def test_bf16_operand_gradient_is_the_exact_one_within_rounding():
+    """The tensor-core reference (every product operand rounded to BF16)
+    stays within the BF16 rounding bound of the exact gradient, which is
+    pinned by finite differences above: a dropped term, a sign or a
+    transposed operand would move a tensor by far more.  Its loss is the
+    loss of the BF16-activation logits."""
+    rng = np.random.default_rng(17)
+    w = mlp.bf16_round(mlp.init_params(17)).astype(np.float64)
+    X = np.concatenate([rng.uniform(-1, 1, (300, 3)), rng.normal(size=(300, 3))], 1)
+    X[:, 3:] /= np.linalg.norm(X[:, 3:], axis=1, keepdims=True)
+    y = rng.integers(0, 256, 300)
+    lb, gb = mlp.loss_and_grad_bf16_operands(w, X, y)
+    le, ge = mlp.loss_and_grad(w, X, y)
+    z = mlp.logits_bf16_activations(w, X)
+    m = z.max(1, keepdims=True)
+    ref = float(np.mean(np.log(np.exp(z - m).sum(1)) + m[:, 0] - z[np.arange(300), y]))
+    assert abs(lb - ref) <= 1e-12 * abs(ref)
+    assert abs(lb - le) <= 1e-2 * abs(le)
+    db, de = mlp.unpack(gb), mlp.unpack(ge)
+    for name, _ in mlp.SHAPES:
+        rel = np.linalg.norm(db[name] - de[name]) / np.linalg.norm(de[name])
+        assert 0 < rel <= 2e-2, (name, rel)
