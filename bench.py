@@ -634,11 +634,15 @@ def run_gpu(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        # an NVTX range around the timed steps, so that a profiler can be
+        # limited to them (ncu --nvtx --nvtx-include "timed_culled/")
+        torch.cuda.nvtx.range_push("timed_culled" if cull else "timed_plain")
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
             step(i_graph, dbvh, cull, bufs)
             ev[i][1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -683,112 +687,32 @@ def run_gpu(args):
             torch.cuda.synchronize()
             anyhit[name] = 3 * n / (ev[2].elapsed_time(ev[3]) * 1e-3) / 1e6
 
-    # end to end through the public API: every step copies its rays from
-    # pinned host memory, runs the wave pipeline and copies every wave's hit
-    # buffer back to pinned host memory.  Two buffer sets and three streams
-    # (upload, traversal, download) let step i+1's upload and step i-1's
-    # download overlap step i's traversal.
+    # end to end through the C-ABI with host buffers: every step is one
+    # sc_trace_waves_host call, which copies the step's rays from pinned host
+    # memory, runs the wave pipeline, reads the wave sizes and copies every
+    # wave's hits back to pinned host memory, then synchronizes.
     h_rays = torch.from_numpy(rays_np).pin_memory()
-    h_hits = [[torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in range(bounces + 1)]
-              for _ in range(2)]
-    d_rays2 = [torch.empty((n, 8), dtype=torch.float32, device=dev) for _ in range(2)]
-    bufs2 = [bufs_c, sc.WaveBuffers(n, bounces, with_counts=False, device=dev)]
-    s_up, s_run, s_down = (torch.cuda.Stream(device=dev) for _ in range(3))
+    h_outs = [(torch.empty((n, 4), dtype=torch.float32).pin_memory(), None, None, None)
+              for _ in range(bounces + 1)]
+    d_rays_e = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    s_e2e = torch.cuda.Stream(device=dev)
 
     def e2e_run(k_steps):
-        up = [torch.cuda.Event() for _ in range(2)]
-        ran = [torch.cuda.Event() for _ in range(2)]
-        down = [None, None]
-        for i in range(k_steps):
-            k = i & 1
-            with torch.cuda.stream(s_up):
-                if down[k] is not None:  # the slot's previous hits have left
-                    s_up.wait_event(down[k])
-                d_rays2[k].copy_(h_rays, non_blocking=True)
-                up[k].record(s_up)
-            s_run.wait_event(up[k])
-            sc.sc_trace_waves(d_masked, d_rays2[k], bounces, seed, 1, bufs2[k].outs(), bufs2[k].ws,
-                              opts_c, stream=s_run)
-            ran[k].record(s_run)
-            with torch.cuda.stream(s_down):
-                s_down.wait_event(ran[k])
-                for w in range(bounces + 1):
-                    h_hits[k][w].copy_(bufs2[k].hits[w], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(s_down)
-                down[k] = ev
-        for st in (s_up, s_run, s_down):
-            st.synchronize()
+        szs = None
+        for _ in range(k_steps):
+            szs = sc.sc_trace_waves_host(d_masked, h_rays, bounces, seed, 1, h_outs, d_rays_e,
+                                         bufs_c.outs(), bufs_c.ws, opts_c, stream=s_e2e)
+        return szs
 
     e2e_run(max(2, args.warmup))
     t0 = time.perf_counter()
-    e2e_run(args.steps)
+    szs = e2e_run(args.steps)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": rays_per_step * args.steps / e2e_s / 1e6, "unit": "Mrays/s",
-           "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 16 * (bounces + 1),
-           "overlap": "double-buffered: upload i+1 and download i-1 overlap traversal i"}
-    sc.sc_waves_poll(bufs2[1].ws, bounces)
-
-    # roofline of the wave kernel.  Algorithmic bytes per ray (the method's
-    # own fetches, from the exact per-ray counters): 32 (ray) + 16 (hit) +
-    # node visits x B_node + triangle tests x 48, plus 32 per spawned bounce
-    # ray.  B_node is the method's record: a 64-byte child pair, plus the two
-    # R^3-bit masks when uncompressed (80 / 128 / 192 bytes at R = 4 / 6 / 8);
-    # the image's own records (stored scales, 4-wide layouts) are reported
-    # beside it as record_bytes_per_ray.
-    mstride = {4: 8, 6: 32, 8: 64}[R]
-    b_node = 64 + (0 if comp else 2 * mstride)
-    if wide:
-        # a 4-wide node is made from every binary node at even depth and
-        # holds 2 + its inner children: node tests / mean children = visits
-        rec_bytes = 176 + (0 if comp else 4 * mstride)
-        visits = cnt_c[0] / mean_wide_children(bvh)
-        b_node_w = 2 * b_node
-    else:
-        rec_bytes = (96 if args.layout in (1, 5) else 64) + (0 if comp else 2 * mstride)
-        visits = cnt_c[0] / 2.0
-        b_node_w = b_node
-    spawned = float(np.sum(sizes[1:])) / rays_per_step
-    b_ray = 32 + 16 + visits * b_node_w + cnt_c[1] * 48 + spawned * 32
-    b_ray_rec = 32 + 16 + 4 + visits * rec_bytes + cnt_c[1] * 48 + spawned * (32 + 4)
-    per_launch_bytes = b_ray * rays_per_step
-    avg_ms = float(np.mean(ms_cull))
-    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-    peaks = load_peaks()
-    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic, traffic_src = measured_traffic(args.workload)
-    if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
-            or args.leaf_min or args.L != 3 or args.max_leaf != 4 or wide
-            or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
-            or opts.variant != DEFAULT_VARIANT):
-        traffic, traffic_src = None, None  # measured for the default configuration only
-    l2_peak, l2_mb = measure_l2_peak(dev)
-    # The bound: DRAM traffic far below the algorithmic bytes means the
-    # fetched bytes come from L2 (the working set of one frame stays there),
-    # so the L2 read bandwidth is the roofline; HBM otherwise.
-    on_chip = traffic is not None and traffic < 0.25 * per_launch_bytes
-    if traffic is None:
-        bound_basis = ("no DRAM capture of this kernel source: bound taken as HBM; the "
-                       "fraction against L2 is given beside it")
-    elif on_chip:
-        bound_basis = (f"DRAM traffic {traffic / 1e9:.2f} GB per launch is "
-                       f"{100 * traffic / per_launch_bytes:.1f}% of the algorithmic bytes")
-    else:
-        bound_basis = "DRAM traffic is a large part of the algorithmic bytes"
-    bound_l2 = on_chip and bool(l2_peak)
-    peak = l2_peak if bound_l2 else hbm_peak
-    roofline = {"bound": "l2" if bound_l2 else "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": traffic_src, "bound_basis": bound_basis,
-                "peak_source": ("measured (sc_l2_read probe, this run)" if bound_l2 else
-                                ("measured" if peaks else "fallback")),
-                "bytes_per_ray": b_ray, "b_node": b_node, "node_visits_per_ray": visits,
-                "record_bytes_per_ray": b_ray_rec, "record_bytes": rec_bytes,
-                "kernel": "waves_kernel (culled)",
-                "hbm_peak": hbm_peak, "frac_hbm": achieved / hbm_peak,
-                "l2_peak": l2_peak, "frac_l2": achieved / l2_peak if l2_peak else None,
-                "l2_peak_source": f"sc_l2_read probe, best over 16-64 MB resident buffers "
-                                  f"({l2_mb} MB), measured in this run"}
+           "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": int(np.sum(szs)) * 16,
+           "call": "sc_trace_waves_host (host rays in, every wave's hits out, synchronous)"}
+    ok_e2e = [int(x) for x in szs] == [int(x) for x in sizes]
+    e2e["identical_wave_sizes"] = ok_e2e
 
     # Test selection (an option beside the paper's method, which tests
     # every child): children whose decoded mask has at least skip_bits bits

@@ -319,6 +319,8 @@ enum {
                                   octant and origin cell before tracing     */
   SC_VARIANT_LAZY = 64,        /* the per-child Alg. 1 scales are fetched only
                                   for nodes with a child to test            */
+  SC_VARIANT_SSTACK = 128,     /* the top 8 stack entries of each ray in
+                                  shared memory, the rest in local memory   */
   SC_VARIANT_DEFER = 32        /* compressed masks with the bit table: each
                                   child's bit-table lookup is issued when the
                                   child is visited, beside its own fetch
@@ -420,6 +422,21 @@ sc_status sc_trace_waves(const sc_dbvh* d, const float* d_rays, int64_t n0,
    of rays of each bounce wave (sizes[0] = 0: wave 0 is the n0 primaries).
    Returns SC_ERR_TIMEOUT / SC_ERR_STACK / SC_ERR_STATE on device errors. */
 sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* stream);
+
+/* End-to-end form of sc_trace_waves for host data: copies h_rays (host
+   float[n0][8], ideally pinned) to d_rays_buf (device, n0 * 32 bytes,
+   16-byte aligned), runs the wave pipeline into the device buffers d_outs
+   (as sc_trace_waves), reads the wave sizes, and copies each wave's entries
+   back to the host buffers h_outs: hits always (h_outs[w].hits: host
+   sc_hit[n0]), path ids, counts and traced rays where both the host and the
+   device pointer are given; then synchronizes `stream`.  sizes (host
+   uint32[bounces+1] or NULL) as sc_waves_poll.  Device errors as
+   sc_waves_poll. */
+sc_status sc_trace_waves_host(const sc_dbvh* d, const float* h_rays, int64_t n0, int bounces,
+                              uint32_t seed, int cull, const sc_wave_out* h_outs,
+                              const sc_trace_opts* opts, float* d_rays_buf,
+                              const sc_wave_out* d_outs, void* d_ws, size_t ws_bytes,
+                              uint32_t* sizes, void* stream);
 
 /* Autotuner of the wave pipeline: times sc_trace_waves (one warm-up, then
    `reps` rounds over all candidates, CUDA events, median per candidate;

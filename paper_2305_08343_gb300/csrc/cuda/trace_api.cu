@@ -597,11 +597,13 @@ sc_status sc_trace_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int 
   SC_CATCH
 }
 
-sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* stream) {
-  SC_TRY
-  if (!d_ws || !sizes || bounces < 0 || bounces + 1 > sct::kMaxWaves)
-    fail(SC_ERR_ARG, "sc_waves_poll: bad argument");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// Wave sizes and the device status of a finished wave launch (stream
+// synchronized); throws on a device error.
+void read_wave_sizes(const void* d_ws, int bounces, uint32_t* sizes, cudaStream_t st) {
   unsigned head[sct::WW_HEAD];
   CUDA_OK(cudaMemcpyAsync(head, d_ws, sizeof(head), cudaMemcpyDeviceToHost, st));
   CUDA_OK(cudaStreamSynchronize(st));
@@ -623,6 +625,60 @@ sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* st
   if (status & sct::ST_STACK) fail(SC_ERR_STACK, "device: a traversal stack overflowed");
   if (status & sct::ST_BAD_NODE)
     fail(SC_ERR_STATE, "device: the BVH image holds an invalid child reference");
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_trace_waves_host(const sc_dbvh* d, const float* h_rays, int64_t n0, int bounces,
+                              uint32_t seed, int cull, const sc_wave_out* h_outs,
+                              const sc_trace_opts* opts, float* d_rays_buf,
+                              const sc_wave_out* d_outs, void* d_ws, size_t ws_bytes,
+                              uint32_t* sizes, void* stream) {
+  SC_TRY
+  if (!h_outs || !d_outs || bounces < 0 || bounces + 1 > sct::kMaxWaves)
+    fail(SC_ERR_ARG, "sc_trace_waves_host: bad arguments");
+  if (n0 > 0 && (!h_rays || !d_rays_buf)) fail(SC_ERR_ARG, "sc_trace_waves_host: NULL rays");
+  for (int w = 0; w <= bounces; ++w)
+    if (n0 > 0 && !h_outs[w].hits)
+      fail(SC_ERR_ARG, "sc_trace_waves_host: wave %d has no host hit buffer", w);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n0 > 0)
+    CUDA_OK(cudaMemcpyAsync(d_rays_buf, h_rays, (size_t)n0 * 32, cudaMemcpyHostToDevice, st));
+  launch_waves(d, d_rays_buf, n0, bounces, seed, cull, d_outs, opts, d_ws, ws_bytes, st);
+  uint32_t local[sct::kMaxWaves] = {0};
+  if (n0 > 0) read_wave_sizes(d_ws, bounces, local, st);
+  local[0] = (uint32_t)n0;
+  for (int w = 0; w <= bounces; ++w) {
+    const size_t m = local[w];
+    if (m == 0) continue;
+    CUDA_OK(cudaMemcpyAsync(h_outs[w].hits, d_outs[w].hits, m * 16, cudaMemcpyDeviceToHost, st));
+    if (h_outs[w].path && d_outs[w].path)
+      CUDA_OK(cudaMemcpyAsync(h_outs[w].path, d_outs[w].path, m * 4, cudaMemcpyDeviceToHost, st));
+    if (h_outs[w].counts && d_outs[w].counts)
+      CUDA_OK(cudaMemcpyAsync(h_outs[w].counts, d_outs[w].counts, m * 8, cudaMemcpyDeviceToHost,
+                              st));
+    if (h_outs[w].rays && d_outs[w].rays)
+      CUDA_OK(cudaMemcpyAsync(h_outs[w].rays, d_outs[w].rays, m * 32, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_OK(cudaStreamSynchronize(st));
+  if (sizes)
+    for (int w = 0; w <= bounces; ++w) sizes[w] = w == 0 ? 0u : local[w];
+  return SC_OK;
+  SC_CATCH
+}
+
+}  // extern "C"
+
+extern "C" {
+
+sc_status sc_waves_poll(const void* d_ws, int bounces, uint32_t* sizes, void* stream) {
+  SC_TRY
+  if (!d_ws || !sizes || bounces < 0 || bounces + 1 > sct::kMaxWaves)
+    fail(SC_ERR_ARG, "sc_waves_poll: bad argument");
+  read_wave_sizes(d_ws, bounces, sizes, reinterpret_cast<cudaStream_t>(stream));
+  sizes[0] = 0;
   return SC_OK;
   SC_CATCH
 }

@@ -94,6 +94,7 @@ enum : int {
   OPT_SORT = 16,  // waves: each bounce queue is sorted by direction octant and
                   // origin cell before its wave is traced
   OPT_LAZY = 64,  // the per-child scales are loaded only when a child needs a test
+  OPT_SSTACK = 128, // the top kRing stack entries in shared memory (blocks of kBlock)
   OPT_DEFER = 32, // compressed, bit table: a child's culling lookup is issued
                   // when the child is visited, beside its own fetch (the
                   // cells still come from the parent's slab test)
@@ -422,10 +423,27 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
 // Stack push / pop.  OPT_TOS keeps the top entry in a register and the
 // entries below it in the array, so a pop takes the register and refills it
 // with a load whose latency hides behind the next node's work.
+// OPT_SSTACK: a ring of the kRing top entries per thread in shared memory
+// (entry k of thread t at ring[k * kBlock + t], conflict-free); entries
+// further down live in the local array.  A push that overwrites a ring slot
+// first moves its entry (kRing below the new top) to the array; a pop
+// refills the freed slot from the array.
+constexpr int kRing = 8;
+
+__device__ __forceinline__ uint2* ring_array() {
+  __shared__ uint2 ring[kBlock * kRing];
+  return ring + threadIdx.x;
+}
+
 template <int STACK, int OPT>
 __device__ __forceinline__ bool stack_push(RayState& s, uint2* stack, uint2 e) {
   if (s.sp >= STACK) return false;
-  if constexpr ((OPT & OPT_TOS) != 0) {
+  if constexpr ((OPT & OPT_SSTACK) != 0) {
+    uint2* ring = ring_array();
+    const int k = s.sp & (kRing - 1);
+    if (s.sp >= kRing) stack[s.sp - kRing] = ring[k * kBlock];
+    ring[k * kBlock] = e;
+  } else if constexpr ((OPT & OPT_TOS) != 0) {
     if (s.sp > 0) stack[s.sp - 1] = s.top;
     s.top = e;
   } else {
@@ -439,7 +457,12 @@ template <int OPT>
 __device__ __forceinline__ uint2 stack_pop(RayState& s, uint2* stack) {
   uint2 e;
   --s.sp;
-  if constexpr ((OPT & OPT_TOS) != 0) {
+  if constexpr ((OPT & OPT_SSTACK) != 0) {
+    uint2* ring = ring_array();
+    const int k = s.sp & (kRing - 1);
+    e = ring[k * kBlock];
+    if (s.sp >= kRing) ring[k * kBlock] = stack[s.sp - kRing];
+  } else if constexpr ((OPT & OPT_TOS) != 0) {
     e = s.top;
     if (s.sp > 0) s.top = stack[s.sp - 1];
   } else {
@@ -630,6 +653,8 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
   constexpr bool kSplit = CULL != 0 && (LUTV == 2 || (LUTV == 0 && RR <= 6)) &&
                           (OPT & (OPT_PAIR | OPT_SPEC)) != 0;
   constexpr bool kDefer = (OPT & OPT_DEFER) != 0;
+  static_assert((OPT & OPT_SSTACK) == 0 || (OPT & (OPT_TOS | OPT_DEFER)) == 0,
+                "one stack placement at a time");
   static_assert(!kDefer || (CULL == 2 && LUTV == 2 && kTrisPerStep == 1 &&
                             (OPT & (OPT_PAIR | OPT_SPEC | OPT_TOS)) == 0),
                 "the deferred test is built for the compressed bit table alone");
@@ -850,7 +875,8 @@ constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 template <int R, int CULL, int MODE, int LUTV, int SCALES, int STACK = kStack, int OPT = 0>
 __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2* stack,
                                             const SharedTables<(R > 0 ? R : 4), LUTV>& sh) {
-  static_assert((OPT & (OPT_PAIR | OPT_SPEC | OPT_TOS)) == 0, "binary-step options only");
+  static_assert((OPT & (OPT_PAIR | OPT_SPEC | OPT_TOS | OPT_SSTACK)) == 0,
+                "binary-step options only");
   constexpr int RR = (R > 0 ? R : 4);
   constexpr int MB = MaskTraits<RR>::kStrideBytes;
   bool done = false;
@@ -884,30 +910,47 @@ __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2*
       }
     } else {
       const float4* nd = p.nodes + (long long)s.cur * p.node_f4;
-      const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
-      const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5);
       const uint4 sl = __ldg(reinterpret_cast<const uint4*>(nd + 6));
       const uint32_t slot[4] = {sl.x, sl.y, sl.z, sl.w};
-      const float lo[4][3] = {{lx.x, ly.x, lz.x}, {lx.y, ly.y, lz.y}, {lx.z, ly.z, lz.z},
-                              {lx.w, ly.w, lz.w}};
-      const float hi[4][3] = {{hx.x, hy.x, hz.x}, {hx.y, hy.y, hz.y}, {hx.z, hy.z, hz.z},
-                              {hx.w, hy.w, hz.w}};
-      const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+      // slab tests one axis at a time over the four children: only one
+      // axis's bounds are live at once.  The min / max grouping is the
+      // binary step's: tn = max(max(near_x, near_y), max(near_z, tmin)),
+      // tf = min(min(far_x, far_y), min(far_z, tcur)).
       float tn[4], tf[4];
-      bool hit[4];
+      {
+        const float4 l = __ldg(nd), h = __ldg(nd + 3);
+        const float lv[4] = {l.x, l.y, l.z, l.w}, hv[4] = {h.x, h.y, h.z, h.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float a0[3], a1[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          a0[k] = __fmul_rn(__fsub_rn(lo[c][k], o[k]), inv[k]);
-          a1[k] = __fmul_rn(__fsub_rn(hi[c][k], o[k]), inv[k]);
+        for (int c = 0; c < 4; ++c) {
+          const float a0 = __fmul_rn(__fsub_rn(lv[c], s.ox), s.ix);
+          const float a1 = __fmul_rn(__fsub_rn(hv[c], s.ox), s.ix);
+          tn[c] = fminf(a0, a1);
+          tf[c] = fmaxf(a0, a1);
         }
-        tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
-                      fmaxf(fminf(a0[2], a1[2]), s.tmin));
-        tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
-                      fminf(fmaxf(a0[2], a1[2]), s.tcur));
-        hit[c] = slot[c] != kNoSlot && tn[c] <= __fmul_rn(tf[c], kRobust);
+      }
+      {
+        const float4 l = __ldg(nd + 1), h = __ldg(nd + 4);
+        const float lv[4] = {l.x, l.y, l.z, l.w}, hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float a0 = __fmul_rn(__fsub_rn(lv[c], s.oy), s.iy);
+          const float a1 = __fmul_rn(__fsub_rn(hv[c], s.oy), s.iy);
+          tn[c] = fmaxf(tn[c], fminf(a0, a1));
+          tf[c] = fminf(tf[c], fmaxf(a0, a1));
+        }
+      }
+      bool hit[4];
+      {
+        const float4 l = __ldg(nd + 2), h = __ldg(nd + 5);
+        const float lv[4] = {l.x, l.y, l.z, l.w}, hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float a0 = __fmul_rn(__fsub_rn(lv[c], s.oz), s.iz);
+          const float a1 = __fmul_rn(__fsub_rn(hv[c], s.oz), s.iz);
+          tn[c] = fmaxf(tn[c], fmaxf(fminf(a0, a1), s.tmin));
+          tf[c] = fminf(tf[c], fminf(fmaxf(a0, a1), s.tcur));
+          hit[c] = slot[c] != kNoSlot && tn[c] <= __fmul_rn(tf[c], kRobust);
+        }
       }
       s.ntest += (slot[2] != kNoSlot ? 1u : 0u) + (slot[3] != kNoSlot ? 1u : 0u) + 2u;
       if constexpr (CULL != 0) {
@@ -918,21 +961,18 @@ __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2*
         for (int c = 0; c < 4; ++c)
           if (hit[c] && !(meta[c] & kMetaFull)) need |= 1u << c;
         if (need) {
-          const float4 sx = __ldg(nd + 8), sy = __ldg(nd + 9), sz = __ldg(nd + 10);
-          const float scl[4][3] = {{sx.x, sy.x, sz.x}, {sx.y, sy.y, sz.y}, {sx.z, sy.z, sz.z},
-                                   {sx.w, sy.w, sz.w}};
+          const float o[3] = {s.ox, s.oy, s.oz};
           const float d[3] = {s.dx, s.dy, s.dz};
+          const float* rec = reinterpret_cast<const float*>(nd);
           const uint8_t* objs = reinterpret_cast<const uint8_t*>(nd + p.mask_off_f4);
-          // one test per needed child; a lane runs only its own
+          // one test per needed child; a lane runs only its own.  The
+          // child's lower corner and scales are read again from the record
+          // (float c of rows 0..2 and 8..10), already in L1.
           while (need) {
             const int c = __ffs(need) - 1;
             need &= need - 1u;
-            float l3[3], s3[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              l3[k] = c == 0 ? lo[0][k] : c == 1 ? lo[1][k] : c == 2 ? lo[2][k] : lo[3][k];
-              s3[k] = c == 0 ? scl[0][k] : c == 1 ? scl[1][k] : c == 2 ? scl[2][k] : scl[3][k];
-            }
+            const float l3[3] = {__ldg(rec + c), __ldg(rec + 4 + c), __ldg(rec + 8 + c)};
+            const float s3[3] = {__ldg(rec + 32 + c), __ldg(rec + 36 + c), __ldg(rec + 40 + c)};
             const float tnc = c == 0 ? tn[0] : c == 1 ? tn[1] : c == 2 ? tn[2] : tn[3];
             const float tfc = c == 0 ? tf[0] : c == 1 ? tf[1] : c == 2 ? tf[2] : tf[3];
             const unsigned mc = c == 0 ? meta[0] : c == 1 ? meta[1] : c == 2 ? meta[2] : meta[3];

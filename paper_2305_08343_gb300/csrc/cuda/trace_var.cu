@@ -1,6 +1,6 @@
 // trace_var.cu — kernels with non-default OPT bits (trace_kernel.cuh): the
-// fused Alg. 1 cell form, and the load-scheduling, stack and bounce-sort
-// options, for the R = 6 images (uncompressed masks with the full table,
+// fused Alg. 1 cell form, and the load-scheduling, stack-placement and
+// bounce-sort options, for the R = 6 images (uncompressed masks with the full table,
 // compressed masks with the bit table) and the plain traversal, in the
 // single-batch kernel and the wave pipeline (block 128, stack 64).
 #include "trace_kernel.cuh"
@@ -23,7 +23,7 @@ WaveKernelFn waves_of() {
 #define SCT_OPTS(X)                                                                   \
   X(OPT_FUSED) X(OPT_PAIR) X(OPT_SPEC) X(OPT_TOS) X(OPT_SPEC | OPT_TOS) X(OPT_SORT) \
   X(OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_FUSED | OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_DEFER) \
-  X(OPT_LAZY)
+  X(OPT_LAZY) X(OPT_SSTACK)
 
 }  // namespace
 

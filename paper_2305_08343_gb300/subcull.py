@@ -80,6 +80,7 @@ SC_VARIANT_TOS = 8
 SC_VARIANT_SORT = 16
 SC_VARIANT_DEFER = 32
 SC_VARIANT_LAZY = 64
+SC_VARIANT_SSTACK = 128
 
 
 class sc_tune_result(C.Structure):
@@ -138,6 +139,9 @@ def lib():
             "sc_trace_waves": (C.c_int, [vp, vp, i64, C.c_int, C.c_uint32, C.c_int,
                                          P(sc_wave_out), P(sc_trace_opts), vp, C.c_size_t, vp]),
             "sc_waves_poll": (C.c_int, [vp, C.c_int, u32p, vp]),
+            "sc_trace_waves_host": (C.c_int, [vp, vp, i64, C.c_int, C.c_uint32, C.c_int,
+                                              P(sc_wave_out), P(sc_trace_opts), vp,
+                                              P(sc_wave_out), vp, C.c_size_t, u32p, vp]),
             "sc_bvh_frontier": (C.c_int, [vp, C.c_int, vp, C.c_int, P(C.c_int), u8p]),
             "sc_trace_seeded": (C.c_int, [vp, vp, i64, vp, vp, C.c_int, vp, vp, C.c_int,
                                           P(sc_trace_opts), vp, C.c_size_t, vp]),
@@ -474,6 +478,25 @@ def sc_trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, ou
     _check(lib().sc_trace_waves(dbvh.handle, C.c_void_p(rays.data_ptr()), n0, bounces,
                                 seed & 0xFFFFFFFF, cull, arr, C.byref(o),
                                 C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+
+
+def sc_trace_waves_host(dbvh: DeviceBVH, h_rays, bounces: int, seed: int, cull: int, h_outs,
+                        d_rays, d_outs, ws, opts: sc_trace_opts | None = None, stream=None):
+    """End to end through the C-ABI: h_rays (host float32[n0, 8] tensor,
+    ideally pinned) in, the wave pipeline, each wave's entries out to h_outs
+    (host tensors laid out like sc_trace_waves' outs); d_rays / d_outs are
+    the device buffers.  Returns the wave sizes (sizes[0] = n0)."""
+    n0 = h_rays.shape[0]
+    ha, da = _wave_arr(h_outs, bounces), _wave_arr(d_outs, bounces)
+    o = opts or _opts()
+    sizes = np.zeros(bounces + 1, np.uint32)
+    _check(lib().sc_trace_waves_host(dbvh.handle, C.c_void_p(h_rays.data_ptr()), n0, bounces,
+                                     seed & 0xFFFFFFFF, cull, ha, C.byref(o),
+                                     C.c_void_p(d_rays.data_ptr()), da,
+                                     C.c_void_p(ws.data_ptr()), ws.numel(),
+                                     _ptr(sizes, C.c_uint32), _stream_ptr(stream)))
+    sizes[0] = n0
+    return sizes
 
 
 def sc_waves_poll(ws, bounces: int, stream=None):

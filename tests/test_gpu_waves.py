@@ -195,3 +195,36 @@ def test_wide_waves_match_oracle(cull, comp, lut, block):
         assert np.array_equal(g[w]["id"], o[w]["id"]), w
         assert np.array_equal(g[w]["t"], o[w]["t"]), w
         assert np.array_equal(g[w]["counts"], o[w]["counts"]), w
+
+
+def test_waves_host_entry_point_matches_device_pipeline():
+    """sc_trace_waves_host (host rays in, each wave's entries copied back)
+    gives, per wave, the sizes, paths, hits and counts of sc_trace_waves on
+    device buffers."""
+    tris = sg.hair(500, 16, True, seed=37)
+    rays = sg.pinhole(96, 48)
+    b = sc.sc_bvh_build(tris, 6, 1)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    r = torch.from_numpy(rays).cuda()
+    ref, sizes = sc.trace_waves(d, r, 2, 11, 1)
+    torch.cuda.synchronize()
+    n = rays.shape[0]
+    h_rays = torch.from_numpy(rays).pin_memory()
+    h_outs = [(torch.full((n, 4), -9.0).pin_memory(), torch.full((n,), -9, dtype=torch.int32).pin_memory(),
+               torch.full((n, 2), -9, dtype=torch.int32).pin_memory(), None) for _ in range(3)]
+    bufs = sc.WaveBuffers(n, 2, with_counts=True)
+    d_rays = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    got = sc.sc_trace_waves_host(d, h_rays, 2, 11, 1, h_outs, d_rays, bufs.outs(), bufs.ws)
+    assert list(got) == list(sizes)
+    for w in range(3):
+        m = int(sizes[w])
+        hp, hh, hc = h_outs[w][1][:m].numpy(), h_outs[w][0][:m].numpy(), h_outs[w][2][:m].numpy()
+        rp = ref.path[w][:m].cpu().numpy()
+        rh = ref.hits[w][:m].cpu().numpy()
+        rc = ref.counts[w][:m].cpu().numpy()
+        a, b_ = np.argsort(hp, kind="stable"), np.argsort(rp, kind="stable")
+        assert np.array_equal(hp[a], rp[b_])
+        assert np.array_equal(hh[a].view(np.int32), rh[b_].view(np.int32))
+        assert np.array_equal(hc[a], rc[b_])
+        if m < n:
+            assert (h_outs[w][1][m:].numpy() == -9).all()  # nothing past the wave
