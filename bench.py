@@ -714,6 +714,67 @@ def run_gpu(args):
     ok_e2e = [int(x) for x in szs] == [int(x) for x in sizes]
     e2e["identical_wave_sizes"] = ok_e2e
 
+    # roofline of the wave kernel.  Algorithmic bytes per ray (the method's
+    # own fetches, from the exact per-ray counters): 32 (ray) + 16 (hit) +
+    # node visits x B_node + triangle tests x 48, plus 32 per spawned bounce
+    # ray.  B_node is the method's record: a 64-byte child pair, plus the two
+    # R^3-bit masks when uncompressed (80 / 128 / 192 bytes at R = 4 / 6 / 8);
+    # the image's own records (stored scales, 4-wide layouts) are reported
+    # beside it as record_bytes_per_ray.
+    mstride = {4: 8, 6: 32, 8: 64}[R]
+    b_node = 64 + (0 if comp else 2 * mstride)
+    if wide:
+        # a 4-wide node is made from every binary node at even depth and
+        # holds 2 + its inner children: node tests / mean children = visits
+        rec_bytes = 176 + (0 if comp else 4 * mstride)
+        visits = cnt_c[0] / mean_wide_children(bvh)
+        b_node_w = 2 * b_node
+    else:
+        rec_bytes = (96 if args.layout in (1, 5) else 64) + (0 if comp else 2 * mstride)
+        visits = cnt_c[0] / 2.0
+        b_node_w = b_node
+    spawned = float(np.sum(sizes[1:])) / rays_per_step
+    b_ray = 32 + 16 + visits * b_node_w + cnt_c[1] * 48 + spawned * 32
+    b_ray_rec = 32 + 16 + 4 + visits * rec_bytes + cnt_c[1] * 48 + spawned * (32 + 4)
+    per_launch_bytes = b_ray * rays_per_step
+    avg_ms = float(np.mean(ms_cull))
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    peaks = load_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic, traffic_src = measured_traffic(args.workload)
+    if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
+            or args.leaf_min or args.L != 3 or args.max_leaf != 4 or wide
+            or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
+            or opts.variant != DEFAULT_VARIANT):
+        traffic, traffic_src = None, None  # measured for the default configuration only
+    l2_peak, l2_mb = measure_l2_peak(dev)
+    # The bound: DRAM traffic far below the algorithmic bytes means the
+    # fetched bytes come from L2 (the working set of one frame stays there),
+    # so the L2 read bandwidth is the roofline; HBM otherwise.
+    on_chip = traffic is not None and traffic < 0.25 * per_launch_bytes
+    if traffic is None:
+        bound_basis = ("no DRAM capture of this kernel source: bound taken as HBM; the "
+                       "fraction against L2 is given beside it")
+    elif on_chip:
+        bound_basis = (f"DRAM traffic {traffic / 1e9:.2f} GB per launch is "
+                       f"{100 * traffic / per_launch_bytes:.1f}% of the algorithmic bytes")
+    else:
+        bound_basis = "DRAM traffic is a large part of the algorithmic bytes"
+    bound_l2 = on_chip and bool(l2_peak)
+    peak = l2_peak if bound_l2 else hbm_peak
+    roofline = {"bound": "l2" if bound_l2 else "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": traffic_src, "bound_basis": bound_basis,
+                "peak_source": ("measured (sc_l2_read probe, this run)" if bound_l2 else
+                                ("measured" if peaks else "fallback")),
+                "bytes_per_ray": b_ray, "b_node": b_node, "node_visits_per_ray": visits,
+                "record_bytes_per_ray": b_ray_rec, "record_bytes": rec_bytes,
+                "kernel": "waves_kernel (culled)",
+                "hbm_peak": hbm_peak, "frac_hbm": achieved / hbm_peak,
+                "l2_peak": l2_peak, "frac_l2": achieved / l2_peak if l2_peak else None,
+                "l2_peak_source": f"sc_l2_read probe, best over 16-64 MB resident buffers "
+                                  f"({l2_mb} MB), measured in this run"}
+
     # Test selection (an option beside the paper's method, which tests
     # every child): children whose decoded mask has at least skip_bits bits
     # set are kept untested.  Same hits; counts between the fully tested
