@@ -129,6 +129,80 @@ __device__ __forceinline__ void cell_coords(float o, float d, float lo, float s,
   }
 }
 
+// Two FP32 lanes in one 64-bit register pair, and the sm_100-family packed
+// operations on them (add / sub / mul .rn.f32x2): each lane is rounded to
+// nearest exactly as the scalar __fadd_rn / __fsub_rn / __fmul_rn, so the
+// packed forms below give the same bits as the scalar ones.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(f2x r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// Alg. 1 cell coordinates of both segment ends on all three axes: x and y
+// as packed pairs, z scalar (the same operations, lane by lane, as
+// cell_coords); the fused option stays scalar.
+template <int OPT>
+__device__ __forceinline__ void cell_coords3(const float* o, const float* d, const float* lo,
+                                             const float* sk, float tn, float tf, float* q0,
+                                             float* q1) {
+  if constexpr ((OPT & OPT_FUSED) != 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cell_coords<OPT>(o[k], d[k], lo[k], sk[k], tn, tf, q0[k], q1[k]);
+  } else {
+    const f2x oxy = pk2(o[0], o[1]), dxy = pk2(d[0], d[1]);
+    const f2x lxy = pk2(lo[0], lo[1]), sxy = pk2(sk[0], sk[1]);
+    const f2x a = mul2(sub2(add2(oxy, mul2(pk2(tn, tn), dxy)), lxy), sxy);
+    const f2x b = mul2(sub2(add2(oxy, mul2(pk2(tf, tf), dxy)), lxy), sxy);
+    up2(a, q0[0], q0[1]);
+    up2(b, q1[0], q1[1]);
+    cell_coords<OPT>(o[2], d[2], lo[2], sk[2], tn, tf, q0[2], q1[2]);
+  }
+}
+
+// Slab tests of the two children of a binary record (f0..f2 in the layout
+// {lo0.xy, hi0.xy} {lo1.xy, hi1.xy} {lo0.z, hi0.z, lo1.z, hi1.z}): entry
+// and exit distances clipped to [tmin, tcur], x and y as packed pairs.
+// tn = max(max(near_x, near_y), max(near_z, tmin)), tf = min(min(far_x,
+// far_y), min(far_z, tcur)); hit iff tn <= tf * kRobust.
+__device__ __forceinline__ void slab2(const float4 f0, const float4 f1, const float4 f2,
+                                      float ox, float oy, float oz, float ix, float iy, float iz,
+                                      float tmin, float tcur, float* tn, float* tf, bool* hit) {
+  const f2x oxy = pk2(ox, oy), ixy = pk2(ix, iy);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float4 f = c ? f1 : f0;
+    const float loz = c ? f2.z : f2.x, hiz = c ? f2.w : f2.y;
+    float a0x, a0y, a1x, a1y;
+    up2(mul2(sub2(pk2(f.x, f.y), oxy), ixy), a0x, a0y);
+    up2(mul2(sub2(pk2(f.z, f.w), oxy), ixy), a1x, a1y);
+    const float a0z = __fmul_rn(__fsub_rn(loz, oz), iz);
+    const float a1z = __fmul_rn(__fsub_rn(hiz, oz), iz);
+    tn[c] = fmaxf(fmaxf(fminf(a0x, a1x), fminf(a0y, a1y)), fmaxf(fminf(a0z, a1z), tmin));
+    tf[c] = fminf(fminf(fmaxf(a0x, a1x), fmaxf(a0y, a1y)), fminf(fmaxf(a0z, a1z), tcur));
+    hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
+  }
+}
+
 template <int R>
 __device__ __forceinline__ float scale_of(float lo, float hi) {
   return __fdiv_rn((float)R, fmaxf(__fsub_rn(hi, lo), 1e-30f));
@@ -387,12 +461,14 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
         reinterpret_cast<const uint8_t*>(p.lut2) + ((size_t)beg2 * (R2 * R2 * R2) + end2) * MB;
     return masks_overlap<R>(rm, obj);
   }
+  {
+    float q0[3], q1[3];
+    cell_coords3<OPT>(o, d, lo, sk, tn, tf, q0, q1);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float q0, q1;
-    cell_coords<OPT>(o[k], d[k], lo[k], sk[k], tn, tf, q0, q1);
-    cb[k] = cell_of_q<R>(q0);
-    ce[k] = cell_of_q<R>(q1);
+    for (int k = 0; k < 3; ++k) {
+      cb[k] = cell_of_q<R>(q0[k]);
+      ce[k] = cell_of_q<R>(q1[k]);
+    }
   }
   const int beg = cb[0] + R * cb[1] + R * R * cb[2];
   const int end = ce[0] + R * ce[1] + R * R * ce[2];
@@ -475,13 +551,13 @@ __device__ __forceinline__ uint2 stack_pop(RayState& s, uint2* stack) {
 template <int R, int OPT>
 __device__ __forceinline__ int2 cell_pair(const float* o, const float* d, const float* lo,
                                           const float* sk, float tn, float tf) {
+  float q0[3], q1[3];
+  cell_coords3<OPT>(o, d, lo, sk, tn, tf, q0, q1);
   int cb[3], ce[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    float q0, q1;
-    cell_coords<OPT>(o[k], d[k], lo[k], sk[k], tn, tf, q0, q1);
-    cb[k] = cell_of_q<R>(q0);
-    ce[k] = cell_of_q<R>(q1);
+    cb[k] = cell_of_q<R>(q0[k]);
+    ce[k] = cell_of_q<R>(q1[k]);
   }
   return make_int2(cb[0] + R * cb[1] + R * R * cb[2], ce[0] + R * ce[1] + R * R * ce[2]);
 }
@@ -576,29 +652,13 @@ __device__ __forceinline__ bool trace_inner_deferred(const Params& p, RayState& 
   const uint32_t s0 = __float_as_uint(rc.f3.x), s1 = __float_as_uint(rc.f3.y);
   const uint32_t m0 = __float_as_uint(rc.f3.z), m1 = __float_as_uint(rc.f3.w);
   s.ntest += 2;
-  const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-  const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-  const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+  const float lo0[3] = {f0.x, f0.y, f2.x}, lo1[3] = {f1.x, f1.y, f2.z};
+  const float o[3] = {s.ox, s.oy, s.oz};
   const float d[3] = {s.dx, s.dy, s.dz};
-  const float sc0[3] = {rc.f4.x, rc.f4.y, rc.f4.z}, sc1[3] = {rc.f4.w, rc.f5.x, rc.f5.y};
+  const float sc0[3] = {rc.f4.x, rc.f4.y, rc.f5.x}, sc1[3] = {rc.f4.z, rc.f4.w, rc.f5.y};
   float tn[2], tf[2];
   bool hit[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const float* lo = c ? lo1 : lo0;
-    const float* hi = c ? hi1 : hi0;
-    float a0[3], a1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
-      a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
-    }
-    tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
-                  fmaxf(fminf(a0[2], a1[2]), s.tmin));
-    tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
-                  fminf(fmaxf(a0[2], a1[2]), s.tcur));
-    hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
-  }
+  slab2(f0, f1, f2, s.ox, s.oy, s.oz, s.ix, s.iy, s.iz, s.tmin, s.tcur, tn, tf, hit);
   uint32_t code[2] = {kNoTest, kNoTest};
   if (hit[0] && !(m0 & kMetaFull)) {
     const int2 be = cell_pair<R, 0>(o, d, lo0, sc0, tn[0], tf[0]);
@@ -760,27 +820,12 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
       const uint4 f3 = make_uint4(__float_as_uint(rc.f3.x), __float_as_uint(rc.f3.y),
                                   __float_as_uint(rc.f3.z), __float_as_uint(rc.f3.w));
       s.ntest += 2;
-      const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-      const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-      const float o[3] = {s.ox, s.oy, s.oz}, inv[3] = {s.ix, s.iy, s.iz};
+      const float lo0[3] = {f0.x, f0.y, f2.x}, hi0[3] = {f0.z, f0.w, f2.y};
+      const float lo1[3] = {f1.x, f1.y, f2.z}, hi1[3] = {f1.z, f1.w, f2.w};
+      const float o[3] = {s.ox, s.oy, s.oz};
       float tn[2], tf[2];
       bool hit[2];
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float* lo = c ? lo1 : lo0;
-        const float* hi = c ? hi1 : hi0;
-        float a0[3], a1[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          a0[k] = __fmul_rn(__fsub_rn(lo[k], o[k]), inv[k]);
-          a1[k] = __fmul_rn(__fsub_rn(hi[k], o[k]), inv[k]);
-        }
-        tn[c] = fmaxf(fmaxf(fminf(a0[0], a1[0]), fminf(a0[1], a1[1])),
-                      fmaxf(fminf(a0[2], a1[2]), s.tmin));
-        tf[c] = fminf(fminf(fmaxf(a0[0], a1[0]), fmaxf(a0[1], a1[1])),
-                      fminf(fmaxf(a0[2], a1[2]), s.tcur));
-        hit[c] = tn[c] <= __fmul_rn(tf[c], kRobust);
-      }
+      slab2(f0, f1, f2, s.ox, s.oy, s.oz, s.ix, s.iy, s.iz, s.tmin, s.tcur, tn, tf, hit);
       const uint32_t s0 = f3.x, s1 = f3.y;
       uint32_t spec_slot = kLeaf;  // a leaf word: nothing fetched
       if constexpr (CULL != 0) {
@@ -795,8 +840,8 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
         }
         float sc[2][3];
         if constexpr (SCALES) {
-          sc[0][0] = rc.f4.x; sc[0][1] = rc.f4.y; sc[0][2] = rc.f4.z;
-          sc[1][0] = rc.f4.w; sc[1][1] = rc.f5.x; sc[1][2] = rc.f5.y;
+          sc[0][0] = rc.f4.x; sc[0][1] = rc.f4.y; sc[0][2] = rc.f5.x;
+          sc[1][0] = rc.f4.z; sc[1][1] = rc.f4.w; sc[1][2] = rc.f5.y;
         } else {
 #pragma unroll
           for (int c = 0; c < 2; ++c)

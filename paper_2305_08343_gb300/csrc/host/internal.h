@@ -91,13 +91,14 @@ void raylut2r_full(int R, uint32_t* out);
 
 // ---------------------------------------------------------- device image --
 // Node record (child pair), 16-byte aligned, fetched as float4s:
-//   f0 = {lo0.x, lo0.y, lo0.z, hi0.x}  f1 = {hi0.y, hi0.z, lo1.x, lo1.y}
-//   f2 = {lo1.z, hi1.x, hi1.y, hi1.z}  f3 = {slot0, slot1, meta0, meta1}
+//   f0 = {lo0.x, lo0.y, hi0.x, hi0.y}  f1 = {lo1.x, lo1.y, hi1.x, hi1.y}
+//   f2 = {lo0.z, hi0.z, lo1.z, hi1.z}  f3 = {slot0, slot1, meta0, meta1}
 // slot: inner -> child node index (>= 0); leaf -> 0x80000000 |
 // (count-1) << 28 | first triangle position.  meta: compression LUT index.
 // meta bit 8: the child's (decoded) mask is all ones, so its culling test
 // cannot remove it.  SC_LAYOUT_MASKED stores the scales R / max(extent,
-// 1e-30) of both children at +64 (six floats, two pad); the two uncompressed
+// 1e-30) of both children at +64 as {s0.x, s0.y, s1.x, s1.y} {s0.z, s1.z,
+// 0, 0}; the two uncompressed
 // masks follow at mask_off and mask_off + mask_stride.
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr uint32_t kMetaFull = 0x100u;

@@ -1,10 +1,14 @@
 // layout.cpp — the device image of a BVH (node records, triangles, tables).
 //
 // Nodes are child pairs of 64 bytes (four 16-byte vectors, one 128-bit load
-// each).  The masked layout adds the two children's Alg. 1 scales
+// each): {lo0.x, lo0.y, hi0.x, hi0.y} {lo1.x, lo1.y, hi1.x, hi1.y}
+// {lo0.z, hi0.z, lo1.z, hi1.z} {slot0, slot1, meta0, meta1}, so that each
+// child's x, y bounds are adjacent for packed two-lane arithmetic.  The
+// masked layout adds the two children's Alg. 1 scales
 // R / extent (32 bytes) and, uncompressed, the two R^3-bit object masks
 // (mask_stride bytes each, zero padded): 112 / 160 / 224 bytes at
-// R = 4 / 6 / 8; compressed, the 1-byte LUT index of each child sits in the
+// R = 4 / 6 / 8, as {s0.x, s0.y, s1.x, s1.y} {s0.z, s1.z, 0, 0}; compressed,
+// the 1-byte LUT index of each child sits in the
 // fourth vector (Sec. 3.2.4: the index replaces the mask) and the node is
 // 96 bytes.  The compact masked layout omits the scales (80 / 128 / 192 and
 // 64 bytes).  Records stay 16-byte aligned.
@@ -257,9 +261,11 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
     float* f = reinterpret_cast<float*>(rec);
     const float* b0 = &b.box[12 * n];
     const float* b1 = b0 + 6;
-    f[0] = b0[0]; f[1] = b0[1]; f[2] = b0[2]; f[3] = b0[3];
-    f[4] = b0[4]; f[5] = b0[5]; f[6] = b1[0]; f[7] = b1[1];
-    f[8] = b1[2]; f[9] = b1[3]; f[10] = b1[4]; f[11] = b1[5];
+    // {lo0.xy, hi0.xy} {lo1.xy, hi1.xy} {lo0.z, hi0.z, lo1.z, hi1.z}: each
+    // child's x, y bounds sit in adjacent lanes for the packed slab test
+    f[0] = b0[0]; f[1] = b0[1]; f[2] = b0[3]; f[3] = b0[4];
+    f[4] = b1[0]; f[5] = b1[1]; f[6] = b1[3]; f[7] = b1[4];
+    f[8] = b0[2]; f[9] = b0[5]; f[10] = b1[2]; f[11] = b1[5];
     uint32_t* u = reinterpret_cast<uint32_t*>(rec + 48);
     u[0] = slot_word(b.child[2 * n], b.count[2 * n]);
     u[1] = slot_word(b.child[2 * n + 1], b.count[2 * n + 1]);
@@ -272,12 +278,16 @@ void pack_image(const Bvh& b, const ImageLayout& L, std::vector<uint8_t>& img) {
                       4 * L.W);
       }
       if (L.scales) {
+        // {s0.x, s0.y, s1.x, s1.y} {s0.z, s1.z, 0, 0}
         float* sc = reinterpret_cast<float*>(rec + 64);
+        float v[2][3];
         for (int c = 0; c < 2; ++c)
           for (int k = 0; k < 3; ++k) {
             const float* bx = &b.box[12 * n + 6 * c];
-            sc[3 * c + k] = (float)L.R / std::fmax(bx[3 + k] - bx[k], 1e-30f);
+            v[c][k] = (float)L.R / std::fmax(bx[3 + k] - bx[k], 1e-30f);
           }
+        sc[0] = v[0][0]; sc[1] = v[0][1]; sc[2] = v[1][0]; sc[3] = v[1][1];
+        sc[4] = v[0][2]; sc[5] = v[1][2]; sc[6] = 0.0f; sc[7] = 0.0f;
       }
     }
   });
