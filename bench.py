@@ -60,12 +60,12 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "
 # SHA-256 of the traversal kernel header.
 MEASURED_TRAFFIC = {
     # workload: (bytes per launch, kernel source sha256, profile summary)
-    "hair1m": (1.681529e9 + 0.245082e9,
-               "4ceeb1bf8057b738464c49fd38c8e76afd7bd25785121df83d8411c6c80bd499",
-               "profiles/waves_kernel_hair1m.md"),
-    "hair12m": (1.852002e9 + 0.380839e9,
-                "4ceeb1bf8057b738464c49fd38c8e76afd7bd25785121df83d8411c6c80bd499",
+    "hair12m": (1.983838e9 + 0.398654e9,
+                "4615e02414128b73b8c1fe3b8d2bca708ee82ef02ba120ab30e6c7bc38a3ae0d",
                 "profiles/waves_kernel_hair12m.md"),
+    "hair1m": (1.732292e9 + 0.259648e9,
+               "4615e02414128b73b8c1fe3b8d2bca708ee82ef02ba120ab30e6c7bc38a3ae0d",
+               "profiles/waves_kernel_hair1m.md"),
 }
 
 
