@@ -726,11 +726,12 @@ def run_gpu(args):
     if wide:
         # a 4-wide node is made from every binary node at even depth and
         # holds 2 + its inner children: node tests / mean children = visits
-        rec_bytes = 176 + (0 if comp else 4 * mstride)
+        rec_bytes = 176 if comp else 192 + 4 * mstride
         visits = cnt_c[0] / mean_wide_children(bvh)
         b_node_w = 2 * b_node
     else:
         rec_bytes = (96 if args.layout in (1, 5) else 64) + (0 if comp else 2 * mstride)
+        rec_bytes = (rec_bytes + 31) // 32 * 32  # records are whole 32-byte sectors
         visits = cnt_c[0] / 2.0
         b_node_w = b_node
     spawned = float(np.sum(sizes[1:])) / rays_per_step

@@ -207,7 +207,8 @@ enum {
   SC_LAYOUT_MASKED = 1,        /* masks (or LUT indices) plus each child's
                                   Alg. 1 scales R/extent precomputed in the
                                   node: 96 B compressed, 64+32+2*mask bytes
-                                  uncompressed                             */
+                                  uncompressed, rounded up to a multiple of
+                                  32 B (128 / 160 / 224 B at R = 4 / 6 / 8) */
   SC_LAYOUT_PLAIN4 = 3,        /* 4-wide nodes without masks (see below)         */
   SC_LAYOUT_MASKED4 = 4,       /* 4-wide nodes with masks (or LUT indices) and
                                   scales.  4-wide nodes (the paper's Sec. 3.2.4
@@ -221,13 +222,15 @@ enum {
                                   four children, the four slot words (unused:
                                   0xFFFFFFFF), the four meta words, then (masked)
                                   the four children's scales as three float4
-                                  and the four masks: 128 bytes plain, 176
-                                  compressed, 176 + 4 mask strides else.
+                                  and, from byte 192, the four masks: 128
+                                  bytes plain, 176 compressed, 192 + 4 mask
+                                  strides else.
                                   Children are visited by entry distance,
                                   ties by position. */
   SC_LAYOUT_MASKED_COMPACT = 2, /* masks (or LUT indices) only; the scales are
                                   divided on the fly: 64 B compressed,
-                                  64+2*mask bytes uncompressed               */
+                                  64+2*mask bytes uncompressed, rounded up to
+                                  a multiple of 32 B (96 / 128 / 192 B)      */
   SC_LAYOUT_MASKED_RAY2R = 5   /* SC_LAYOUT_MASKED plus the ray-mask table at
                                   R_ray = 2R (Sec. 4.2): begin and end cells
                                   on the 2R grid (twice the R-grid coordinate,

@@ -6,12 +6,14 @@
 // child's x, y bounds are adjacent for packed two-lane arithmetic.  The
 // masked layout adds the two children's Alg. 1 scales
 // R / extent (32 bytes) and, uncompressed, the two R^3-bit object masks
-// (mask_stride bytes each, zero padded): 112 / 160 / 224 bytes at
-// R = 4 / 6 / 8, as {s0.x, s0.y, s1.x, s1.y} {s0.z, s1.z, 0, 0}; compressed,
-// the 1-byte LUT index of each child sits in the
+// (mask_stride bytes each, zero padded): 128 / 160 / 224 bytes at
+// R = 4 / 6 / 8 (records are padded to whole 32-byte sectors), the scales as
+// {s0.x, s0.y, s1.x, s1.y} {s0.z, s1.z, 0, 0}; compressed, the 1-byte LUT
+// index of each child sits in the
 // fourth vector (Sec. 3.2.4: the index replaces the mask) and the node is
-// 96 bytes.  The compact masked layout omits the scales (80 / 128 / 192 and
-// 64 bytes).  Records stay 16-byte aligned.
+// 96 bytes.  The compact masked layout omits the scales (96 / 128 / 192 and
+// 64 bytes).  Records stay 32-byte aligned: the masks are compared with
+// 256-bit loads.
 // Triangles are 48 bytes in leaf order: {v0, id}, {e1 = v1 - v0}, {e2 =
 // v2 - v0}.  Every region starts on a 256-byte boundary.
 #include <cmath>
@@ -119,8 +121,10 @@ ImageLayout image_layout(const Bvh& b, int layout) {
       L.compress = b.compress;
       L.K = b.K;
       L.scales = 1;
-      L.mask_off = 176;
-      L.node_bytes = b.compress ? 176 : 176 + 4 * L.mstride;
+      // the masks start on a 32-byte boundary (16 bytes of padding after
+      // the scales): they are compared with 256-bit loads
+      L.mask_off = 192;
+      L.node_bytes = b.compress ? 176 : 192 + 4 * L.mstride;
     }
   } else {
     L.nodes = b.nn;
@@ -142,6 +146,9 @@ ImageLayout image_layout(const Bvh& b, int layout) {
     L.ray2r = layout == SC_LAYOUT_MASKED_RAY2R ? 1 : 0;
     L.mask_off = L.scales ? 96 : 64;
     L.node_bytes = b.compress ? L.mask_off : L.mask_off + 2 * L.mstride;
+    // whole 32-byte sectors: the kernels compare the masks with 256-bit
+    // loads, which need 32-byte aligned addresses
+    L.node_bytes = (L.node_bytes + 31) / 32 * 32;
   } else if (layout != SC_LAYOUT_PLAIN && layout != SC_LAYOUT_PLAIN4 &&
              layout != SC_LAYOUT_MASKED4) {
     fail(SC_ERR_ARG, "unknown layout %d", layout);
