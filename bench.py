@@ -60,11 +60,11 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "
 # SHA-256 of the traversal kernel header.
 MEASURED_TRAFFIC = {
     # workload: (bytes per launch, kernel source sha256, profile summary)
-    "hair12m": (1.983838e9 + 0.398654e9,
-                "4615e02414128b73b8c1fe3b8d2bca708ee82ef02ba120ab30e6c7bc38a3ae0d",
+    "hair12m": (1.982873e9 + 0.397949e9,
+                "473135ac74b6b2d07a132200a57971cce310ca8f90e4541e8518c2bf11347715",
                 "profiles/waves_kernel_hair12m.md"),
-    "hair1m": (1.732292e9 + 0.259648e9,
-               "4615e02414128b73b8c1fe3b8d2bca708ee82ef02ba120ab30e6c7bc38a3ae0d",
+    "hair1m": (1.730561e9 + 0.259186e9,
+               "473135ac74b6b2d07a132200a57971cce310ca8f90e4541e8518c2bf11347715",
                "profiles/waves_kernel_hair1m.md"),
 }
 

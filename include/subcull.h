@@ -377,8 +377,10 @@ sc_status sc_trace_host(const sc_dbvh* d, const float* h_rays, int64_t n,
  * blocks until its trace has finished.  The first call on a device looks up
  * the array's device address (once per device, with that device current)
  * and keeps it for the life of the process, so the library must not be used
- * across a cudaDeviceReset; make that first call before any stream capture
- * begins.  All calls share the one array, which keeps the last call's
+ * across a cudaDeviceReset.  No call can be captured in a CUDA graph (each
+ * one waits for its trace): on a capturing stream the call returns
+ * SC_ERR_STATE before it enqueues anything, and the capture stays valid.
+ * All calls share the one array, which keeps the last call's
  * contents: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialized by the caller.  Returns
  * SC_ERR_UNSUPPORTED if the trace ever needed more scratch than the array

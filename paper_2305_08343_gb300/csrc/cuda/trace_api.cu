@@ -564,6 +564,14 @@ sc_status sc_trace_noalloc(const sc_dbvh* d, const float* d_rays, int64_t n, sc_
                            uint32_t* d_counts, int mode, int cull, const sc_trace_opts* opts,
                            void* stream) {
   SC_TRY
+  {
+    // the call waits for its trace and reads the status back, which a
+    // stream capture cannot record: refuse before touching the stream
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_OK(cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      fail(SC_ERR_STATE, "sc_trace_noalloc cannot be captured: it waits for its trace");
+  }
   const size_t need = kWorkBytes;
   if (need > kNoallocScratchBytes)
     fail(SC_ERR_UNSUPPORTED,

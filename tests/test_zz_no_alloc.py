@@ -55,3 +55,33 @@ def test_noalloc_matches_workspace_trace_twice(cull):
         hit = ri >= 0
         rel = np.abs(t[hit] - rt[hit]) / np.maximum(np.abs(rt[hit]), 1e-30)
         assert (rel <= 1e-6).all() and np.array_equal(np.isinf(t), np.isinf(rt))
+
+
+def test_noalloc_refuses_stream_capture():
+    """A call on a capturing stream returns SC_ERR_STATE before it enqueues
+    anything; the capture stays valid and replays the rest of its work."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    tris = sg.hair(64, 16, True, seed=22)
+    rays = sg.pinhole(16, 16)
+    b = sc.sc_bvh_build(tris, 6, 1)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    r = torch.from_numpy(rays).cuda()
+    n = r.shape[0]
+    hits = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    counts = torch.zeros((n, 2), dtype=torch.int32, device="cuda")
+    # an uncaptured call first, so the capture below sees no first-call setup
+    sc.sc_trace_noalloc(d, r, hits, counts, sc.SC_CLOSEST, 1)
+    x = torch.zeros(4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            with pytest.raises(sc.SubcullError, match="cannot be captured"):
+                sc.sc_trace_noalloc(d, r, hits, counts, sc.SC_CLOSEST, 1)
+            x.add_(1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert x.tolist() == [1.0, 1.0, 1.0, 1.0]
