@@ -41,6 +41,8 @@ WORKLOADS = {
     "hair12m": ("12,100,000 thin hair triangles (378,125 strands x 16 x 2), seed 4; 1920x1080 "
                 "pinhole primary rays + two diffuse bounce waves; R=6 LUT-compressed masks, L=3",
                 dict(strands=378125, ground=False, seed=4), (1920, 1080), 6, 1),
+    "hair12m_unc": ("as hair12m with uncompressed R=6 masks (216 bits per child in the node "
+                    "record)", dict(strands=378125, ground=False, seed=4), (1920, 1080), 6, 0),
     "hair65k": ("65,536 hair triangles (2,048 strands), seed 1; 256x256 pinhole rays; R=6 "
                 "uncompressed", dict(strands=2048, ground=False, seed=1), (256, 256), 6, 0),
     "soup4m": ("triangle soup stress: 4,194,304 triangles in the unit cube (50% slivers of "
@@ -51,7 +53,8 @@ WORKLOADS = {
 }
 
 
-WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "soup4m": 0}
+WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair12m_unc": 2, "hair65k": 1,
+                    "soup4m": 0}
 
 
 # DRAM traffic per launch of the timed kernel (dram__bytes_read.sum +
@@ -60,11 +63,11 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair65k": 1, "
 # SHA-256 of the traversal kernel header.
 MEASURED_TRAFFIC = {
     # workload: (bytes per launch, kernel source sha256, profile summary)
-    "hair12m": (1.982873e9 + 0.397949e9,
-                "473135ac74b6b2d07a132200a57971cce310ca8f90e4541e8518c2bf11347715",
+    "hair12m": (1.986597e9 + 0.398794e9,
+                "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
                 "profiles/waves_kernel_hair12m.md"),
-    "hair1m": (1.730561e9 + 0.259186e9,
-               "473135ac74b6b2d07a132200a57971cce310ca8f90e4541e8518c2bf11347715",
+    "hair1m": (1.720535e9 + 0.259359e9,
+               "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
                "profiles/waves_kernel_hair1m.md"),
 }
 
@@ -520,7 +523,7 @@ def run_gpu(args):
     rays = torch.from_numpy(rays_np).to(dev)
     opts = sc._opts(lut_mode=args.lut, refill=args.refill,
                     variant=max(args.variant, 0) if args.variant >= 0 else DEFAULT_VARIANT)
-    opts_plain = sc._opts(lut_mode=args.lut, refill=args.refill,
+    opts_plain = sc._opts(refill=args.refill,  # the plain kernel looks nothing up
                           variant=args.plain_variant if args.plain_variant >= 0
                           else DEFAULT_PLAIN_VARIANT)
     seed = SEED
@@ -776,45 +779,67 @@ def run_gpu(args):
                 "l2_peak_source": f"sc_l2_read probe, best over 16-64 MB resident buffers "
                                   f"({l2_mb} MB), measured in this run"}
 
+    def measure_alt(comp_a, **build_kw):
+        """Culled waves on another mask build of the same tree (the GPU tree
+        builder is deterministic): counted pass, autotune, then the bench's
+        warm-up and timed steps with the L2 flushed before each."""
+        bvh_a = sc.sc_bvh_build(tris, R, comp_a, max_leaf=args.max_leaf, gpu_masks=gpu_build,
+                                gpu_bvh=gpu_build, **build_kw)
+        d_a = sc.DeviceBVH(bvh_a, args.layout)
+        o_a = sc._opts(refill=args.refill)
+        ref_a = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
+        _, sizes_a = sc.trace_waves(d_a, rays, bounces, seed, 1, ref_a, o_a)
+        wa = _sorted_waves(ref_a, sizes_a)
+        same_a = bool(np.array_equal(sizes_a, sizes))
+        cnt_a = torch.cat([x[2] for x in wa]).double().mean(0).tolist()
+        del ref_a
+        bufs_a = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
+        opts_a, _ = sc.sc_autotune_waves(d_a, rays, bounces, seed, 1, bufs_a, o_a, 3, flush)
+        ms_a = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sc.sc_trace_waves(d_a, rays, bounces, seed, 1, bufs_a.outs(), bufs_a.ws, opts_a)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                ms_a.append(e0.elapsed_time(e1))
+        sc.sc_waves_poll(bufs_a.ws, bounces)
+        same_a = same_a and all(torch.equal(x[1], h) for x, h in zip(wa, hit_ref_c))
+        v_a = rays_per_step * len(ms_a) / (float(np.sum(ms_a)) * 1e-3) / 1e6
+        out = {"mrays_s": v_a, "speedup_vs_plain": v_a / plain_value, "identical_hits": same_a,
+               "tests_per_ray": {"node": cnt_a[0], "tri": cnt_a[1],
+                                 "node_plus_tri": cnt_a[0] + cnt_a[1]},
+               "autotuned": {"block": opts_a.block, "stack": opts_a.stack,
+                             "refill": opts_a.refill},
+               "build_ms": {"bvh": bvh_a.info().ms_bvh, "masks": bvh_a.info().ms_masks,
+                            "compress": bvh_a.info().ms_compress}}
+        del d_a, bvh_a, bufs_a, wa
+        torch.cuda.empty_cache()
+        return out
+
     # Test selection (an option beside the paper's method, which tests
     # every child): children whose decoded mask has at least skip_bits bits
     # set are kept untested.  Same hits; counts between the fully tested
     # culled traversal's and plain's (the oracle applies the same rule).
     tuned_policy = None
+    uncompressed_alt = None
     if not args.no_policy and not wide and args.skip_bits == 0:
         kbits = max(1, (R ** 3 * 5) // 9)  # 120 of 216 bits at R = 6
-        bvh_t = sc.sc_bvh_build(tris, R, comp, skip_bits=kbits, L=args.L, max_leaf=args.max_leaf,
-                                gpu_masks=gpu_build, gpu_bvh=gpu_build)
-        d_t = sc.DeviceBVH(bvh_t, args.layout)
-        ref_t = sc.WaveBuffers(n, bounces, with_counts=True, device=dev)
-        _, sizes_t = sc.trace_waves(d_t, rays, bounces, seed, 1, ref_t, opts)
-        wt = _sorted_waves(ref_t, sizes_t)
-        same_t = bool(np.array_equal(sizes_t, sizes))
-        cnt_t = torch.cat([x[2] for x in wt]).double().mean(0).tolist()
-        del ref_t
-        bufs_t = sc.WaveBuffers(n, bounces, with_counts=False, device=dev)
-        opts_t, _ = sc.sc_autotune_waves(d_t, rays, bounces, seed, 1, bufs_t, opts, 3, flush)
-        ms_t = []
-        for i in range(args.warmup + args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sc.sc_trace_waves(d_t, rays, bounces, seed, 1, bufs_t.outs(), bufs_t.ws, opts_t)
-            e1.record(stream)
-            e1.synchronize()
-            if i >= args.warmup:
-                ms_t.append(e0.elapsed_time(e1))
-        sc.sc_waves_poll(bufs_t.ws, bounces)
-        hits_t = [x[1] for x in wt]
-        same_t = same_t and all(torch.equal(a, b) for a, b in zip(hits_t, hit_ref_c))
-        v_t = rays_per_step * len(ms_t) / (float(np.sum(ms_t)) * 1e-3) / 1e6
-        tuned_policy = {"skip_bits": kbits, "mrays_s": v_t, "speedup_vs_plain": v_t / plain_value,
-                        "identical_hits": same_t,
-                        "tests_per_ray": {"node": cnt_t[0], "tri": cnt_t[1],
-                                          "node_plus_tri": cnt_t[0] + cnt_t[1]},
+        tuned_policy = measure_alt(comp, skip_bits=kbits, L=args.L)
+        tuned_policy = {"skip_bits": kbits, **tuned_policy,
                         "note": "children whose decoded mask has >= skip_bits of R^3 bits set "
                                 "are kept untested (not the paper's policy)"}
-        del d_t, bvh_t, bufs_t, wt
+        if comp and R == 6:
+            # the same scene with uncompressed masks, deeper mask approximation
+            # (L = 8) and masks of >= 160 of 216 bits untested: the best
+            # culled configuration measured on this tree
+            uncompressed_alt = {"compressed": False, "L": 8, "skip_bits": 160,
+                                **measure_alt(0, skip_bits=160, L=8),
+                                "note": "uncompressed 216-bit masks in the node record "
+                                        "(160-byte records), L = 8; masks with >= 160 bits "
+                                        "set kept untested"}
 
     learned_out = None
     if not args.no_learned:
@@ -879,6 +904,7 @@ def run_gpu(args):
                                        for k, v in pct_p.items()}}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "learned_proposal": learned_out, "culled_dense_masks_untested": tuned_policy,
+        "culled_uncompressed_l8": uncompressed_alt,
         "gpu_launches": args.steps,
         "build_s": build_s, "bvh": {"nodes": info.num_nodes, "max_depth": info.max_depth,
                                     "ms_bvh": info.ms_bvh, "ms_masks": info.ms_masks,
@@ -901,7 +927,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="hair12m", choices=sorted(WORKLOADS))
     ap.add_argument("--lut", type=int, default=0,
-                    help="0 auto, 1 global table, 2 shared, 3 bit table, 4 the R_ray = 2R table")
+                    help="0 auto, 1 global table, 2 shared, 3 bit table, 4 the R_ray = 2R table, "
+                         "5 factored tables through L1 (R = 6 uncompressed)")
     ap.add_argument("--layout", type=int, default=1,
                     help="1 masked (Alg. 1 scales stored per child), 2 compact (scales "
                          "divided), 5 masked plus the R_ray = 2R table")

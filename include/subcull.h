@@ -268,7 +268,7 @@ typedef struct {
 enum { SC_CLOSEST = 0, SC_ANY = 1 };
 
 enum { SC_LUT_AUTO = 0, SC_LUT_GLOBAL = 1, SC_LUT_SHARED = 2, SC_LUT_BITTABLE = 3,
-       SC_LUT_RAY2R = 4 };
+       SC_LUT_RAY2R = 4, SC_LUT_FACTORED_L1 = 5 };
 
 typedef struct {
   int block;         /* threads per block: 0 (= 128) or 128               */
@@ -276,11 +276,18 @@ typedef struct {
   int lut_mode;      /* ray-mask lookup: SC_LUT_GLOBAL = full table through
                         L1/L2; SC_LUT_SHARED = shared memory (R = 4: the
                         whole 32-KB table and the LUT; R = 6, 8: factored
-                        per-axis-pair tables, single-batch traces only);
+                        per-axis-pair tables in single-batch traces, and
+                        in the wave pipeline for R = 6 uncompressed images
+                        with stored scales; other wave launches and
+                        seeded traces use the full table);
                         SC_LUT_BITTABLE (compressed images) = the
                         precomputed bit table of Sec. 3.2.2, one bit per
                         (ray mask, LUT entry); SC_LUT_RAY2R (images in
                         SC_LAYOUT_MASKED_RAY2R) = the R_ray = 2R table;
+                        SC_LUT_FACTORED_L1 = the factored tables read from
+                        the image through L1 (binary R = 6 uncompressed
+                        images with stored scales; seeded traces use the
+                        full table), else SC_ERR_UNSUPPORTED;
                         SC_LUT_AUTO = the 2R table when the image holds it,
                         else the bit table when compressed, else the full
                         table                                             */
@@ -324,6 +331,12 @@ enum {
                                   for nodes with a child to test            */
   SC_VARIANT_SSTACK = 128,     /* the top 8 stack entries of each ray in
                                   shared memory, the rest in local memory   */
+  SC_VARIANT_TABLE_L1 = 256,   /* rows of the full ray-mask table (R = 6,
+                                  8) and of the R_ray = 2R table, and the
+                                  uncompressed object masks, allocated in
+                                  L1 like other loads; by default they are
+                                  loaded without L1 allocation, so that
+                                  they do not evict node records            */
   SC_VARIANT_DEFER = 32        /* compressed masks with the bit table: each
                                   child's bit-table lookup is issued when the
                                   child is visited, beside its own fetch
@@ -444,7 +457,9 @@ sc_status sc_trace_waves_host(const sc_dbvh* d, const float* h_rays, int64_t n0,
                               uint32_t* sizes, void* stream);
 
 /* Autotuner of the wave pipeline: times sc_trace_waves (one warm-up, then
-   `reps` rounds over all candidates, CUDA events, median per candidate;
+   `reps` rounds over all candidates, then 2 reps + 2 more rounds over the
+   four fastest of them, CUDA events, median per candidate over all its
+   runs;
    when d_flush is not NULL its flush_bytes -- make it larger than the L2
    cache -- are overwritten before every timed run, so candidates are
    compared from a cold cache) for block size {64, 128, 256},

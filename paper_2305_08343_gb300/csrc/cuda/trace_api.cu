@@ -71,7 +71,9 @@ DevInfo device_info() {
 
 // Ray-mask lookup variant: 0 full table (global), 1 shared memory (the full
 // table at R = 4, the factored tables otherwise), 2 bit table (compressed
-// images only), 4 the R_ray = 2R table (images that hold it).  AUTO: the 2R
+// images only), 4 the R_ray = 2R table (images that hold it), 5 the
+// factored tables read through L1 (binary R = 6 uncompressed images with
+// stored scales).  AUTO: the 2R
 // table when present, else the bit table when compressed, else the full
 // table (shared-memory tables take the L1 capacity the node fetches need).
 int lut_variant(const sc_dbvh* d, int lut_mode) {
@@ -85,6 +87,12 @@ int lut_variant(const sc_dbvh* d, int lut_mode) {
     case SC_LUT_RAY2R:
       if (!d->lay.ray2r) fail(SC_ERR_ARG, "the R_ray = 2R table needs an SC_LAYOUT_MASKED_RAY2R image");
       return 4;
+    case SC_LUT_FACTORED_L1:
+      if (d->lay.R != 6 || d->lay.compress || !d->lay.scales || d->lay.width != 2)
+        fail(SC_ERR_UNSUPPORTED,
+             "the L1-read factored tables are built for binary R = 6 images with uncompressed "
+             "masks and stored scales");
+      return 5;
   }
   fail(SC_ERR_ARG, "bad lut_mode %d", lut_mode);
 }
@@ -296,7 +304,10 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
          stack);
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   int lutv = lut_variant(d, o.lut_mode);
-  if (lutv == 1 && d->lay.R != 4) lutv = 0;  // factored tables: single-batch kernel only
+  // factored tables in shared memory: built for the wave pipeline only at
+  // R = 6 with uncompressed masks and stored scales; the full table elsewhere
+  if (lutv == 1 && d->lay.R != 4 && !(d->lay.R == 6 && !d->lay.compress && d->lay.scales))
+    lutv = 0;
   sct::WaveKernelFn k = nullptr;
   if (o.variant) {
     check_variant(d, cull, lutv, o.variant);
@@ -496,7 +507,7 @@ sc_status sc_trace_seeded(const sc_dbvh* d, const float* d_rays, int64_t n, cons
   if (o.variant) fail(SC_ERR_UNSUPPORTED, "sc_trace_seeded: kernel variants are not built");
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
   int lutv = lut_variant(d, o.lut_mode);
-  if (lutv == 1 || lutv == 3) lutv = 0;
+  if (lutv == 1 || lutv == 3 || lutv == 5) lutv = 0;  // seeded traces: the full table
   sct::SeededKernelFn k = nullptr;
   if (!cull) {
     k = sct::get_seeded_plain();
@@ -730,20 +741,39 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
   CUDA_OK(cudaEventCreate(&e0));
   CUDA_OK(cudaEventCreate(&e1));
   std::vector<std::vector<float>> ms(cands.size());
+  auto median = [](std::vector<float> v) {
+    std::sort(v.begin(), v.end());
+    return v[v.size() / 2];
+  };
+  // one timed launch of candidate i, the flush buffer overwritten first
+  auto time_one = [&](size_t i, int r) {
+    if (d_flush && flush_bytes) CUDA_OK(cudaMemsetAsync(d_flush, r & 0xFF, flush_bytes, st));
+    CUDA_OK(cudaEventRecord(e0, st));
+    launch_waves(d, d_rays, n0, bounces, seed, cull, outs, &cands[i], d_ws, ws_bytes, st);
+    CUDA_OK(cudaEventRecord(e1, st));
+    CUDA_OK(cudaEventSynchronize(e1));
+    float x = 0;
+    CUDA_OK(cudaEventElapsedTime(&x, e0, e1));
+    ms[i].push_back(x);
+  };
+  std::vector<size_t> order(cands.size());
   try {
     for (auto& t : cands)  // warm-up: code, first touches
       launch_waves(d, d_rays, n0, bounces, seed, cull, outs, &t, d_ws, ws_bytes, st);
     for (int r = 0; r < reps; ++r)
-      for (size_t i = 0; i < cands.size(); ++i) {
-        if (d_flush && flush_bytes) CUDA_OK(cudaMemsetAsync(d_flush, r & 0xFF, flush_bytes, st));
-        CUDA_OK(cudaEventRecord(e0, st));
-        launch_waves(d, d_rays, n0, bounces, seed, cull, outs, &cands[i], d_ws, ws_bytes, st);
-        CUDA_OK(cudaEventRecord(e1, st));
-        CUDA_OK(cudaEventSynchronize(e1));
-        float x = 0;
-        CUDA_OK(cudaEventElapsedTime(&x, e0, e1));
-        ms[i].push_back(x);
-      }
+      for (size_t i = 0; i < cands.size(); ++i) time_one(i, r);
+    // second round: candidates a few percent apart are within the run-to-run
+    // spread of one launch, so the best kTop of the first round are timed
+    // again, interleaved, 2 reps + 2 more times each
+    std::vector<float> first(cands.size());
+    for (size_t i = 0; i < cands.size(); ++i) first[i] = median(ms[i]);
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return first[a] < first[b]; });
+    constexpr size_t kTop = 4;
+    const size_t top = std::min(kTop, order.size());
+    for (int r = 0; r < 2 * reps + 2; ++r)
+      for (size_t k = 0; k < top; ++k) time_one(order[k], reps + r);
   } catch (...) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -753,8 +783,7 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
   cudaEventDestroy(e1);
   float best_ms = 1e30f;
   for (size_t i = 0; i < cands.size(); ++i) {
-    std::sort(ms[i].begin(), ms[i].end());
-    const float med = ms[i][ms[i].size() / 2];
+    const float med = median(ms[i]);
     if (results && (int)i < cap)
       results[i] = sc_tune_result{cands[i].block, cands[i].stack, cands[i].refill,
                                   cands[i].wave_chunk, med};

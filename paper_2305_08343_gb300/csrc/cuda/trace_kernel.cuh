@@ -85,6 +85,21 @@ __device__ __forceinline__ void ldg8u(const void* p, uint4& a, uint4& b) {
       : "l"(p));
 }
 
+// The same 256-bit load without allocating the line in L1 (NA), for rows of
+// the ray-mask tables: random 32- or 64-byte rows of a 1.49 MB (96 MB at
+// R_ray = 2R) table that few other lanes read again, which would otherwise
+// evict node records that neighbouring rays fetch next.
+template <bool NA>
+__device__ __forceinline__ void ldg8u_row(const void* p, uint4& a, uint4& b) {
+  if constexpr (NA) {
+    asm("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(p));
+  } else {
+    ldg8u(p, a, b);
+  }
+}
+
 template <int R>
 struct MaskTraits {
   static constexpr int kStrideBytes = (R == 4) ? 8 : (R == 6 ? 32 : 64);
@@ -105,12 +120,21 @@ enum : int {
                   // origin cell before its wave is traced
   OPT_LAZY = 64,  // the per-child scales are loaded only when a child needs a test
   OPT_SSTACK = 128, // the top kRing stack entries in shared memory (blocks of kBlock)
+  OPT_TL1 = 256,  // full-table rows and uncompressed object masks allocated in L1
+                  // like other loads (by default they bypass L1 allocation)
   OPT_DEFER = 32, // compressed, bit table: a child's culling lookup is issued
                   // when the child is visited, beside its own fetch (the
                   // cells still come from the parent's slab test)
 };
 
 constexpr uint32_t kNoTest = 0xFFFFFFFFu;
+
+// Rows of the full ray-mask table (R = 6, 8) and of the R_ray = 2R table,
+// and the uncompressed object masks of the node records, skip L1
+// allocation unless OPT_TL1 is set: both are fetched only for a tested
+// child, while the records' boxes are what neighbouring rays fetch next.
+template <int OPT>
+constexpr bool kRowNA = (OPT & OPT_TL1) == 0;
 
 // floor(q) clamped to [0, R-1]: the saturating float-to-unsigned conversion
 // (cvt.rmi, negatives and NaN to 0) and a min.
@@ -218,8 +242,10 @@ __device__ __forceinline__ float scale_of(float lo, float hi) {
   return __fdiv_rn((float)R, fmaxf(__fsub_rn(hi, lo), 1e-30f));
 }
 
-// AND of two masks in global memory (aligned, zero padded) != 0.
-template <int R>
+// AND of two masks in global memory (aligned, zero padded) != 0.  ROW_NA /
+// OBJ_NA: the first (a ray-mask table row) / second (an object mask) is
+// loaded without L1 allocation.
+template <int R, bool ROW_NA = false, bool OBJ_NA = false>
 __device__ __forceinline__ bool masks_overlap(const void* a, const void* b) {
   if constexpr (R == 4) {
     const uint2 x = __ldg(reinterpret_cast<const uint2*>(a));
@@ -231,8 +257,8 @@ __device__ __forceinline__ bool masks_overlap(const void* a, const void* b) {
 #pragma unroll
     for (int q = 0; q < MaskTraits<R>::kQuads; q += 2) {
       uint4 x0, x1, y0, y1;
-      ldg8u(reinterpret_cast<const uint4*>(a) + q, x0, x1);
-      ldg8u(reinterpret_cast<const uint4*>(b) + q, y0, y1);
+      ldg8u_row<ROW_NA>(reinterpret_cast<const uint4*>(a) + q, x0, x1);
+      ldg8u_row<OBJ_NA>(reinterpret_cast<const uint4*>(b) + q, y0, y1);
       acc |= (x0.x & y0.x) | (x0.y & y0.y) | (x0.z & y0.z) | (x0.w & y0.w) | (x1.x & y1.x) |
              (x1.y & y1.y) | (x1.z & y1.z) | (x1.w & y1.w);
     }
@@ -300,6 +326,31 @@ struct SharedTables<4, 3> {
   SmemFull4 full;
 };
 
+// The two 2^R-entry expansion tables of SmemLut as read-only device data
+// (for the factored test read through L1, lookup variant 5).
+template <int R>
+struct ExpandTables {
+  unsigned long long rows[1 << R];
+  unsigned long long cols[1 << R];
+};
+
+template <int R>
+constexpr ExpandTables<R> make_expand() {
+  ExpandTables<R> e{};
+  for (int m = 0; m < (1 << R); ++m) {
+    unsigned long long r = 0, c = 0;
+    for (int k = 0; k < R; ++k) {
+      if ((m >> k) & 1) r |= ((1ULL << R) - 1ULL) << (R * k);
+      c |= (unsigned long long)m << (R * k);
+    }
+    e.rows[m] = r;
+    e.cols[m] = c;
+  }
+  return e;
+}
+
+__device__ const ExpandTables<6> kExpand6 = make_expand<6>();
+
 // R^2-bit slice z of a dense R^3-bit mask held in W (+1 zero) words.
 template <int R>
 __device__ __forceinline__ unsigned long long mask_slice(const uint32_t* w, int z) {
@@ -321,9 +372,15 @@ __device__ __forceinline__ unsigned long long mask_slice(const uint32_t* w, int 
   }
 }
 
-template <int R>
-__device__ __forceinline__ bool overlap_factored(const SmemLut<R>& s, const int* cb,
-                                                 const int* ce, const uint8_t* objp) {
+// The factored test (Helly: the ray mask of slice z is the (x,y) table's
+// R^2 bits restricted to the rows of the (y,z) table's set for z and the
+// columns of the (x,z) table's set for z), slice by slice over the z range
+// of the segment.  FROM_L1: the pair table and the expansion tables are
+// read from global memory through L1 instead of from shared memory.
+template <int R, bool FROM_L1 = false>
+__device__ __forceinline__ bool overlap_factored(const SmemLut<R>* s, const uint2* gpair,
+                                                 const int* cb, const int* ce,
+                                                 const uint8_t* objp) {
   constexpr int W = MaskTraits<R>::kWords;
   uint32_t w[W + 1];
   if constexpr (R == 4) {
@@ -342,15 +399,30 @@ __device__ __forceinline__ bool overlap_factored(const SmemLut<R>& s, const int*
   }
   w[W] = 0u;
   auto pidx = [](int ba, int bb, int ea, int eb) { return ((ba * R + bb) * R + ea) * R + eb; };
-  const unsigned long long pxy = s.P[pidx(cb[0], cb[1], ce[0], ce[1])];
-  const unsigned long long pyz = s.P[pidx(cb[1], cb[2], ce[1], ce[2])];
-  const unsigned long long pxz = s.P[pidx(cb[0], cb[2], ce[0], ce[2])];
+  auto pget = [&](int i) -> unsigned long long {
+    if constexpr (FROM_L1) {
+      const uint2 v = __ldg(gpair + i);
+      return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+    } else {
+      return s->P[i];
+    }
+  };
+  const unsigned long long pxy = pget(pidx(cb[0], cb[1], ce[0], ce[1]));
+  const unsigned long long pyz = pget(pidx(cb[1], cb[2], ce[1], ce[2]));
+  const unsigned long long pxz = pget(pidx(cb[0], cb[2], ce[0], ce[2]));
   const int z0 = min(cb[2], ce[2]), z1 = max(cb[2], ce[2]);
   constexpr unsigned long long m = (1ULL << R) - 1ULL;
   for (int z = z0; z <= z1; ++z) {
-    const unsigned long long ray =
-        pxy & s.rows[(pyz >> (R * z)) & m] & s.cols[(pxz >> (R * z)) & m];
-    if (ray & mask_slice<R>(w, z)) return true;
+    unsigned long long rsel, csel;
+    if constexpr (FROM_L1) {
+      static_assert(R == 6, "the L1 expansion tables are built for R = 6");
+      rsel = __ldg(&kExpand6.rows[(pyz >> (R * z)) & m]);
+      csel = __ldg(&kExpand6.cols[(pxz >> (R * z)) & m]);
+    } else {
+      rsel = s->rows[(pyz >> (R * z)) & m];
+      csel = s->cols[(pxz >> (R * z)) & m];
+    }
+    if (pxy & rsel & csel & mask_slice<R>(w, z)) return true;
   }
   return false;
 }
@@ -475,7 +547,7 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
     const int end2 = ce[0] + R2 * ce[1] + R2 * R2 * ce[2];
     const uint8_t* rm =
         reinterpret_cast<const uint8_t*>(p.lut2) + ((size_t)beg2 * (R2 * R2 * R2) + end2) * MB;
-    return masks_overlap<R>(rm, obj);
+    return masks_overlap<R, kRowNA<OPT>, kRowNA<OPT>>(rm, obj);
   }
   {
     float q0[3], q1[3];
@@ -504,10 +576,12 @@ __device__ __forceinline__ bool cull_test(const Params& p, const SharedTables<R,
   } else {
     if constexpr (CULL == 2) obj = reinterpret_cast<const uint8_t*>(p.clut) + (meta & 0xFFu) * MB;
     if constexpr (LUTV == 1) {
-      return overlap_factored<R>(sh.f, cb, ce, obj);
+      return overlap_factored<R>(&sh.f, p.pair, cb, ce, obj);
+    } else if constexpr (LUTV == 5) {
+      return overlap_factored<R, true>(nullptr, p.pair, cb, ce, obj);
     } else {
       const uint8_t* rm = reinterpret_cast<const uint8_t*>(p.lut) + (size_t)(beg * R3 + end) * MB;
-      return masks_overlap<R>(rm, obj);
+      return masks_overlap<R, kRowNA<OPT>, CULL == 1 && kRowNA<OPT>>(rm, obj);
     }
   }
 }

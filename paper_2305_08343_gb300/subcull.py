@@ -25,6 +25,7 @@ SC_LAYOUT_PLAIN4, SC_LAYOUT_MASKED4 = 3, 4
 SC_LAYOUT_MASKED_RAY2R = 5
 SC_CLOSEST, SC_ANY = 0, 1
 SC_LUT_AUTO, SC_LUT_GLOBAL, SC_LUT_SHARED, SC_LUT_BITTABLE, SC_LUT_RAY2R = 0, 1, 2, 3, 4
+SC_LUT_FACTORED_L1 = 5
 STATUS_NAMES = {0: "SC_OK", -1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_NOMEM",
                 -4: "SC_ERR_TIMEOUT", -5: "SC_ERR_STACK", -6: "SC_ERR_UNSUPPORTED",
                 -7: "SC_ERR_STATE", -8: "SC_ERR_IO"}
@@ -81,6 +82,7 @@ SC_VARIANT_SORT = 16
 SC_VARIANT_DEFER = 32
 SC_VARIANT_LAZY = 64
 SC_VARIANT_SSTACK = 128
+SC_VARIANT_TABLE_L1 = 256
 
 
 class sc_tune_result(C.Structure):

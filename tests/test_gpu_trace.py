@@ -100,6 +100,26 @@ def test_resolutions_lut_modes_layouts(hair_small, R, comp, lut, layout):
     assert_parity(g, o, f"R={R} comp={comp} lut={lut} layout={layout}")
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_factored_tables_through_l1(hair_small, mode):
+    """SC_LUT_FACTORED_L1: the Helly-factored 2-D tables read from the image
+    through L1 give the oracle's hits and per-ray counts."""
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, 6, 0)
+    g = gpu_trace(b, rays, mode, 1, lut_mode=sc.SC_LUT_FACTORED_L1)
+    o = oracle_trace(tris, rays, 6, 0, mode, 1)
+    assert_parity(g, o, f"factored L1 mode={mode}")
+
+
+@pytest.mark.parametrize("R,comp,layout", [(4, 0, None), (6, 1, None),
+                                           (6, 0, sc.SC_LAYOUT_MASKED_COMPACT)])
+def test_factored_tables_through_l1_rejects_other_images(hair_small, R, comp, layout):
+    tris, rays = hair_small
+    b = sc.sc_bvh_build(tris, R, comp)
+    with pytest.raises(sc.SubcullError, match="L1-read factored"):
+        gpu_trace(b, rays, 0, 1, lut_mode=sc.SC_LUT_FACTORED_L1, layout=layout)
+
+
 @pytest.mark.parametrize("skip", [150, 100, 40])
 @pytest.mark.parametrize("comp", [0, 1])
 def test_dense_mask_skip_threshold(hair_small, skip, comp):

@@ -82,6 +82,23 @@ def test_waves_r4_lookup_variants(comp, lut):
         assert np.array_equal(g[w]["counts"], o[w]["counts"][order])
 
 
+@pytest.mark.parametrize("lut", [sc.SC_LUT_SHARED, sc.SC_LUT_FACTORED_L1])
+@pytest.mark.parametrize("cfg", [dict(), dict(block=64, stack=32), dict(block=256, stack=64)])
+def test_waves_r6_factored_tables(lut, cfg):
+    """R = 6, uncompressed masks, stored scales: the Helly-factored ray-mask
+    tables in shared memory or read through L1, in several block / stack
+    shapes of the wave pipeline, against the oracle."""
+    tris = sg.hair(400, 16, True, seed=36)
+    rays = sg.pinhole(64, 48)
+    g = _gpu_waves(tris, rays, 2, 91, 6, 0, 1, sc.SC_LAYOUT_MASKED, lut, **cfg)
+    o = _oracle_waves(tris, rays, 2, 91, 6, 0, 1)
+    for w in range(3):
+        order = np.argsort(o[w]["path"], kind="stable")
+        assert np.array_equal(g[w]["path"], np.sort(o[w]["path"])), f"wave {w} {cfg}"
+        assert np.array_equal(g[w]["id"], o[w]["id"][order])
+        assert np.array_equal(g[w]["counts"], o[w]["counts"][order])
+
+
 @pytest.mark.parametrize("cfg", [dict(wave_chunk=1000), dict(wave_chunk=777, block=64, stack=32),
                                  dict(block=256, stack=32, refill=16), dict(block=64, refill=1)])
 @pytest.mark.parametrize("cull,comp", [(1, 1), (1, 0), (0, 0)])
