@@ -60,21 +60,29 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair12m_unc": 
 # DRAM traffic per launch of the timed kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture, summarised in profiles/), valid
 # only while the kernel source is the one that was measured: keyed by the
-# SHA-256 of the traversal kernel header.
+# workload and the kernel option set the autotuner chose (0, or the
+# shared-memory stack ring), and checked against the SHA-256 of the
+# traversal kernel header.
 MEASURED_TRAFFIC = {
-    # workload: (bytes per launch, kernel source sha256, profile summary)
-    "hair12m": (1.986597e9 + 0.398794e9,
-                "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
-                "profiles/waves_kernel_hair12m.md"),
-    "hair1m": (1.720535e9 + 0.259359e9,
-               "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
-               "profiles/waves_kernel_hair1m.md"),
+    # (workload, variant): (bytes per launch, kernel source sha256, profile summary)
+    ("hair12m", 0): (1.986597e9 + 0.398794e9,
+                     "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
+                     "profiles/waves_kernel_hair12m.md"),
+    ("hair1m", 0): (1.720535e9 + 0.259359e9,
+                    "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
+                    "profiles/waves_kernel_hair1m.md"),
+    ("hair12m", 128): (1.544110e9 + 0.298593e9,
+                       "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
+                       "profiles/waves_kernel_hair12m.md"),
+    ("hair1m", 128): (1.329470e9 + 0.210057e9,
+                      "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
+                      "profiles/waves_kernel_hair1m.md"),
 }
 
 
-def measured_traffic(workload: str):
+def measured_traffic(workload: str, variant: int = 0):
     import hashlib
-    entry = MEASURED_TRAFFIC.get(workload)
+    entry = MEASURED_TRAFFIC.get((workload, variant))
     if entry is None:
         return None, None
     src = os.path.join(ROOT, "paper_2305_08343_gb300", "csrc", "cuda", "trace_kernel.cuh")
@@ -596,7 +604,7 @@ def run_gpu(args):
         opts_p, rows_p = sc.sc_autotune_waves(d_plain, rays, bounces, seed, 0, bufs_p, opts_plain, 3,
                                               flush)
         pick = lambda o: {"block": o.block, "stack": o.stack, "refill": o.refill,
-                          "wave_chunk": int(o.wave_chunk)}
+                          "wave_chunk": int(o.wave_chunk), "variant": o.variant}
         tuned = {"culled": pick(opts_c), "plain": pick(opts_p), "candidates": len(rows_c),
                  "seconds": time.perf_counter() - t0}
 
@@ -745,7 +753,7 @@ def run_gpu(args):
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peaks = load_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic, traffic_src = measured_traffic(args.workload)
+    traffic, traffic_src = measured_traffic(args.workload, opts_c.variant)
     if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
             or args.leaf_min or args.L != 3 or args.max_leaf != 4 or wide
             or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
@@ -812,7 +820,7 @@ def run_gpu(args):
                "tests_per_ray": {"node": cnt_a[0], "tri": cnt_a[1],
                                  "node_plus_tri": cnt_a[0] + cnt_a[1]},
                "autotuned": {"block": opts_a.block, "stack": opts_a.stack,
-                             "refill": opts_a.refill},
+                             "refill": opts_a.refill, "variant": opts_a.variant},
                "build_ms": {"bvh": bvh_a.info().ms_bvh, "masks": bvh_a.info().ms_masks,
                             "compress": bvh_a.info().ms_compress}}
         del d_a, bvh_a, bufs_a, wa

@@ -469,11 +469,15 @@ sc_status sc_trace_waves_host(const sc_dbvh* d, const float* h_rays, int64_t n0,
    from `base`), and the tried configurations into results (host array of
    `cap` entries, may be NULL) with their count in *n_results.  Block sizes
    other than 128 and stack 32 exist for R = 6 and plain traversal only.
+   When base->variant is 0 and the image has kernel variants, the candidates
+   also hold block 128 / stack 64 with SC_VARIANT_SSTACK (the top stack
+   entries in shared memory); *best->variant then says which was chosen.
    d_ws must be sized for the largest chunk (wave_chunk = 0).  Synchronous. */
 typedef struct {
   int block, stack, refill;
   int64_t wave_chunk;
   float ms;
+  int variant;  /* SC_VARIANT_SSTACK for the shared-memory stack ring, else 0 */
 } sc_tune_result;
 
 sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0,

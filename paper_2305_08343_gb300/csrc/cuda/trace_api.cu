@@ -123,18 +123,20 @@ sct::KernelFn pick_kernel(const sc_dbvh* d, int mode, int cull, int lutv) {
 // Kernels with non-default options (sc_trace_opts.variant): R = 6 images
 // with the full table (uncompressed) or the bit table (compressed), scales
 // stored, and the plain traversal.
+bool variant_image_ok(const sc_dbvh* d, int cull, int lutv) {
+  if (d->lay.width != 2) return false;
+  return !cull || (d->lay.R == 6 && d->lay.scales &&
+                   ((!d->lay.compress && lutv == 0) || (d->lay.compress && lutv == 2)));
+}
+
 void check_variant(const sc_dbvh* d, int cull, int lutv, int variant) {
   if (!sct::var_supported(variant))
     fail(SC_ERR_UNSUPPORTED, "kernel variant %d is not built", variant);
   if (d->lay.width != 2) fail(SC_ERR_UNSUPPORTED, "kernel variants need a binary image");
-  if (cull) {
-    const bool ok = d->lay.R == 6 && d->lay.scales &&
-                    ((!d->lay.compress && lutv == 0) || (d->lay.compress && lutv == 2));
-    if (!ok)
-      fail(SC_ERR_UNSUPPORTED,
-           "kernel variants are built for R = 6 images with stored scales (full table "
-           "uncompressed, bit table compressed)");
-  }
+  if (!variant_image_ok(d, cull, lutv))
+    fail(SC_ERR_UNSUPPORTED,
+         "kernel variants are built for R = 6 images with stored scales (full table "
+         "uncompressed, bit table compressed)");
 }
 
 sct::KernelFn pick_kernel_var(const sc_dbvh* d, int mode, int cull, int lutv, int variant) {
@@ -737,6 +739,22 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
           t.wave_chunk = ch;
           cands.push_back(t);
         }
+  // the stack's top entries in a shared-memory ring: built at block 128 /
+  // stack 64 for the images that have kernel variants
+  int lutv = lut_variant(d, o.lut_mode);
+  if (lutv == 1) lutv = 0;
+  if (o.variant == 0 && variant_image_ok(d, cull, lutv) && d->stack_need <= 64 &&
+      sct::var_supported(sct::OPT_SSTACK))
+    for (int rf : refills)
+      for (int64_t ch : chunks) {
+        sc_trace_opts t = o;
+        t.block = kBlock;
+        t.stack = sct::kStack;
+        t.refill = rf;
+        t.wave_chunk = ch;
+        t.variant = sct::OPT_SSTACK;
+        cands.push_back(t);
+      }
   cudaEvent_t e0, e1;
   CUDA_OK(cudaEventCreate(&e0));
   CUDA_OK(cudaEventCreate(&e1));
@@ -786,7 +804,7 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
     const float med = median(ms[i]);
     if (results && (int)i < cap)
       results[i] = sc_tune_result{cands[i].block, cands[i].stack, cands[i].refill,
-                                  cands[i].wave_chunk, med};
+                                  cands[i].wave_chunk, med, cands[i].variant};
     if (med < best_ms) {
       best_ms = med;
       *best = cands[i];

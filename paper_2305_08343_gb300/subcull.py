@@ -87,7 +87,7 @@ SC_VARIANT_TABLE_L1 = 256
 
 class sc_tune_result(C.Structure):
     _fields_ = [("block", C.c_int), ("stack", C.c_int), ("refill", C.c_int),
-                ("wave_chunk", C.c_int64), ("ms", C.c_float)]
+                ("wave_chunk", C.c_int64), ("ms", C.c_float), ("variant", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -545,7 +545,9 @@ def trace_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, buffe
 def sc_autotune_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int, buffers,
                       base: sc_trace_opts | None = None, reps: int = 3, flush=None, stream=None):
     """Times the wave pipeline over block / stack / refill / wave-chunk
-    candidates; returns (best opts, list of (block, stack, refill, chunk, ms))."""
+    candidates (and the shared-memory stack ring where the image has kernel
+    variants); returns (best opts, list of (block, stack, refill, chunk,
+    variant, ms))."""
     n0 = rays.shape[0]
     arr = _wave_arr(buffers.outs(), bounces)
     best = sc_trace_opts()
@@ -559,7 +561,8 @@ def sc_autotune_waves(dbvh: DeviceBVH, rays, bounces: int, seed: int, cull: int,
                                    C.c_void_p(flush.data_ptr()) if flush is not None else None,
                                    flush.numel() if flush is not None else 0,
                                    C.byref(best), res, cap, C.byref(nres), _stream_ptr(stream)))
-    rows = [(r.block, r.stack, r.refill, r.wave_chunk, r.ms) for r in res[: min(nres.value, cap)]]
+    rows = [(r.block, r.stack, r.refill, r.wave_chunk, r.variant, r.ms)
+            for r in res[: min(nres.value, cap)]]
     return best, rows
 
 

@@ -133,6 +133,32 @@ def test_autotuner_returns_a_valid_config():
     assert torch.equal(b1.hits[0].view(torch.int32), b2.hits[0].view(torch.int32))
 
 
+@pytest.mark.parametrize("comp,cull", [(1, 1), (0, 1), (0, 0)])
+def test_autotuner_considers_the_stack_ring(comp, cull):
+    """On images with kernel variants the tuner also times the shared-memory
+    stack ring (block 128, stack 64); whatever it picks traces the same."""
+    tris = sg.hair(300, 16, True, seed=37)
+    rays = sg.pinhole(128, 128)
+    b = sc.sc_bvh_build(tris, 6, comp)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED if cull else sc.SC_LAYOUT_PLAIN)
+    r = torch.from_numpy(rays).cuda()
+    bufs = sc.WaveBuffers(r.shape[0], 2, with_counts=False)
+    best, rows = sc.sc_autotune_waves(d, r, 2, 9, cull, bufs, reps=1)
+    ring = [x for x in rows if x[4] == sc.SC_VARIANT_SSTACK]
+    assert ring and all(x[0] == 128 and x[1] == 64 for x in ring)
+    assert best.variant in (0, sc.SC_VARIANT_SSTACK)
+    ring_opts = sc._opts(block=128, stack=64, variant=sc.SC_VARIANT_SSTACK)
+    for o in (best, ring_opts):
+        b1, s1 = sc.trace_waves(d, r, 2, 9, cull, opts=o)
+        b2, s2 = sc.trace_waves(d, r, 2, 9, cull)
+        assert list(s1) == list(s2)
+        for w in range(3):
+            m = int(s1[w])
+            ia, ib = torch.argsort(b1.path[w][:m]), torch.argsort(b2.path[w][:m])
+            assert torch.equal(b1.hits[w][:m].view(torch.int32)[ia],
+                               b2.hits[w][:m].view(torch.int32)[ib])
+
+
 def test_waves_culled_equals_plain_and_sizes():
     tris = sg.hair(800, 16, True, seed=32)
     rays = sg.pinhole(96, 64)
