@@ -60,23 +60,21 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair12m_unc": 
 # DRAM traffic per launch of the timed kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture, summarised in profiles/), valid
 # only while the kernel source is the one that was measured: keyed by the
-# workload and the kernel option set the autotuner chose (0, or the
-# shared-memory stack ring), and checked against the SHA-256 of the
-# traversal kernel header.
+# workload and the kernel option set the autotuner chose (0, the
+# shared-memory stack ring 128, 9 blocks per SM 1024, or both 1152), and
+# checked against the SHA-256 of the traversal kernel header.
+_TRAFFIC_SRC = "22ddcb918572195aa2d0f89e8a0e91ab1354b1d086cc720a6ab0d3440e7f9186"
+_P12, _P1 = "profiles/waves_kernel_hair12m.md", "profiles/waves_kernel_hair1m.md"
 MEASURED_TRAFFIC = {
     # (workload, variant): (bytes per launch, kernel source sha256, profile summary)
-    ("hair12m", 0): (1.986597e9 + 0.398794e9,
-                     "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
-                     "profiles/waves_kernel_hair12m.md"),
-    ("hair1m", 0): (1.720535e9 + 0.259359e9,
-                    "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
-                    "profiles/waves_kernel_hair1m.md"),
-    ("hair12m", 128): (1.544110e9 + 0.298593e9,
-                       "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
-                       "profiles/waves_kernel_hair12m.md"),
-    ("hair1m", 128): (1.329470e9 + 0.210057e9,
-                      "6cfa4485891444723c2168c6eab675915cd528b957bf33017e5e62e4a9eac5c0",
-                      "profiles/waves_kernel_hair1m.md"),
+    ("hair12m", 0): (1.985320e+09 + 3.990750e+08, _TRAFFIC_SRC, _P12),
+    ("hair12m", 128): (1.546924e+09 + 2.983990e+08, _TRAFFIC_SRC, _P12),
+    ("hair12m", 1024): (2.692479e+09 + 5.732360e+08, _TRAFFIC_SRC, _P12),
+    ("hair12m", 1152): (1.956720e+09 + 3.609250e+08, _TRAFFIC_SRC, _P12),
+    ("hair1m", 0): (1.720134e+09 + 2.593690e+08, _TRAFFIC_SRC, _P1),
+    ("hair1m", 128): (1.329806e+09 + 2.098700e+08, _TRAFFIC_SRC, _P1),
+    ("hair1m", 1024): (2.174589e+09 + 3.720220e+08, _TRAFFIC_SRC, _P1),
+    ("hair1m", 1152): (1.610462e+09 + 2.512270e+08, _TRAFFIC_SRC, _P1),
 }
 
 

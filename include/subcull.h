@@ -337,6 +337,13 @@ enum {
                                   L1 like other loads; by default they are
                                   loaded without L1 allocation, so that
                                   they do not evict node records            */
+  SC_VARIANT_OCC9 = 1024,      /* waves: 9 resident blocks of 128 threads per
+                                  SM (56 registers a thread) instead of 8
+                                  (64 registers); combinable with
+                                  SC_VARIANT_SSTACK                         */
+  SC_VARIANT_OCC10 = 2048,     /* waves: 10 resident blocks per SM (48
+                                  registers); combinable with
+                                  SC_VARIANT_SSTACK                         */
   SC_VARIANT_DEFER = 32        /* compressed masks with the bit table: each
                                   child's bit-table lookup is issued when the
                                   child is visited, beside its own fetch
@@ -470,8 +477,10 @@ sc_status sc_trace_waves_host(const sc_dbvh* d, const float* h_rays, int64_t n0,
    `cap` entries, may be NULL) with their count in *n_results.  Block sizes
    other than 128 and stack 32 exist for R = 6 and plain traversal only.
    When base->variant is 0 and the image has kernel variants, the candidates
-   also hold block 128 / stack 64 with SC_VARIANT_SSTACK (the top stack
-   entries in shared memory); *best->variant then says which was chosen.
+   also hold block 128 / stack 64 (refill 4 and 8) with SC_VARIANT_SSTACK
+   (the top stack entries in shared memory), SC_VARIANT_OCC9 and
+   SC_VARIANT_OCC10 (more resident blocks, fewer registers) and their
+   combinations; *best->variant then says which was chosen.
    d_ws must be sized for the largest chunk (wave_chunk = 0).  Synchronous. */
 typedef struct {
   int block, stack, refill;

@@ -739,22 +739,27 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
           t.wave_chunk = ch;
           cands.push_back(t);
         }
-  // the stack's top entries in a shared-memory ring: built at block 128 /
+  // the stack's top entries in a shared-memory ring, and 9 or 10 resident
+  // blocks per SM (56 or 48 registers a thread): built at block 128 /
   // stack 64 for the images that have kernel variants
   int lutv = lut_variant(d, o.lut_mode);
   if (lutv == 1) lutv = 0;
-  if (o.variant == 0 && variant_image_ok(d, cull, lutv) && d->stack_need <= 64 &&
-      sct::var_supported(sct::OPT_SSTACK))
-    for (int rf : refills)
-      for (int64_t ch : chunks) {
-        sc_trace_opts t = o;
-        t.block = kBlock;
-        t.stack = sct::kStack;
-        t.refill = rf;
-        t.wave_chunk = ch;
-        t.variant = sct::OPT_SSTACK;
-        cands.push_back(t);
-      }
+  const int placements[5] = {sct::OPT_SSTACK, sct::OPT_OCC9, sct::OPT_OCC9 | sct::OPT_SSTACK,
+                             sct::OPT_OCC10, sct::OPT_OCC10 | sct::OPT_SSTACK};
+  if (o.variant == 0 && variant_image_ok(d, cull, lutv) && d->stack_need <= 64)
+    for (int v : placements) {
+      if (!sct::var_supported(v)) continue;
+      for (int rf : {4, 8})
+        for (int64_t ch : chunks) {
+          sc_trace_opts t = o;
+          t.block = kBlock;
+          t.stack = sct::kStack;
+          t.refill = rf;
+          t.wave_chunk = ch;
+          t.variant = v;
+          cands.push_back(t);
+        }
+    }
   cudaEvent_t e0, e1;
   CUDA_OK(cudaEventCreate(&e0));
   CUDA_OK(cudaEventCreate(&e1));

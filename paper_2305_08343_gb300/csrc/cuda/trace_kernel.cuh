@@ -122,6 +122,9 @@ enum : int {
   OPT_SSTACK = 128, // the top kRing stack entries in shared memory (blocks of kBlock)
   OPT_TL1 = 256,  // full-table rows and uncompressed object masks allocated in L1
                   // like other loads (by default they bypass L1 allocation)
+  OPT_OCC9 = 1024,  // waves: 9 resident blocks of 128 threads per SM (56 registers)
+                    // instead of 8 (64 registers)
+  OPT_OCC10 = 2048, // waves: 10 resident blocks of 128 threads per SM (48 registers)
   OPT_DEFER = 32, // compressed, bit table: a child's culling lookup is issued
                   // when the child is visited, beside its own fetch (the
                   // cells still come from the parent's slab test)
@@ -1457,10 +1460,17 @@ static __device__ __noinline__ bool make_bounce(float ox, float oy, float oz, fl
 // bounce ray to the queue of wave w + 1 (warp-aggregated atomicAdd, so a
 // queue holds only spawned rays: compacted).  A bounded grid barrier
 // separates the waves.  Outputs: wave 0 by primary index; wave w >= 1 after
-// the entries of the previous chunks.
+// the entries of the previous chunks.  The blocks resident per SM (the
+// register bound) are kWaveMinBlocks of kBlock threads unless OPT_OCC9 /
+// OPT_OCC10 raise them.
+template <int OPT>
+constexpr int kWaveBlocksPerSM =
+    kWaveMinBlocks + ((OPT & OPT_OCC10) ? 2 : ((OPT & OPT_OCC9) ? 1 : 0));
+
 template <int R, int CULL, int LUTV, int SCALES, int BLOCK = kBlock, int STACK = kStack,
           int WIDTH = 2, int OPT = 0>
-__global__ void __launch_bounds__(BLOCK, kWaveMinBlocks * kBlock / BLOCK) waves_kernel(WaveParams wp) {
+__global__ void __launch_bounds__(BLOCK, kWaveBlocksPerSM<OPT> * kBlock / BLOCK)
+    waves_kernel(WaveParams wp) {
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
   const Params& p = wp.p;

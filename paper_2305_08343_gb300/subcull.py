@@ -83,6 +83,8 @@ SC_VARIANT_DEFER = 32
 SC_VARIANT_LAZY = 64
 SC_VARIANT_SSTACK = 128
 SC_VARIANT_TABLE_L1 = 256
+SC_VARIANT_OCC9 = 1024
+SC_VARIANT_OCC10 = 2048
 
 
 class sc_tune_result(C.Structure):

@@ -136,7 +136,8 @@ def test_autotuner_returns_a_valid_config():
 @pytest.mark.parametrize("comp,cull", [(1, 1), (0, 1), (0, 0)])
 def test_autotuner_considers_the_stack_ring(comp, cull):
     """On images with kernel variants the tuner also times the shared-memory
-    stack ring (block 128, stack 64); whatever it picks traces the same."""
+    stack ring and the 9- and 10-block occupancy bounds (block 128, stack
+    64); whatever it picks traces the same."""
     tris = sg.hair(300, 16, True, seed=37)
     rays = sg.pinhole(128, 128)
     b = sc.sc_bvh_build(tris, 6, comp)
@@ -144,11 +145,13 @@ def test_autotuner_considers_the_stack_ring(comp, cull):
     r = torch.from_numpy(rays).cuda()
     bufs = sc.WaveBuffers(r.shape[0], 2, with_counts=False)
     best, rows = sc.sc_autotune_waves(d, r, 2, 9, cull, bufs, reps=1)
-    ring = [x for x in rows if x[4] == sc.SC_VARIANT_SSTACK]
-    assert ring and all(x[0] == 128 and x[1] == 64 for x in ring)
-    assert best.variant in (0, sc.SC_VARIANT_SSTACK)
-    ring_opts = sc._opts(block=128, stack=64, variant=sc.SC_VARIANT_SSTACK)
-    for o in (best, ring_opts):
+    placed = {sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_OCC9, sc.SC_VARIANT_OCC10,
+              sc.SC_VARIANT_OCC9 | sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_OCC10 | sc.SC_VARIANT_SSTACK}
+    ring = [x for x in rows if x[4] != 0]
+    assert {x[4] for x in ring} == placed and all(x[0] == 128 and x[1] == 64 for x in ring)
+    assert best.variant in placed | {0}
+    others = [sc._opts(block=128, stack=64, variant=v) for v in sorted(placed)]
+    for o in [best] + others:
         b1, s1 = sc.trace_waves(d, r, 2, 9, cull, opts=o)
         b2, s2 = sc.trace_waves(d, r, 2, 9, cull)
         assert list(s1) == list(s2)
