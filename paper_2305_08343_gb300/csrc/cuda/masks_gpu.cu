@@ -20,8 +20,18 @@ namespace {
 // collecting bits in its own copy of the mask, OR-reduced at the end.  The
 // per-voxel and per-cell arithmetic is mask_math.h's, so the bits are those
 // of the host build.
+// Per-warp tables of the FP32 SAT filter: the half extents of the slot's
+// voxels per axis and index (set once per slot), and each vertex coordinate
+// of the current triangle relative to every voxel centre on its axis (set
+// once per triangle), so that a triangle/voxel pair needs no FP64 work
+// unless the filter leaves it undecided.
+struct SatTables {
+  mm::Ef h[3][8];
+  mm::Ef a[3][3][8];  // [vertex][axis][voxel index]
+};
+
 __device__ void voxelize_warp(const float* t9, const mm::Grid& g, uint32_t* acc, int W,
-                              int lane) {
+                              int lane, SatTables& tab) {
   double v[9];
   for (int i = 0; i < 9; ++i) v[i] = (double)t9[i];
   int r0[3], r1[3];
@@ -31,15 +41,29 @@ __device__ void voxelize_warp(const float* t9, const mm::Grid& g, uint32_t* acc,
     g.candidates(k, tlo, thi, r0[k], r1[k]);
   }
   const int R = g.R, nx = r1[0] - r0[0] + 1, ny = r1[1] - r0[1] + 1, nz = r1[2] - r0[2] + 1;
+  __syncwarp();  // the previous triangle's table has been read
+  for (int idx = lane; idx < 9 * R; idx += 32) {
+    const int i = idx / (3 * R), k = (idx / R) % 3, j = idx % R;
+    tab.a[i][k][j] = mm::ef_rel(v[3 * i + k], g.b0[k][j], g.b1[k][j]);
+  }
+  __syncwarp();
   // voxels an earlier triangle set need no test (the bits are an OR)
   uint32_t have[16];
   for (int w = 0; w < W; ++w) have[w] = __reduce_or_sync(0xffffffffu, acc[w]);
   for (int i = lane; i < nx * ny * nz; i += 32) {
     const int x = r0[0] + i % nx, y = r0[1] + (i / nx) % ny, z = r0[2] + i / (nx * ny);
     if (mm::get_bit(have, x + R * y + R * R * z)) continue;
-    const double bmin[3] = {g.b0[0][x], g.b0[1][y], g.b0[2][z]};
-    const double bmax[3] = {g.b1[0][x], g.b1[1][y], g.b1[2][z]};
-    if (mm::tri_box_overlap(v, bmin, bmax)) mm::set_bit(acc, x + R * y + R * R * z);
+    const mm::Ef a[3][3] = {{tab.a[0][0][x], tab.a[0][1][y], tab.a[0][2][z]},
+                            {tab.a[1][0][x], tab.a[1][1][y], tab.a[1][2][z]},
+                            {tab.a[2][0][x], tab.a[2][1][y], tab.a[2][2][z]}};
+    const mm::Ef h[3] = {tab.h[0][x], tab.h[1][y], tab.h[2][z]};
+    int hit = mm::tri_box_overlap_ef(a, h);
+    if (hit < 0) {
+      const double bmin[3] = {g.b0[0][x], g.b0[1][y], g.b0[2][z]};
+      const double bmax[3] = {g.b1[0][x], g.b1[1][y], g.b1[2][z]};
+      hit = mm::tri_box_overlap(v, bmin, bmax) ? 1 : 0;
+    }
+    if (hit) mm::set_bit(acc, x + R * y + R * R * z);
   }
 }
 
@@ -71,9 +95,9 @@ __device__ void fill_warp(uint32_t* acc, const float* pbox, const uint32_t* cmas
 }
 
 __device__ void leaf_warp(const mm::MaskInputs& b, int32_t first, int32_t count,
-                          const mm::Grid& g, uint32_t* acc, int lane) {
+                          const mm::Grid& g, uint32_t* acc, int lane, SatTables& tab) {
   for (int32_t i = 0; i < count; ++i)
-    voxelize_warp(&b.tris[9 * (size_t)b.perm[first + i]], g, acc, b.W, lane);
+    voxelize_warp(&b.tris[9 * (size_t)b.perm[first + i]], g, acc, b.W, lane, tab);
 }
 
 __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64_t nslots) {
@@ -85,11 +109,18 @@ __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64
   const float* gbox = &in.box[12 * n + 6 * c];
   mm::Grid g;
   g.init(gbox, in.R, in.eps);
+  __shared__ SatTables tables[4];  // one per warp of a 128-thread block
+  SatTables& tab = tables[(threadIdx.x >> 5) & 3];
+  for (int idx = lane; idx < 3 * in.R; idx += 32) {
+    const int k = idx / in.R, j = idx % in.R;
+    tab.h[k][j] = mm::ef_half_extent(g.b0[k][j], g.b1[k][j]);
+  }
+  __syncwarp();
   uint32_t acc[16];
   for (int w = 0; w < 16; ++w) acc[w] = 0u;
   const int32_t ch = in.child[2 * n + c], cn = in.count[2 * n + c];
   if (cn > 0) {
-    leaf_warp(in, ch, cn, g, acc, lane);
+    leaf_warp(in, ch, cn, g, acc, lane, tab);
   } else {
     // the descendants of mm::collect, visited in the same order by every lane
     int64_t node[mm::kMaxL];
@@ -110,7 +141,7 @@ __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64
       if (depth[sp] == in.L) {
         fill_warp(acc, gbox, &in.masks[((size_t)m * 2 + cc) * in.W], cbox, in.R, in.eps, lane);
       } else if (mcn > 0) {
-        leaf_warp(in, mch, mcn, g, acc, lane);
+        leaf_warp(in, mch, mcn, g, acc, lane, tab);
       } else {
         node[sp + 1] = mch;
         depth[sp + 1] = depth[sp] + 1;

@@ -2,7 +2,10 @@
 // Alg. 2), shared by the host builder (masks.cpp) and the GPU builder
 // (cuda/masks_gpu.cu): one source, compiled for both, so both set the same
 // bits.  Double precision, each operation written out in the order of its
-// definition (built without FMA contraction on either side).
+// definition (built without FMA contraction on either side).  The GPU
+// builder first tries each SAT test with an FP32 filter that decides only
+// where the FP64 result is certain (below); on the host, where FP64 is as
+// fast as FP32, the FP64 test runs directly.
 #ifndef SUBCULL_MASK_MATH_H
 #define SUBCULL_MASK_MATH_H
 
@@ -60,6 +63,136 @@ SC_HD bool tri_box_overlap(const double* v, const double* bmin, const double* bm
     }
   }
   return true;
+}
+
+// ---- single-precision filter for tri_box_overlap ----------------------
+// FP64 runs at a small fraction of FP32's rate on the GPU, and the SAT
+// test above dominates the GPU mask build.  The filter evaluates the same axes
+// in FP32, each value carrying a bound on its distance from the exact real
+// value of the same expression on the same (double) inputs.  A comparison
+// is decided only when its two sides differ by more than their bounds
+// (times a safety factor that also covers the rounding of the bounds
+// themselves and the far smaller error of the FP64 evaluation); the exact
+// comparison, and so the FP64 one, then has the same outcome.  The overlap
+// result is "no axis separates", independent of the order of the axes:
+// it is decided as "separated" as soon as one axis separates with margin,
+// as "overlap" when every axis fails to separate with margin, and left to
+// the FP64 test otherwise.
+
+// An FP32 value and a bound on |value - exact|.
+struct Ef {
+  float v, e;
+};
+constexpr float kEfU = 5.9604644775390625e-08f;  // 2^-24, unit roundoff
+SC_HD Ef ef_exact(float x) { return Ef{x, 0.0f}; }
+SC_HD Ef ef_add(Ef a, Ef b) {
+  const float v = a.v + b.v;
+  return Ef{v, a.e + b.e + kEfU * fabsf(v)};
+}
+SC_HD Ef ef_sub(Ef a, Ef b) {
+  const float v = a.v - b.v;
+  return Ef{v, a.e + b.e + kEfU * fabsf(v)};
+}
+SC_HD Ef ef_mul(Ef a, Ef b) {
+  const float v = a.v * b.v;
+  return Ef{v, fabsf(a.v) * b.e + fabsf(b.v) * a.e + a.e * b.e + kEfU * fabsf(v)};
+}
+SC_HD Ef ef_neg(Ef a) { return Ef{-a.v, a.e}; }
+SC_HD Ef ef_abs(Ef a) { return Ef{fabsf(a.v), a.e}; }
+SC_HD Ef ef_min(Ef a, Ef b) { return Ef{a.v < b.v ? a.v : b.v, a.e > b.e ? a.e : b.e}; }
+SC_HD Ef ef_max(Ef a, Ef b) { return Ef{a.v > b.v ? a.v : b.v, a.e > b.e ? a.e : b.e}; }
+
+// x > y: +1 certainly, -1 certainly not, 0 too close to tell (and for
+// values so small that their bounds could have underflowed).
+SC_HD int ef_gt(Ef x, Ef y) {
+  if (fabsf(x.v) < 1e-18f && fabsf(y.v) < 1e-18f) return 0;
+  const float margin = (x.e + y.e) * 1.001f + 1e-30f;
+  const float d = x.v - y.v;
+  return d > margin ? 1 : (-d > margin ? -1 : 0);
+}
+
+// One axis: separated when min(p) > r or max(p) < -r.  +1 separated, -1 not
+// separated, 0 undecided.
+SC_HD int ef_sep(Ef p0, Ef p1, Ef p2, Ef r) {
+  const int lo = ef_gt(ef_min(ef_min(p0, p1), p2), r);
+  const int hi = ef_gt(ef_neg(r), ef_max(ef_max(p0, p1), p2));
+  if (lo > 0 || hi > 0) return 1;
+  return (lo < 0 && hi < 0) ? -1 : 0;
+}
+
+// The FP32 inputs of one axis: a vertex coordinate relative to the box
+// centre, vk - (bmin + bmax) / 2, and the half extent (bmax - bmin) / 2.
+// Both are formed in FP64, where the cancellation of nearby coordinates is
+// exact enough, then rounded to FP32; the bounds cover both roundings (the
+// FP64 ones are at most 2^-52 (|bmin| + |bmax|)).
+SC_HD Ef ef_rel(double vk, double bmin, double bmax) {
+  const double c = 0.5 * (bmin + bmax);
+  const float absk = 4.5e-16f * ((float)fabs(bmin) + (float)fabs(bmax));
+  const float af = (float)(vk - c);
+  return Ef{af, 2.0f * kEfU * fabsf(af) + absk + 1e-38f};
+}
+SC_HD Ef ef_half_extent(double bmin, double bmax) {
+  const float absk = 4.5e-16f * ((float)fabs(bmin) + (float)fabs(bmax));
+  const float hf = (float)(0.5 * (bmax - bmin));
+  return Ef{hf, 2.0f * kEfU * fabsf(hf) + absk + 1e-38f};
+}
+
+// The 13 axes of tri_box_overlap in FP32 on a[vertex][axis] (vertices
+// relative to the box centre) and the half extents h: 1 overlap, 0 none,
+// -1 undecided.
+SC_HD int tri_box_overlap_ef(const Ef (*a)[3], const Ef* h) {
+  bool open = false;  // an axis left undecided
+  for (int k = 0; k < 3; ++k) {
+    const int s = ef_sep(a[0][k], a[1][k], a[2][k], h[k]);
+    if (s > 0) return 0;
+    open |= s == 0;
+  }
+  Ef e[3][3];
+  for (int k = 0; k < 3; ++k) {
+    e[0][k] = ef_sub(a[1][k], a[0][k]);
+    e[1][k] = ef_sub(a[2][k], a[1][k]);
+    e[2][k] = ef_sub(a[0][k], a[2][k]);
+  }
+  const Ef nx = ef_sub(ef_mul(e[0][1], e[1][2]), ef_mul(e[0][2], e[1][1]));
+  const Ef ny = ef_sub(ef_mul(e[0][2], e[1][0]), ef_mul(e[0][0], e[1][2]));
+  const Ef nz = ef_sub(ef_mul(e[0][0], e[1][1]), ef_mul(e[0][1], e[1][0]));
+  const Ef d = ef_add(ef_add(ef_mul(nx, a[0][0]), ef_mul(ny, a[0][1])), ef_mul(nz, a[0][2]));
+  const Ef rn = ef_add(ef_add(ef_mul(h[0], ef_abs(nx)), ef_mul(h[1], ef_abs(ny))),
+                       ef_mul(h[2], ef_abs(nz)));
+  {
+    const int s = ef_gt(ef_abs(d), rn);
+    if (s > 0) return 0;
+    open |= s == 0;
+  }
+  const Ef zero = ef_exact(0.0f);
+  for (int i = 0; i < 3; ++i) {
+    const Ef ex = e[i][0], ey = e[i][1], ez = e[i][2];
+    const Ef axes[3][3] = {{zero, ez, ef_neg(ey)}, {ef_neg(ez), zero, ex}, {ey, ef_neg(ex), zero}};
+    for (int k = 0; k < 3; ++k) {
+      const Ef* ax = axes[k];
+      Ef p[3];
+      for (int j = 0; j < 3; ++j)
+        p[j] = ef_add(ef_add(ef_mul(ax[0], a[j][0]), ef_mul(ax[1], a[j][1])),
+                      ef_mul(ax[2], a[j][2]));
+      const Ef r = ef_add(ef_add(ef_mul(h[0], ef_abs(ax[0])), ef_mul(h[1], ef_abs(ax[1]))),
+                          ef_mul(h[2], ef_abs(ax[2])));
+      const int s = ef_sep(p[0], p[1], p[2], r);
+      if (s > 0) return 0;
+      open |= s == 0;
+    }
+  }
+  return open ? -1 : 1;
+}
+
+// tri_box_overlap(v, bmin, bmax) through the FP32 filter: 1 overlap, 0 none,
+// -1 undecided.
+SC_HD int tri_box_overlap_f32(const double* v, const double* bmin, const double* bmax) {
+  Ef h[3], a[3][3];
+  for (int k = 0; k < 3; ++k) {
+    h[k] = ef_half_extent(bmin[k], bmax[k]);
+    for (int i = 0; i < 3; ++i) a[i][k] = ef_rel(v[3 * i + k], bmin[k], bmax[k]);
+  }
+  return tri_box_overlap_ef(a, h);
 }
 
 // Grid of one slot: per axis the dilated voxel bounds.
