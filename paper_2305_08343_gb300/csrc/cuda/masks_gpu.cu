@@ -28,17 +28,25 @@ namespace {
 struct SatTables {
   mm::Ef h[3][8];
   mm::Ef a[3][3][8];  // [vertex][axis][voxel index]
+  int fill_lo[3][9], fill_hi[3][9];  // Alg. 2 parent ranges of the current fill
 };
 
 __device__ void voxelize_warp(const float* t9, const mm::Grid& g, uint32_t* acc, int W,
                               int lane, SatTables& tab) {
   double v[9];
   for (int i = 0; i < 9; ++i) v[i] = (double)t9[i];
-  int r0[3], r1[3];
-  for (int k = 0; k < 3; ++k) {
+  // the candidate range of axis k is found by lane k and broadcast
+  int c0 = 0, c1 = 0;
+  if (lane < 3) {
+    const int k = lane;
     const double tlo = mm::mn(mm::mn(v[k], v[3 + k]), v[6 + k]);
     const double thi = mm::mx(mm::mx(v[k], v[3 + k]), v[6 + k]);
-    g.candidates(k, tlo, thi, r0[k], r1[k]);
+    g.candidates(k, tlo, thi, c0, c1);
+  }
+  int r0[3], r1[3];
+  for (int k = 0; k < 3; ++k) {
+    r0[k] = __shfl_sync(0xffffffffu, c0, k);
+    r1[k] = __shfl_sync(0xffffffffu, c1, k);
   }
   const int R = g.R, nx = r1[0] - r0[0] + 1, ny = r1[1] - r0[1] + 1, nz = r1[2] - r0[2] + 1;
   __syncwarp();  // the previous triangle's table has been read
@@ -67,23 +75,19 @@ __device__ void voxelize_warp(const float* t9, const mm::Grid& g, uint32_t* acc,
   }
 }
 
+// Alg. 2 fill of one descendant's mask: the parent ranges of the 3 (R + 1)
+// child borders are computed one per lane (R + 1 <= 9) into the warp's
+// table, then the lanes split the child's set cells.
 __device__ void fill_warp(uint32_t* acc, const float* pbox, const uint32_t* cmask,
-                          const float* cbox, int R, double eps, int lane) {
-  int lo_i[3][9], hi_i[3][9];
-  for (int k = 0; k < 3; ++k) {
-    const double cl = (double)cbox[k], cext = (double)cbox[3 + k] - (double)cbox[k];
-    const double pl = (double)pbox[k], pext = (double)pbox[3 + k] - (double)pbox[k];
-    for (int i = 0; i <= R; ++i) {
-      const double border = cl + (cext * (double)i) / (double)R;
-      if (pext > 0.0) {
-        lo_i[k][i] = mm::parent_idx(border - eps, pl, pext, R);
-        hi_i[k][i] = mm::parent_idx(border + eps, pl, pext, R);
-      } else {
-        lo_i[k][i] = 0;
-        hi_i[k][i] = R - 1;
-      }
-    }
+                          const float* cbox, int R, double eps, int lane, SatTables& tab) {
+  __syncwarp();  // the previous fill's table has been read
+  if (lane < 3 * (R + 1)) {
+    const int k = lane / (R + 1), i = lane % (R + 1);
+    mm::fill_range(pbox, cbox, k, i, R, eps, tab.fill_lo[k][i], tab.fill_hi[k][i]);
   }
+  __syncwarp();
+  const int(*lo_i)[9] = tab.fill_lo;
+  const int(*hi_i)[9] = tab.fill_hi;
   for (int cell = lane; cell < R * R * R; cell += 32) {
     if (!mm::get_bit(cmask, cell)) continue;
     const int x = cell % R, y = (cell / R) % R, z = cell / (R * R);
@@ -107,10 +111,21 @@ __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64
   const int64_t n = nodes[slot >> 1];
   const int c = (int)(slot & 1);
   const float* gbox = &in.box[12 * n + 6 * c];
-  mm::Grid g;
-  g.init(gbox, in.R, in.eps);
-  __shared__ SatTables tables[4];  // one per warp of a 128-thread block
-  SatTables& tab = tables[(threadIdx.x >> 5) & 3];
+  // the slot's grid, built entry by entry by the lanes of the warp (the
+  // same operations as Grid::init) in shared memory
+  __shared__ mm::Grid grids[4];    // one per warp of a 128-thread block
+  __shared__ SatTables tables[4];
+  const int wib = (threadIdx.x >> 5) & 3;
+  mm::Grid& g = grids[wib];
+  SatTables& tab = tables[wib];
+  if (lane == 0) {
+    g.R = in.R;
+    g.eps = in.eps;
+  }
+  if (lane < 3) g.init_axis(gbox, lane);
+  __syncwarp();
+  if (lane < 3 * in.R) g.init_cell(lane / in.R, lane % in.R);
+  __syncwarp();
   for (int idx = lane; idx < 3 * in.R; idx += 32) {
     const int k = idx / in.R, j = idx % in.R;
     tab.h[k][j] = mm::ef_half_extent(g.b0[k][j], g.b1[k][j]);
@@ -139,7 +154,8 @@ __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64
       const int32_t mch = in.child[2 * m + cc], mcn = in.count[2 * m + cc];
       const float* cbox = &in.box[12 * m + 6 * cc];
       if (depth[sp] == in.L) {
-        fill_warp(acc, gbox, &in.masks[((size_t)m * 2 + cc) * in.W], cbox, in.R, in.eps, lane);
+        fill_warp(acc, gbox, &in.masks[((size_t)m * 2 + cc) * in.W], cbox, in.R, in.eps, lane,
+                  tab);
       } else if (mcn > 0) {
         leaf_warp(in, mch, mcn, g, acc, lane, tab);
       } else {

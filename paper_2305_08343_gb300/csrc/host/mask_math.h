@@ -205,13 +205,19 @@ struct Grid {
     R = R_;
     eps = eps_;
     for (int k = 0; k < 3; ++k) {
-      lo[k] = (double)box[k];
-      ext[k] = (double)box[3 + k] - (double)box[k];
-      for (int i = 0; i < R; ++i) {
-        b0[k][i] = (lo[k] + (ext[k] * (double)i) / (double)R) - eps_;
-        b1[k][i] = (lo[k] + (ext[k] * (double)(i + 1)) / (double)R) + eps_;
-      }
+      init_axis(box, k);
+      for (int i = 0; i < R; ++i) init_cell(k, i);
     }
+  }
+  // the two steps of init, also run entry by entry by the lanes of a warp
+  // (R and eps set first, then the axes, then the cells)
+  SC_HD void init_axis(const float* box, int k) {
+    lo[k] = (double)box[k];
+    ext[k] = (double)box[3 + k] - (double)box[k];
+  }
+  SC_HD void init_cell(int k, int i) {
+    b0[k][i] = (lo[k] + (ext[k] * (double)i) / (double)R) - eps;
+    b1[k][i] = (lo[k] + (ext[k] * (double)(i + 1)) / (double)R) + eps;
   }
   // Voxels [i0, i1] on axis k whose dilated box may overlap [tlo, thi]; one
   // voxel of margin beyond the eps-widened range keeps this a superset of
@@ -264,24 +270,28 @@ SC_HD int parent_idx(double pos, double plo, double pext, int R) {
   return (int)q;
 }
 
+// Alg. 2: the parent cells [lo, hi] on axis k that child border i (of
+// 0..R) falls in, the border dilated by eps.
+SC_HD void fill_range(const float* pbox, const float* cbox, int k, int i, int R, double eps,
+                      int& lo, int& hi) {
+  const double cl = (double)cbox[k], cext = (double)cbox[3 + k] - (double)cbox[k];
+  const double pl = (double)pbox[k], pext = (double)pbox[3 + k] - (double)pbox[k];
+  const double border = cl + (cext * (double)i) / (double)R;
+  if (pext > 0.0) {
+    lo = parent_idx(border - eps, pl, pext, R);
+    hi = parent_idx(border + eps, pl, pext, R);
+  } else {
+    lo = 0;
+    hi = R - 1;
+  }
+}
+
 // Alg. 2 (fillByApproximatedOccupancy) with borders dilated by eps.
 SC_HD void fill_from_child(uint32_t* out, const float* pbox, const uint32_t* cmask,
                            const float* cbox, int R, double eps) {
   int lo_i[3][9], hi_i[3][9];
-  for (int k = 0; k < 3; ++k) {
-    const double cl = (double)cbox[k], cext = (double)cbox[3 + k] - (double)cbox[k];
-    const double pl = (double)pbox[k], pext = (double)pbox[3 + k] - (double)pbox[k];
-    for (int i = 0; i <= R; ++i) {
-      const double border = cl + (cext * (double)i) / (double)R;
-      if (pext > 0.0) {
-        lo_i[k][i] = parent_idx(border - eps, pl, pext, R);
-        hi_i[k][i] = parent_idx(border + eps, pl, pext, R);
-      } else {
-        lo_i[k][i] = 0;
-        hi_i[k][i] = R - 1;
-      }
-    }
-  }
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i <= R; ++i) fill_range(pbox, cbox, k, i, R, eps, lo_i[k][i], hi_i[k][i]);
   for (int z = 0; z < R; ++z)
     for (int y = 0; y < R; ++y)
       for (int x = 0; x < R; ++x) {
