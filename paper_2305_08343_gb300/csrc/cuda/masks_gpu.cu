@@ -25,6 +25,11 @@ namespace {
 // of the current triangle relative to every voxel centre on its axis (set
 // once per triangle), so that a triangle/voxel pair needs no FP64 work
 // unless the filter leaves it undecided.
+// Threads per block of slot_masks_kernel: one warp per child slot, and
+// one set of shared-memory tables per warp.
+constexpr int kMaskThreads = 128;
+constexpr int kMaskWarps = kMaskThreads / 32;
+
 struct SatTables {
   mm::Ef h[3][8];
   mm::Ef a[3][3][8];  // [vertex][axis][voxel index]
@@ -113,9 +118,9 @@ __global__ void slot_masks_kernel(mm::MaskInputs in, const int64_t* nodes, int64
   const float* gbox = &in.box[12 * n + 6 * c];
   // the slot's grid, built entry by entry by the lanes of the warp (the
   // same operations as Grid::init) in shared memory
-  __shared__ mm::Grid grids[4];    // one per warp of a 128-thread block
-  __shared__ SatTables tables[4];
-  const int wib = (threadIdx.x >> 5) & 3;
+  __shared__ mm::Grid grids[kMaskWarps];
+  __shared__ SatTables tables[kMaskWarps];
+  const int wib = threadIdx.x >> 5;
   mm::Grid& g = grids[wib];
   SatTables& tab = tables[wib];
   if (lane == 0) {
@@ -251,7 +256,7 @@ void masks_gpu_levels(Bvh& b, const std::vector<uint8_t>* node_dirty) {
   for (int dep = b.max_depth; dep >= 0; --dep) {
     const int64_t nslots = 2 * (int64_t)(start[dep + 1] - start[dep]);
     if (nslots == 0) continue;
-    const int threads = 128;  // four slots per block, a warp each
+    const int threads = kMaskThreads;  // a warp per slot
     const int64_t warps_per_block = threads / 32;
     slot_masks_kernel<<<(unsigned)((nslots + warps_per_block - 1) / warps_per_block), threads, 0,
                         st>>>(in, d_order + start[dep], nslots);
