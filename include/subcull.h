@@ -46,7 +46,10 @@
 extern "C" {
 #endif
 
-#define SC_ABI_VERSION 1
+/* Raised whenever a struct or enum of this header changes layout or meaning.
+   2: sc_tune_result gained `variant` (the autotuner also chooses the stack
+   placement and the resident blocks per SM). */
+#define SC_ABI_VERSION 2
 
 typedef enum {
   SC_OK = 0,

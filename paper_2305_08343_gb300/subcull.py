@@ -15,6 +15,7 @@ import numpy as np
 
 from . import _build
 
+SC_ABI_VERSION = 2  # include/subcull.h; the library must report the same
 SC_OK = 0
 SC_ERR_ARG, SC_ERR_CUDA, SC_ERR_NOMEM, SC_ERR_TIMEOUT = -1, -2, -3, -4
 SC_ERR_STACK, SC_ERR_UNSUPPORTED, SC_ERR_STATE, SC_ERR_IO = -5, -6, -7, -8
@@ -165,6 +166,10 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        got = L.sc_abi_version()
+        if got != SC_ABI_VERSION:
+            raise RuntimeError(f"libsubcull reports ABI version {got}, this binding is written "
+                               f"for {SC_ABI_VERSION}: rebuild the library")
         _lib = L
         return L
 

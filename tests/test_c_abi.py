@@ -18,7 +18,7 @@ PROGRAM = r"""
 #include <stdlib.h>
 
 int main(void) {
-  if (sc_abi_version() != 1) return 1;
+  if (sc_abi_version() != SC_ABI_VERSION || SC_ABI_VERSION != 2) return 1;
   sc_build_opts o;
   sc_build_opts_default(&o);
   if (o.max_leaf != 4 || o.bins != 32 || o.gpu_bvh != 0 || o.gpu_masks != 0) return 2;

@@ -105,7 +105,7 @@ def test_library_exports_every_declared_symbol():
     L = sc.lib()
     missing = [n for n in sorted(names) if not hasattr(L, n)]
     assert not missing, missing
-    assert L.sc_abi_version() == 1
+    assert L.sc_abi_version() == sc.SC_ABI_VERSION == 2
 
 
 def test_errors_are_reported_not_raised_through_the_abi():
