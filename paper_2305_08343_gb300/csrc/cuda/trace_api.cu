@@ -243,6 +243,16 @@ void fill_params(const sc_dbvh* d, sct::Params& p) {
   p.has_root = d->has_root;
 }
 
+// The lookup variant of a wave launch: the factored tables in shared memory
+// are built for the wave pipeline only at R = 6 with uncompressed masks and
+// stored scales (and at R = 4 as the full table); the full table elsewhere.
+int waves_lutv(const sc_dbvh* d, int lut_mode) {
+  int lutv = lut_variant(d, lut_mode);
+  if (lutv == 1 && d->lay.R != 4 && !(d->lay.R == 6 && !d->lay.compress && d->lay.scales))
+    lutv = 0;
+  return lutv;
+}
+
 sct::WaveKernelFn pick_waves(const sc_dbvh* d, int cull, int lutv, int block, int stack) {
   if (d->lay.width == 4) {
     if (block == 64 || stack != 64)
@@ -305,11 +315,7 @@ void launch_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, int bounces
     fail(SC_ERR_UNSUPPORTED, "BVH depth %d exceeds the traversal stack (%d)", d->stack_need,
          stack);
   if (o.refill < 0 || o.refill > 32) fail(SC_ERR_ARG, "refill must be 0..32");
-  int lutv = lut_variant(d, o.lut_mode);
-  // factored tables in shared memory: built for the wave pipeline only at
-  // R = 6 with uncompressed masks and stored scales; the full table elsewhere
-  if (lutv == 1 && d->lay.R != 4 && !(d->lay.R == 6 && !d->lay.compress && d->lay.scales))
-    lutv = 0;
+  const int lutv = waves_lutv(d, o.lut_mode);
   sct::WaveKernelFn k = nullptr;
   if (o.variant) {
     check_variant(d, cull, lutv, o.variant);
@@ -742,8 +748,7 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
   // the stack's top entries in a shared-memory ring, and 9 or 10 resident
   // blocks per SM (56 or 48 registers a thread): built at block 128 /
   // stack 64 for the images that have kernel variants
-  int lutv = lut_variant(d, o.lut_mode);
-  if (lutv == 1) lutv = 0;
+  const int lutv = waves_lutv(d, o.lut_mode);
   const int placements[5] = {sct::OPT_SSTACK, sct::OPT_OCC9, sct::OPT_OCC9 | sct::OPT_SSTACK,
                              sct::OPT_OCC10, sct::OPT_OCC10 | sct::OPT_SSTACK};
   if (o.variant == 0 && variant_image_ok(d, cull, lutv) && d->stack_need <= 64)

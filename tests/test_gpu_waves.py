@@ -162,6 +162,30 @@ def test_autotuner_considers_the_stack_ring(comp, cull):
                                b2.hits[w][:m].view(torch.int32)[ib])
 
 
+@pytest.mark.parametrize("lut", [sc.SC_LUT_SHARED, sc.SC_LUT_FACTORED_L1, sc.SC_LUT_GLOBAL])
+def test_autotuner_with_lookup_modes(lut):
+    """The tuner adds its stack / occupancy candidates only where those
+    kernels exist for the image and lookup mode; with the factored tables it
+    tunes the factored kernels alone, and the result traces the same."""
+    tris = sg.hair(300, 16, True, seed=38)
+    rays = sg.pinhole(96, 96)
+    b = sc.sc_bvh_build(tris, 6, 0)
+    d = sc.DeviceBVH(b, sc.SC_LAYOUT_MASKED)
+    r = torch.from_numpy(rays).cuda()
+    bufs = sc.WaveBuffers(r.shape[0], 2, with_counts=False)
+    best, rows = sc.sc_autotune_waves(d, r, 2, 9, 1, bufs, sc._opts(lut_mode=lut), reps=1)
+    placed = [x for x in rows if x[4] != 0]
+    assert (len(placed) > 0) == (lut == sc.SC_LUT_GLOBAL)
+    b1, s1 = sc.trace_waves(d, r, 2, 9, 1, opts=best)
+    b2, s2 = sc.trace_waves(d, r, 2, 9, 1)
+    assert list(s1) == list(s2)
+    for w in range(3):
+        m = int(s1[w])
+        ia, ib = torch.argsort(b1.path[w][:m]), torch.argsort(b2.path[w][:m])
+        assert torch.equal(b1.hits[w][:m].view(torch.int32)[ia],
+                           b2.hits[w][:m].view(torch.int32)[ib])
+
+
 def test_waves_culled_equals_plain_and_sizes():
     tris = sg.hair(800, 16, True, seed=32)
     rays = sg.pinhole(96, 64)
