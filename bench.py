@@ -60,21 +60,20 @@ WORKLOAD_BOUNCES = {"hair1m": 1, "hair1m_comp": 1, "hair12m": 2, "hair12m_unc": 
 # DRAM traffic per launch of the timed kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture, summarised in profiles/), valid
 # only while the kernel source is the one that was measured: keyed by the
-# workload and the kernel option set the autotuner chose (0, the
-# shared-memory stack ring 128, 9 blocks per SM 1024, or both 1152), and
-# checked against the SHA-256 of the traversal kernel header.
-_TRAFFIC_SRC = "22ddcb918572195aa2d0f89e8a0e91ab1354b1d086cc720a6ab0d3440e7f9186"
+# workload and the kernel option set the autotuner chose (0; the
+# shared-memory stack ring 128; 9 blocks per SM with the hit in shared
+# memory 5120, and with the ring as well 5248), and checked against the
+# SHA-256 of the traversal kernel header.
+_TRAFFIC_SRC = "9bd81071782f1e9abad85e5c18b4b890c5d92ac0d691dd23f101de14390d4ced"
 _P12, _P1 = "profiles/waves_kernel_hair12m.md", "profiles/waves_kernel_hair1m.md"
 MEASURED_TRAFFIC = {
     # (workload, variant): (bytes per launch, kernel source sha256, profile summary)
-    ("hair12m", 0): (1.985320e+09 + 3.990750e+08, _TRAFFIC_SRC, _P12),
-    ("hair12m", 128): (1.546924e+09 + 2.983990e+08, _TRAFFIC_SRC, _P12),
-    ("hair12m", 1024): (2.692479e+09 + 5.732360e+08, _TRAFFIC_SRC, _P12),
-    ("hair12m", 1152): (1.956720e+09 + 3.609250e+08, _TRAFFIC_SRC, _P12),
-    ("hair1m", 0): (1.720134e+09 + 2.593690e+08, _TRAFFIC_SRC, _P1),
-    ("hair1m", 128): (1.329806e+09 + 2.098700e+08, _TRAFFIC_SRC, _P1),
-    ("hair1m", 1024): (2.174589e+09 + 3.720220e+08, _TRAFFIC_SRC, _P1),
-    ("hair1m", 1152): (1.610462e+09 + 2.512270e+08, _TRAFFIC_SRC, _P1),
+    ("hair12m", 0): (1.870604e+09 + 3.807340e+08, _TRAFFIC_SRC, _P12),
+    ("hair12m", 128): (1.472805e+09 + 2.905644e+08, _TRAFFIC_SRC, _P12),
+    ("hair12m", 5120): (2.369406e+09 + 4.878799e+08, _TRAFFIC_SRC, _P12),
+    ("hair12m", 5248): (1.751152e+09 + 3.291162e+08, _TRAFFIC_SRC, _P12),
+    ("hair1m", 0): (1.721418e+09 + 2.544407e+08, _TRAFFIC_SRC, _P1),
+    ("hair1m", 5120): (2.065885e+09 + 3.354545e+08, _TRAFFIC_SRC, _P1),
 }
 
 

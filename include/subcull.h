@@ -347,6 +347,10 @@ enum {
   SC_VARIANT_OCC10 = 2048,     /* waves: 10 resident blocks per SM (48
                                   registers); combinable with
                                   SC_VARIANT_SSTACK                         */
+  SC_VARIANT_HSLOT = 4096,     /* the accepted hit's u, v and triangle id in
+                                  a per-thread shared-memory slot instead of
+                                  registers; combinable with SC_VARIANT_OCC9
+                                  and SC_VARIANT_SSTACK                     */
   SC_VARIANT_DEFER = 32        /* compressed masks with the bit table: each
                                   child's bit-table lookup is issued when the
                                   child is visited, beside its own fetch
@@ -481,9 +485,10 @@ sc_status sc_trace_waves_host(const sc_dbvh* d, const float* h_rays, int64_t n0,
    other than 128 and stack 32 exist for R = 6 and plain traversal only.
    When base->variant is 0 and the image has kernel variants, the candidates
    also hold block 128 / stack 64 (refill 4 and 8) with SC_VARIANT_SSTACK
-   (the top stack entries in shared memory), SC_VARIANT_OCC9 and
-   SC_VARIANT_OCC10 (more resident blocks, fewer registers) and their
-   combinations; *best->variant then says which was chosen.
+   (the top stack entries in shared memory), SC_VARIANT_OCC9 (more resident
+   blocks, fewer registers), SC_VARIANT_HSLOT (the hit's u, v and id in
+   shared memory) and their combinations; *best->variant then says which
+   was chosen.
    d_ws must be sized for the largest chunk (wave_chunk = 0).  Synchronous. */
 typedef struct {
   int block, stack, refill;

@@ -745,12 +745,17 @@ sc_status sc_autotune_waves(const sc_dbvh* d, const float* d_rays, int64_t n0, i
           t.wave_chunk = ch;
           cands.push_back(t);
         }
-  // the stack's top entries in a shared-memory ring, and 9 or 10 resident
-  // blocks per SM (56 or 48 registers a thread): built at block 128 /
-  // stack 64 for the images that have kernel variants
+  // the stack's top entries in a shared-memory ring, 9 resident blocks per
+  // SM (56 registers a thread) and the hit's u, v and id in shared memory,
+  // and their combinations: built at block 128 / stack 64 for the images
+  // that have kernel variants (10 blocks per SM never won and is not tried)
   const int lutv = waves_lutv(d, o.lut_mode);
-  const int placements[5] = {sct::OPT_SSTACK, sct::OPT_OCC9, sct::OPT_OCC9 | sct::OPT_SSTACK,
-                             sct::OPT_OCC10, sct::OPT_OCC10 | sct::OPT_SSTACK};
+  const int placements[6] = {sct::OPT_SSTACK,
+                             sct::OPT_OCC9,
+                             sct::OPT_OCC9 | sct::OPT_SSTACK,
+                             sct::OPT_HSLOT,
+                             sct::OPT_HSLOT | sct::OPT_OCC9,
+                             sct::OPT_HSLOT | sct::OPT_OCC9 | sct::OPT_SSTACK};
   if (o.variant == 0 && variant_image_ok(d, cull, lutv) && d->stack_need <= 64)
     for (int v : placements) {
       if (!sct::var_supported(v)) continue;

@@ -125,6 +125,8 @@ enum : int {
   OPT_OCC9 = 1024,  // waves: 9 resident blocks of 128 threads per SM (56 registers)
                     // instead of 8 (64 registers)
   OPT_OCC10 = 2048, // waves: 10 resident blocks of 128 threads per SM (48 registers)
+  OPT_HSLOT = 4096, // the accepted hit's u, v and triangle id kept in a per-thread
+                    // shared-memory slot instead of three registers
   OPT_DEFER = 32, // compressed, bit table: a child's culling lookup is issued
                   // when the child is visited, beside its own fetch (the
                   // cells still come from the parent's slab test)
@@ -503,6 +505,32 @@ struct RayState {
   uint32_t ctest;  // OPT_DEFER: pending test of `cur`: bit-table word index << 5 | bit, or kNoTest
 };
 
+// OPT_HSLOT: the u, v and triangle id of each thread's accepted hit live in
+// shared memory (written at each accept, a few times per ray; read once when
+// the ray finishes), which frees three registers.  Blocks of up to kMaxBlock
+// threads.
+constexpr int kMaxBlock = 256;
+__device__ __forceinline__ float4* hit_slot() {
+  __shared__ float4 slots[kMaxBlock];
+  return slots + threadIdx.x;
+}
+
+// An accepted triangle at leaf position pos (A: its first float4, whose w is
+// the id).
+template <int OPT>
+__device__ __forceinline__ void record_accept(RayState& s, float t, float u, float v,
+                                              const float4 A, int pos) {
+  s.ht = t;
+  s.hpos = pos;
+  if constexpr ((OPT & OPT_HSLOT) != 0) {
+    *hit_slot() = make_float4(u, v, A.w, 0.0f);
+  } else {
+    s.hu = u;
+    s.hv = v;
+    s.hid = __float_as_int(A.w);
+  }
+}
+
 __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const float4 rb,
                                          const Params& p) {
   s.ox = ra.x; s.oy = ra.y; s.oz = ra.z; s.tmin = ra.w;
@@ -522,6 +550,19 @@ __device__ __forceinline__ void ray_init(RayState& s, const float4 ra, const flo
   s.have = p.has_root != 0;
   s.pre = false;
   s.ctest = kNoTest;
+}
+
+// The hit record {t, id bits, u, v} of a finished ray; {inf, -1, 0, 0} for
+// a miss.
+template <int OPT>
+__device__ __forceinline__ float4 hit_record(const RayState& s) {
+  if constexpr ((OPT & OPT_HSLOT) != 0) {
+    if (s.hpos < 0) return make_float4(s.ht, __int_as_float(-1), 0.0f, 0.0f);
+    const float4 h = *hit_slot();
+    return make_float4(s.ht, h.z, h.x, h.y);
+  } else {
+    return make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+  }
 }
 
 // Culling test of one child from its record data: Alg. 1 cells of the
@@ -831,11 +872,7 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
           ++s.ttest;
           float t, u, v;
           if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
-            s.ht = t;
-            s.hu = u;
-            s.hv = v;
-            s.hid = __float_as_int(A.w);
-            s.hpos = first;
+            record_accept<OPT>(s, t, u, v, A, first);
             if (MODE == 1) return true;
             s.tcur = t;
           }
@@ -871,11 +908,7 @@ __device__ __forceinline__ bool trace_step(const Params& p, RayState& s, uint2* 
         ++s.ttest;
         float t, u, v;
         if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
-          s.ht = t;
-          s.hu = u;
-          s.hv = v;
-          s.hid = __float_as_int(A.w);
-          s.hpos = first + i;
+          record_accept<OPT>(s, t, u, v, A, first + i);
           if (MODE == 1) {
             done = true;
             break;
@@ -1029,11 +1062,7 @@ __device__ __forceinline__ bool trace_step4(const Params& p, RayState& s, uint2*
         ++s.ttest;
         float t, u, v;
         if (tri_test(A, E1, E2, s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.tmin, s.tcur, t, u, v)) {
-          s.ht = t;
-          s.hu = u;
-          s.hv = v;
-          s.hid = __float_as_int(A.w);
-          s.hpos = first + i;
+          record_accept<OPT>(s, t, u, v, A, first + i);
           if (MODE == 1) {
             done = true;
             break;
@@ -1232,7 +1261,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel(Params p) {
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
     if (step_w<WIDTH, R, CULL, MODE, LUTV, SCALES, kStack, OPT>(p, s, stack, sh, tstack)) {
-      p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+      p.hits[rid] = hit_record<OPT>(s);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
     }
@@ -1471,6 +1500,7 @@ template <int R, int CULL, int LUTV, int SCALES, int BLOCK = kBlock, int STACK =
           int WIDTH = 2, int OPT = 0>
 __global__ void __launch_bounds__(BLOCK, kWaveBlocksPerSM<OPT> * kBlock / BLOCK)
     waves_kernel(WaveParams wp) {
+  static_assert(BLOCK <= kMaxBlock, "the hit slots hold kMaxBlock threads");
   constexpr int RR = (R > 0 ? R : 4);
   __shared__ SharedTables<RR, LUTV> sh;
   const Params& p = wp.p;
@@ -1534,14 +1564,14 @@ __global__ void __launch_bounds__(BLOCK, kWaveBlocksPerSM<OPT> * kBlock / BLOCK)
         if (done) {
           pid = qpath ? (unsigned)__ldcg(&qpath[rid]) : (unsigned)(c0 + rid);
           const long long o = out_base + rid;
-          wp.hits[w][o] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+          wp.hits[w][o] = hit_record<OPT>(s);
           if (wp.path[w]) wp.path[w][o] = (int)pid;
           if (wp.counts[w]) wp.counts[w][o] = make_uint2(s.ntest, s.ttest);
           if (wp.orays[w]) {
             wp.orays[w][2 * o] = __ldcg(&rays[2 * rid]);
             wp.orays[w][2 * o + 1] = __ldcg(&rays[2 * rid + 1]);
           }
-          if (w < wp.bounces && s.hid >= 0) {
+          if (w < wp.bounces && s.hpos >= 0) {
             const float4* tp = p.tris + 3 * (long long)s.hpos;
             spawn = make_bounce(s.ox, s.oy, s.oz, s.dx, s.dy, s.dz, s.ht, __ldg(tp + 1),
                                 __ldg(tp + 2), wp.seed, pid, (unsigned)(w + 1), b0, b1);
@@ -1651,7 +1681,7 @@ __global__ void __launch_bounds__(kBlock) seeded_kernel(Params p, const int* cls
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
     if (phase == 2 && has_seed && s.have && s.cur == seed) {
-      if (s.hid >= 0 && s.hpos == seed_pos) s.tcur = s.ht;  // the seed counts as found here
+      if (s.hpos >= 0 && s.hpos == seed_pos) s.tcur = s.ht;  // the seed counts as found here
       s.have = false;
     }
     if (trace_step<R, CULL, 0, LUTV, SCALES, kStack, OPT>(p, s, stack, sh)) {
@@ -1660,7 +1690,7 @@ __global__ void __launch_bounds__(kBlock) seeded_kernel(Params p, const int* cls
         s.sp = 0;
         s.cur = p.root_slot;
         s.have = p.has_root != 0;
-        if (s.hid >= 0) {
+        if (s.hpos >= 0) {
           seed_pos = s.hpos;
           s.tcur = nextafterf(s.ht, __int_as_float(0x7f800000));
         } else {
@@ -1668,7 +1698,7 @@ __global__ void __launch_bounds__(kBlock) seeded_kernel(Params p, const int* cls
         }
         continue;
       }
-      p.hits[rid] = make_float4(s.ht, __int_as_float(s.hid), s.hu, s.hv);
+      p.hits[rid] = hit_record<OPT>(s);
       if (p.counts) p.counts[rid] = make_uint2(s.ntest, s.ttest);
       active = false;
     }

@@ -24,7 +24,7 @@ WaveKernelFn waves_of() {
   X(OPT_FUSED) X(OPT_PAIR) X(OPT_SPEC) X(OPT_TOS) X(OPT_SPEC | OPT_TOS) X(OPT_SORT) \
   X(OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_FUSED | OPT_SPEC | OPT_TOS | OPT_SORT) X(OPT_DEFER) \
   X(OPT_LAZY) X(OPT_SSTACK) X(OPT_TL1) X(OPT_OCC9) X(OPT_OCC9 | OPT_SSTACK) X(OPT_OCC10) \
-  X(OPT_OCC10 | OPT_SSTACK)
+  X(OPT_OCC10 | OPT_SSTACK) X(OPT_HSLOT) X(OPT_HSLOT | OPT_OCC9) X(OPT_HSLOT | OPT_OCC9 | OPT_SSTACK)
 
 }  // namespace
 

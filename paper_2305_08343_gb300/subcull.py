@@ -86,6 +86,7 @@ SC_VARIANT_SSTACK = 128
 SC_VARIANT_TABLE_L1 = 256
 SC_VARIANT_OCC9 = 1024
 SC_VARIANT_OCC10 = 2048
+SC_VARIANT_HSLOT = 4096
 
 
 class sc_tune_result(C.Structure):

@@ -23,7 +23,9 @@ F, P, S, T, O, D = (sc.SC_VARIANT_FUSED_CELLS, sc.SC_VARIANT_PAIR, sc.SC_VARIANT
 VARIANTS = [F, P, S, T, S | T, O, S | T | O, F | S | T | O, D, sc.SC_VARIANT_LAZY,
             sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_TABLE_L1, sc.SC_VARIANT_OCC9,
             sc.SC_VARIANT_OCC9 | sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_OCC10,
-            sc.SC_VARIANT_OCC10 | sc.SC_VARIANT_SSTACK]
+            sc.SC_VARIANT_OCC10 | sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_HSLOT,
+            sc.SC_VARIANT_HSLOT | sc.SC_VARIANT_OCC9,
+            sc.SC_VARIANT_HSLOT | sc.SC_VARIANT_OCC9 | sc.SC_VARIANT_SSTACK]
 # (cull mode of the oracle, compressed, lookup)
 CONFIGS = [(2, 1, sc.SC_LUT_BITTABLE), (1, 0, sc.SC_LUT_GLOBAL), (0, 0, sc.SC_LUT_AUTO)]
 

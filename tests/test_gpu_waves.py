@@ -136,8 +136,8 @@ def test_autotuner_returns_a_valid_config():
 @pytest.mark.parametrize("comp,cull", [(1, 1), (0, 1), (0, 0)])
 def test_autotuner_considers_the_stack_ring(comp, cull):
     """On images with kernel variants the tuner also times the shared-memory
-    stack ring and the 9- and 10-block occupancy bounds (block 128, stack
-    64); whatever it picks traces the same."""
+    stack ring, the 9-block occupancy bound and the shared-memory hit slot
+    (block 128, stack 64); whatever it picks traces the same."""
     tris = sg.hair(300, 16, True, seed=37)
     rays = sg.pinhole(128, 128)
     b = sc.sc_bvh_build(tris, 6, comp)
@@ -145,8 +145,8 @@ def test_autotuner_considers_the_stack_ring(comp, cull):
     r = torch.from_numpy(rays).cuda()
     bufs = sc.WaveBuffers(r.shape[0], 2, with_counts=False)
     best, rows = sc.sc_autotune_waves(d, r, 2, 9, cull, bufs, reps=1)
-    placed = {sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_OCC9, sc.SC_VARIANT_OCC10,
-              sc.SC_VARIANT_OCC9 | sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_OCC10 | sc.SC_VARIANT_SSTACK}
+    S, O, H = sc.SC_VARIANT_SSTACK, sc.SC_VARIANT_OCC9, sc.SC_VARIANT_HSLOT
+    placed = {S, O, O | S, H, H | O, H | O | S}
     ring = [x for x in rows if x[4] != 0]
     assert {x[4] for x in ring} == placed and all(x[0] == 128 and x[1] == 64 for x in ring)
     assert best.variant in placed | {0}
