@@ -58,7 +58,7 @@ typedef enum {
   SC_ERR_NOMEM = -3,       /* host allocation failed or buffer too small    */
   SC_ERR_TIMEOUT = -4,     /* a bounded device wait ran out                 */
   SC_ERR_STACK = -5,       /* device traversal stack overflow (recorded)    */
-  SC_ERR_UNSUPPORTED = -6, /* configuration not supported by this build     */
+  SC_ERR_UNSUPPORTED = -6, /* configuration the library does not support    */
   SC_ERR_STATE = -7,       /* object in the wrong state for this call       */
   SC_ERR_IO = -8           /* file could not be read or written             */
 } sc_status;
