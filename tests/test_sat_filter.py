@@ -10,12 +10,15 @@ import os
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
+
+from paper_2305_08343_gb300 import scenegen as sg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_fp32_sat_filter_agrees_with_fp64(tmp_path):
+def _checker(tmp_path):
     cxx = shutil.which("g++")
     if cxx is None:
         pytest.skip("no C++ compiler")
@@ -24,6 +27,26 @@ def test_fp32_sat_filter_agrees_with_fp64(tmp_path):
                     os.path.join(ROOT, "paper_2305_08343_gb300", "csrc"),
                     os.path.join(ROOT, "tests", "sat_filter_check.cpp"), "-o", str(exe)],
                    check=True)
+    return exe
+
+
+def test_fp32_sat_filter_on_hair_leaves(tmp_path):
+    """The pairs a mask build of the 65K hair meets (four triangles per leaf
+    slot, every candidate voxel of its R = 6 grid): no disagreement, and the
+    filter decides all but a sliver of them."""
+    exe = _checker(tmp_path)
+    tris = np.ascontiguousarray(sg.hair(2048, 16, seed=1), dtype=np.float32)
+    path = tmp_path / "tris.bin"
+    tris.tofile(path)
+    out = subprocess.run([str(exe), str(path)], capture_output=True, text=True)
+    pairs, undecided, wrong = (int(x) for x in out.stdout.split())
+    assert out.returncode == 0 and wrong == 0, f"{wrong} disagreements"
+    assert pairs > 500000
+    assert undecided < pairs // 1000, f"{undecided} of {pairs} pairs undecided"
+
+
+def test_fp32_sat_filter_agrees_with_fp64(tmp_path):
+    exe = _checker(tmp_path)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     cases, undecided, wrong, rnd, rnd_open = (int(x) for x in out.stdout.split())
     assert out.returncode == 0 and wrong == 0, f"{wrong} disagreements"
