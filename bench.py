@@ -751,17 +751,33 @@ def run_gpu(args):
     peaks = load_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic, traffic_src = measured_traffic(args.workload, opts_c.variant)
-    if (args.layout != 1 or args.R or args.lut or args.skip_bits or args.stride != 1
-            or args.leaf_min or args.L != 3 or args.max_leaf != 4 or wide
-            or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
-            or opts.variant != DEFAULT_VARIANT):
+    default_config = not (args.layout != 1 or args.R or args.lut or args.skip_bits
+                          or args.stride != 1 or args.leaf_min or args.L != 3
+                          or args.max_leaf != 4 or wide
+                          or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
+                          or opts.variant != DEFAULT_VARIANT)
+    if not default_config:
         traffic, traffic_src = None, None  # measured for the default configuration only
+    # the captures of the other option sets of this workload on this source
+    sibling = [t for t in (measured_traffic(args.workload, v)[0]
+                           for (w, v) in MEASURED_TRAFFIC if w == args.workload)
+               if t is not None] if default_config else []
     l2_peak, l2_mb = measure_l2_peak(dev)
     # The bound: DRAM traffic far below the algorithmic bytes means the
     # fetched bytes come from L2 (the working set of one frame stays there),
-    # so the L2 read bandwidth is the roofline; HBM otherwise.
+    # so the L2 read bandwidth is the roofline; HBM otherwise.  Without a
+    # capture of the chosen option set, the bound follows the option sets of
+    # the same kernel source that were captured, if every one of them is on
+    # chip; `traffic` then stays null.
     on_chip = traffic is not None and traffic < 0.25 * per_launch_bytes
-    if traffic is None:
+    if traffic is None and sibling and max(sibling) < 0.25 * per_launch_bytes:
+        on_chip = True
+        bound_basis = (f"no DRAM capture of option set {opts_c.variant}; the "
+                       f"{len(sibling)} captured option sets of this kernel source move "
+                       f"{min(sibling) / 1e9:.2f}-{max(sibling) / 1e9:.2f} GB per launch, at "
+                       f"most {100 * max(sibling) / per_launch_bytes:.1f}% of the "
+                       f"algorithmic bytes")
+    elif traffic is None:
         bound_basis = ("no DRAM capture of this kernel source: bound taken as HBM; the "
                        "fraction against L2 is given beside it")
     elif on_chip:
