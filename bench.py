@@ -77,6 +77,39 @@ MEASURED_TRAFFIC = {
 }
 
 
+def traffic_bound(workload: str, variant: int, per_launch_bytes: float, default_config: bool):
+    """(traffic, its profile, on chip?, why) for the culled kernel of a run.
+
+    DRAM traffic far below the algorithmic bytes means the fetched bytes come
+    from L2 (the working set of one frame stays there), so the L2 read
+    bandwidth is the roofline; HBM otherwise.  Traffic is known only for the
+    default configuration, and only for the option sets captured on the
+    current kernel source.  Without a capture of the chosen option set the
+    bound follows the captured option sets of the same source, if every one
+    of them is on chip; the traffic then stays None."""
+    limit = 0.25 * per_launch_bytes
+    if not default_config:
+        return None, None, False, ("not the default configuration: bound taken as HBM; the "
+                                   "fraction against L2 is given beside it")
+    traffic, src = measured_traffic(workload, variant)
+    if traffic is not None:
+        if traffic < limit:
+            return traffic, src, True, (f"DRAM traffic {traffic / 1e9:.2f} GB per launch is "
+                                        f"{100 * traffic / per_launch_bytes:.1f}% of the "
+                                        f"algorithmic bytes")
+        return traffic, src, False, "DRAM traffic is a large part of the algorithmic bytes"
+    sibling = [t for t in (measured_traffic(w, v)[0] for (w, v) in MEASURED_TRAFFIC
+                           if w == workload) if t is not None]
+    if sibling and max(sibling) < limit:
+        return None, None, True, (
+            f"no DRAM capture of option set {variant}; the {len(sibling)} captured option "
+            f"sets of this kernel source move {min(sibling) / 1e9:.2f}-"
+            f"{max(sibling) / 1e9:.2f} GB per launch, at most "
+            f"{100 * max(sibling) / per_launch_bytes:.1f}% of the algorithmic bytes")
+    return None, None, False, ("no DRAM capture of this kernel source: bound taken as HBM; "
+                               "the fraction against L2 is given beside it")
+
+
 def measured_traffic(workload: str, variant: int = 0):
     import hashlib
     entry = MEASURED_TRAFFIC.get((workload, variant))
@@ -750,41 +783,14 @@ def run_gpu(args):
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     peaks = load_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic, traffic_src = measured_traffic(args.workload, opts_c.variant)
     default_config = not (args.layout != 1 or args.R or args.lut or args.skip_bits
                           or args.stride != 1 or args.leaf_min or args.L != 3
                           or args.max_leaf != 4 or wide
                           or bounces != WORKLOAD_BOUNCES.get(args.workload, 1)
                           or opts.variant != DEFAULT_VARIANT)
-    if not default_config:
-        traffic, traffic_src = None, None  # measured for the default configuration only
-    # the captures of the other option sets of this workload on this source
-    sibling = [t for t in (measured_traffic(args.workload, v)[0]
-                           for (w, v) in MEASURED_TRAFFIC if w == args.workload)
-               if t is not None] if default_config else []
+    traffic, traffic_src, on_chip, bound_basis = traffic_bound(
+        args.workload, opts_c.variant, per_launch_bytes, default_config)
     l2_peak, l2_mb = measure_l2_peak(dev)
-    # The bound: DRAM traffic far below the algorithmic bytes means the
-    # fetched bytes come from L2 (the working set of one frame stays there),
-    # so the L2 read bandwidth is the roofline; HBM otherwise.  Without a
-    # capture of the chosen option set, the bound follows the option sets of
-    # the same kernel source that were captured, if every one of them is on
-    # chip; `traffic` then stays null.
-    on_chip = traffic is not None and traffic < 0.25 * per_launch_bytes
-    if traffic is None and sibling and max(sibling) < 0.25 * per_launch_bytes:
-        on_chip = True
-        bound_basis = (f"no DRAM capture of option set {opts_c.variant}; the "
-                       f"{len(sibling)} captured option sets of this kernel source move "
-                       f"{min(sibling) / 1e9:.2f}-{max(sibling) / 1e9:.2f} GB per launch, at "
-                       f"most {100 * max(sibling) / per_launch_bytes:.1f}% of the "
-                       f"algorithmic bytes")
-    elif traffic is None:
-        bound_basis = ("no DRAM capture of this kernel source: bound taken as HBM; the "
-                       "fraction against L2 is given beside it")
-    elif on_chip:
-        bound_basis = (f"DRAM traffic {traffic / 1e9:.2f} GB per launch is "
-                       f"{100 * traffic / per_launch_bytes:.1f}% of the algorithmic bytes")
-    else:
-        bound_basis = "DRAM traffic is a large part of the algorithmic bytes"
     bound_l2 = on_chip and bool(l2_peak)
     peak = l2_peak if bound_l2 else hbm_peak
     roofline = {"bound": "l2" if bound_l2 else "hbm", "achieved": achieved, "peak": peak,

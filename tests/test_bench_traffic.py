@@ -36,3 +36,29 @@ def test_traffic_entries_match_the_kernel_source_and_profiles():
 def test_unmeasured_workload_reports_no_traffic():
     assert bench.measured_traffic("soup4m") == (None, None)
     assert bench.measured_traffic("hair12m", 2) == (None, None)
+
+
+def test_traffic_bound_cases(monkeypatch):
+    """traffic_bound: the chosen option set's capture decides; without one,
+    the captured option sets of the same source decide when all are on chip;
+    otherwise, and outside the default configuration, the bound is HBM."""
+    sha = hashlib.sha256(open(KERNEL, "rb").read()).hexdigest()
+    table = {("w", 0): (1e9, sha, "p"), ("w", 128): (2e9, sha, "p"),
+             ("x", 0): (30e9, sha, "p")}
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", table)
+    big = 50e9  # algorithmic bytes per launch
+    t, src, on_chip, why = bench.traffic_bound("w", 0, big, True)
+    assert (t, src, on_chip) == (1e9, "p", True) and "2.0%" in why
+    t, src, on_chip, why = bench.traffic_bound("w", 1024, big, True)
+    assert (t, src, on_chip) == (None, None, True) and "option set 1024" in why
+    t, src, on_chip, why = bench.traffic_bound("w", 0, big, False)
+    assert (t, on_chip) == (None, False)
+    t, src, on_chip, why = bench.traffic_bound("x", 0, big, True)
+    assert (t, on_chip) == (30e9, False)
+    t, src, on_chip, why = bench.traffic_bound("x", 5, big, True)
+    assert (t, on_chip) == (None, False)  # its only capture is off chip
+    t, src, on_chip, why = bench.traffic_bound("soup4m", 0, big, True)
+    assert (t, on_chip) == (None, False) and "no DRAM capture" in why
+    # a capture of another kernel source counts for nothing
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", {("w", 0): (1e9, "0" * 64, "p")})
+    assert bench.traffic_bound("w", 128, big, True)[2] is False
